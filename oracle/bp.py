@@ -1,0 +1,165 @@
+"""Belief propagation and the Bethe value of C(t) (oracle, complex128).
+
+Double layer (Sec. 2.3; Eq. 11 read as matrix messages, Eq. 13 damping,
+Eq. 12 stopping rule):
+  M_{v->w}[i,i'] = sum conj(O_v[..i..j..]) O_v[..i'..j'..] prod_{u != w} M_{u->v}[j_u, j'_u]
+  (the physical pair is traced, i.e. the Hilbert-Schmidt norm network);
+  Hermitian-symmetrise, normalise to unit trace, damp
+  M <- (1 - alpha) M_old + alpha M_hat, delta = max_i |M[i,i] - M_old[i,i]|,
+  Jacobi schedule (every new message from the previous sweep), stop when
+  delta < tol or after max_sweeps.
+
+Single layer (Sec. 2.5 step 1: pin Z at c and I elsewhere; vector messages,
+"observable-specific messages can be negative"):
+  t_v = Tr(O_v P_v) / 2,  m_{v->w}[i] = sum t_v[..i..j..] prod_{u != w} m_{u->v}[j_u];
+  unit 2-norm, phase aligned with the previous iterate before damping, same
+  alpha / tol / max_sweeps.  Initial m_{v->w} = sqrt(diag M_{v->w}), normalised.
+
+Bethe value with sign (phase) tracking (Eq. 14-16):
+  log|C_proj| = sum_v log|vs_v| - sum_e log|Z_e|,  Z_e = sum_i m_ab[i] m_ba[i]
+  log N       = sum_v log f_v - sum_e log Z2_e,  Z2_e = sum_ij M_ab[i,j] M_ba[i,j]
+  C(t)        = phase * exp(log|C_proj| - log N / 2)
+where vs_v (f_v) is the full contraction of the single (double) layer site
+with all of its incoming messages, each carrying the per-site factor 1/2 of
+the normalised trace.  Dividing by sqrt(N) (the paper's "Bethe norm",
+Table 1) makes the estimate independent of the network's overall scale; when
+N = 1 it is the paper's Eq. 16.
+
+Pinned by: tests/test_oracle_pepo.py -- on trees (1 x N chains and the star
+around an edge site) BP is exact, so the Bethe value must equal the dense
+C(t), including the negative values of cos(2 J t)^3.  On loops the Bethe
+value itself has no closed form: parity unpinned for the loopy Bethe number
+(only the tree pins cover this code).
+"""
+import numpy as np
+
+from . import gates as G
+from .pepo import bond_key, leg_apply
+
+
+def _contract_all_but(A, B, k):
+    axes = [a for a in range(A.ndim) if a != k]
+    return np.tensordot(A.conj(), B, axes=(axes, axes))
+
+
+def double_message(net, v, k_out, M):
+    Y = net.O[v]
+    for k, (_, u) in enumerate(net.legs[v]):
+        if k != k_out:
+            Y = leg_apply(Y, k, M[(u, v)])
+    return _contract_all_but(net.O[v], Y, k_out)
+
+
+def bp_double(net, alpha, tol, max_sweeps):
+    """Damped Jacobi BP on the double layer; updates net.M in place."""
+    M = {k: m.copy() for k, m in net.M.items()}
+    sweeps, delta = 0, float("inf")
+    for sweep in range(1, max_sweeps + 1):
+        newM = {}
+        delta = 0.0
+        for v in range(net.N):
+            for k, (_, u) in enumerate(net.legs[v]):
+                Mh = double_message(net, v, k, M)
+                Mh = 0.5 * (Mh + Mh.conj().T)
+                tr = np.real(np.trace(Mh))
+                if not tr > 0:
+                    raise FloatingPointError("double-layer message has no weight")
+                Mh = Mh / tr
+                old = M[(v, u)]
+                Mn = (1.0 - alpha) * old + alpha * Mh
+                delta = max(delta, float(np.max(np.abs(np.diag(Mn) - np.diag(old)))))
+                newM[(v, u)] = Mn
+        M = newM
+        sweeps = sweep
+        if delta < tol:
+            break
+    net.M = M
+    return sweeps, delta
+
+
+def pinned_tensors(net):
+    t = []
+    for v in range(net.N):
+        P = G.PAULI[net.obs_pauli] if v == net.obs_site else G.I2
+        t.append(np.einsum("...ab,ba->...", net.O[v], P) / 2.0)
+    return t
+
+
+def _vector_contract(T, legs, v, m, skip):
+    Y = T
+    for k in range(len(legs) - 1, -1, -1):
+        if k == skip:
+            continue
+        u = legs[k][1]
+        Y = np.tensordot(Y, m[(u, v)], axes=([k], [0]))
+    return Y
+
+
+def bp_single(net, t, alpha, tol, max_sweeps):
+    m = {}
+    for (u, v), Muv in net.M.items():
+        d = np.sqrt(np.clip(np.real(np.diag(Muv)), 0.0, None)).astype(np.complex128)
+        n = np.linalg.norm(d)
+        m[(u, v)] = d / n if n > 0 else d
+    sweeps, delta = 0, float("inf")
+    for sweep in range(1, max_sweeps + 1):
+        newm = {}
+        delta = 0.0
+        for v in range(net.N):
+            for k, (_, u) in enumerate(net.legs[v]):
+                mh = _vector_contract(t[v], net.legs[v], v, m, k)
+                n = np.linalg.norm(mh)
+                if n > 0:
+                    mh = mh / n
+                old = m[(v, u)]
+                ph = np.vdot(old, mh)
+                if abs(ph) > 0:
+                    mh = mh * (np.conj(ph) / abs(ph))
+                mn = (1.0 - alpha) * old + alpha * mh
+                delta = max(delta, float(np.max(np.abs(mn - old))))
+                newm[(v, u)] = mn
+        m = newm
+        sweeps = sweep
+        if delta < tol:
+            break
+    return m, sweeps, delta
+
+
+def bethe(net, t, m, M):
+    """Return dict with C, C_proj, norm (Bethe norm N) and their logs."""
+    logc, phase, zero = 0.0, 1.0 + 0j, False
+    for v in range(net.N):
+        vs = complex(_vector_contract(t[v], net.legs[v], v, m, -1))
+        if vs == 0:
+            zero = True
+            continue
+        logc += np.log(abs(vs))
+        phase *= vs / abs(vs)
+    logn = 0.0
+    for v in range(net.N):
+        Y = net.O[v]
+        for k, (_, u) in enumerate(net.legs[v]):
+            Y = leg_apply(Y, k, M[(u, v)])
+        f = np.real(np.vdot(net.O[v].ravel(), Y.ravel())) / 2.0
+        logn += np.log(f)
+    seen = set()
+    for v in range(net.N):
+        for (_, u) in net.legs[v]:
+            b = bond_key(u, v)
+            if b in seen:
+                continue
+            seen.add(b)
+            a, c = b
+            Z = complex(np.sum(m[(a, c)] * m[(c, a)]))
+            if Z == 0:
+                raise FloatingPointError("single-layer edge weight vanished")
+            logc -= np.log(abs(Z))
+            phase /= Z / abs(Z)
+            Z2 = np.real(np.sum(M[(a, c)] * M[(c, a)]))
+            logn -= np.log(Z2)
+    if zero:
+        return {"C": 0.0, "C_proj": 0.0, "norm": float(np.exp(logn)), "log_norm": logn,
+                "phase_imag": 0.0}
+    C = float(np.real(phase)) * np.exp(logc - 0.5 * logn)
+    return {"C": C, "C_proj": float(np.real(phase)) * np.exp(logc), "norm": float(np.exp(logn)),
+            "log_norm": logn, "phase_imag": float(np.imag(phase))}
