@@ -1,0 +1,191 @@
+/*
+ * libpepo -- C ABI of the GB300 (sm_103a) implementation of the
+ * Heisenberg-picture operator-network (PEPO) evolution of the 2D
+ * transverse-field Ising model.
+ *
+ * Method (paper arxiv 2606.30985):
+ *   Sec. 2.1  Eq. 1       H = -J sum X_i X_j - h sum Z_i (or the ZZ/X gate set)
+ *   Sec. 2.2  Eq. 4       C(t) = Tr[Z_c(t) Z_c] / 2^N
+ *   Sec. 2.3              Pauli-basis network, site tensor chi^deg x 4
+ *   Sec. 2.3  Eq. 5, 6    Trotter step O -> U^dagger O U, four-colour bonds
+ *   Sec. 2.4  Alg. 1      bond update: absorb, QR, RR, gate, SVD, truncate,
+ *                         reconstruct, deabsorb, Vidal normalisation
+ *   Sec. 4.2  Eq. 7       hybrid QR (Cholesky-QR for tall n > 150, m/n > 150)
+ *   Sec. 4.2  Eq. 9, 10   truncation and lambda = s / ||s||
+ *   Sec. 4.2  Eq. 11, 12  BP message update and stopping rule
+ *   Sec. 6.4  Eq. 13      damped BP
+ *   Sec. 2.5  Eq. 14-16   Bethe value of C(t) in log space with signs
+ *   Sec. 3.1              zero-malloc workspace / IsingState
+ *   Sec. 5    Eq. 17-19   analytic memory model
+ *
+ * Conventions shared by every entry point
+ *   - Sites: (x, y), x = column in [0, Lx), y = row in [0, Ly), origin top
+ *     left; site index v = y * Lx + x.
+ *   - Bonds: horizontal bond (x,y)-(x+1,y) has id y*(Lx-1) + x; vertical bond
+ *     (x,y)-(x,y+1) has id Ly*(Lx-1) + y*Lx + x.  The "first" site of a bond
+ *     is the left / upper one.  Colour of a horizontal bond = x % 2, of a
+ *     vertical bond = 2 + y % 2 (Sec. 2.3 four-colour partition).
+ *   - Site tensors in the canonical host layout: legs [U, D, L, R] (absent
+ *     legs skipped), then the Pauli index p in {I, X, Y, Z} = {0,1,2,3},
+ *     row-major (Pauli fastest), real coefficients.  Element type double.
+ *   - Directed messages: message of bond b in direction dir (0: first site ->
+ *     second site, 1: second -> first) is the environment of the receiving
+ *     site's leg on b; chi x chi, row-major, real symmetric.
+ *   - Ownership: the caller owns the device arena, the CUDA stream and every
+ *     host array.  After pepo_init the library never allocates device memory
+ *     (Sec. 3.1 zero-malloc rule); it carves everything from the arena.
+ *   - Errors: every call returns a pepo_status and never aborts.  On an error
+ *     pepo_last_error(ctx) returns a message.  BP non-convergence is a
+ *     reported outcome (sweeps == max), not an error.
+ *   - Threading: calls on one context must not run concurrently.
+ *   - Asynchrony: pepo_trotter_step only enqueues work on the stream; calls
+ *     that return host values synchronise the stream.
+ */
+#ifndef PEPO_H
+#define PEPO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pepo_ctx pepo_ctx;
+
+typedef enum {
+  PEPO_OK = 0,
+  PEPO_E_INVALID = 1,   /* bad argument or configuration */
+  PEPO_E_OOM = 2,       /* arena smaller than pepo_required_bytes */
+  PEPO_E_CUDA = 3,      /* a CUDA runtime call failed */
+  PEPO_E_NUMERIC = 4,   /* NaN / Inf or a vanished bond matrix */
+  PEPO_E_STATE = 5      /* call out of order (e.g. spectrum before any step) */
+} pepo_status;
+
+typedef enum {
+  PEPO_GATES_ZZ_X = 0,  /* exp(-i J dt ZZ) bonds, exp(-i h dt X) sites */
+  PEPO_GATES_XX_Z = 1   /* the paper's Eq. 1 / Eq. 6 convention */
+} pepo_gateset;
+
+typedef enum {
+  PEPO_FP64 = 0,        /* site tensors and all arithmetic in double */
+  PEPO_FP32 = 1,        /* site tensors float; small linear algebra double */
+  PEPO_TF32X3 = 2,      /* reserved: split-precision tensor-core GEMMs */
+  PEPO_BF16X3 = 3       /* reserved */
+} pepo_precision;
+
+typedef struct {
+  int Lx, Ly;              /* grid; Lx * Ly >= 2 */
+  double J, h, dt;         /* couplings and Trotter step */
+  int trotter_order;       /* 1: site gates then bonds; 2: symmetric split */
+  int obs_x, obs_y;        /* observable site */
+  int obs_pauli;           /* 1 = X, 2 = Y, 3 = Z */
+  int chi_max;             /* bond-dimension cap, >= 1 */
+  double eps_cut;          /* Eq. 9 relative singular-value cut (1e-11) */
+  double bp_alpha;         /* Eq. 13 damping (1 = undamped) */
+  double bp_tol;           /* Eq. 12 tolerance on the message diagonals */
+  int bp_max_sweeps;       /* sweep budget (100) */
+  int qr_n_thresh;         /* Eq. 7 branch: Cholesky-QR if n > qr_n_thresh ... */
+  double qr_ratio_thresh;  /* ... and m / n > qr_ratio_thresh (150, 150) */
+  double pinv_rel;         /* rank threshold for message square roots (1e-12) */
+  int gates;               /* pepo_gateset */
+  int prec;                /* pepo_precision */
+  int warm_start;          /* reserved, 0 */
+  int inflight_sites;      /* sites updated concurrently (scratch slabs), 0 = auto */
+} pepo_config;
+
+/* Per-instance measurement record (Table 1 diagnostics). */
+typedef struct {
+  double C;                /* Eq. 16 / Bethe ratio: C_proj / sqrt(norm) */
+  double C_proj;           /* single-layer Bethe value (with site scales) */
+  double log_norm;         /* log of the double-layer Bethe value ("Bethe norm") */
+  double gate_err;         /* Table 1: discarded weight summed over the last step */
+  int bp_sweeps;           /* double-layer sweeps of the last pepo_bp_converge */
+  double bp_delta;
+  int bp1_sweeps;          /* single-layer sweeps */
+  double bp1_delta;
+  double entropy_frac_max; /* Table 1: max over bonds of S_e / log chi_e */
+  int trap_type1;          /* sweeps >= 30 and delta < tol (Sec. 6.4) */
+  int trap_type2;          /* sweeps == max */
+  int norm_exploded;       /* exp(log_norm) >= 2 */
+  int flags;               /* bit 0: rank-deficient message met (env projector
+                              skipped), bit 1: non-finite value seen,
+                              bit 2: a Jacobi SVD hit its sweep cap */
+  int steps;               /* Trotter steps taken so far */
+} pepo_diag;
+
+/* Fill *cfg with the paper's defaults (Sec. 6: eps_cut 1e-11, tol 1e-5,
+ * 100 sweeps, thresholds 150/150) and the ZZ_X gate set, 3x3 grid. */
+void pepo_config_default(pepo_config* cfg);
+
+/* Bytes of device memory pepo_init needs for n_inst instances (array cfgs).
+ * Returns 0 if a configuration is invalid.  Follows the analytic memory model
+ * (Eq. 17-19) adapted to this implementation: site tensors at chi_max, two
+ * scratch slabs per in-flight site, messages and small workspaces. */
+size_t pepo_required_bytes(const pepo_config* cfgs, int n_inst);
+
+/* Create a context.  cfgs: n_inst configurations (host, copied).  dev_arena:
+ * device pointer, 256-byte aligned, at least pepo_required_bytes bytes, owned
+ * by the caller and kept alive until pepo_destroy.  cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream).  Initialises every instance to
+ * the Sec. 2.3 initial state (observable Pauli at the chosen site, identity
+ * elsewhere, all chi = 1, all messages [[1]]).  Errors: PEPO_E_INVALID,
+ * PEPO_E_OOM, PEPO_E_CUDA; *out is NULL on error. */
+pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena,
+                      size_t arena_bytes, void* cuda_stream, pepo_ctx** out);
+
+/* Enqueue n_steps Trotter steps (Eq. 6 schedule, Alg. 1 per bond) on every
+ * instance.  Asynchronous. */
+pepo_status pepo_trotter_step(pepo_ctx* ctx, int n_steps);
+
+/* Run damped double-layer BP (Eq. 11-13) to tolerance or the sweep budget.
+ * sweeps_out / delta_out: host arrays of n_inst entries (may be NULL).
+ * Synchronises the stream. */
+pepo_status pepo_bp_converge(pepo_ctx* ctx, int* sweeps_out, double* delta_out);
+
+/* Single-layer BP on the pinned network and the Bethe value of C(t)
+ * (Eq. 14-16).  Uses the current double-layer messages (call
+ * pepo_bp_converge first).  C_out: n_inst doubles; diag_out: n_inst records
+ * (either may be NULL).  Synchronises the stream. */
+pepo_status pepo_correlator(pepo_ctx* ctx, double* C_out, pepo_diag* diag_out);
+
+/* Vidal-normalised singular values of a bond (Eq. 10) from its last update.
+ * lam_out: at least chi_max doubles; *chi_out receives the live chi. */
+pepo_status pepo_get_spectrum(pepo_ctx* ctx, int inst, int bond, double* lam_out,
+                              int* chi_out);
+
+/* Copy a site tensor to the host in the canonical layout, multiplied by its
+ * stored scale exp(sigma_v).  dims_out: 4 ints, the live chi of legs U, D, L,
+ * R (0 for absent legs).  out: host doubles, capacity `count`. */
+pepo_status pepo_get_site(pepo_ctx* ctx, int inst, int site, double* out, size_t count,
+                          int* dims_out);
+
+/* Overwrite the state of one instance: every site tensor (canonical layout,
+ * concatenated in site order), every bond's chi and lambda, and every
+ * directed message.  chi: nbonds ints; lam: nbonds * chi_max doubles (first
+ * chi[b] used); msgs: nbonds * 2 * chi_max * chi_max doubles (row-major
+ * chi[b] x chi[b] block at the start of each chi_max^2 slot).  Used to start
+ * from a synthetic saturated state.  Synchronises the stream. */
+pepo_status pepo_set_state(pepo_ctx* ctx, int inst, const double* sites, size_t count,
+                           const int* chi, const double* lam, const double* msgs);
+
+/* Copy one directed message (chi x chi, row-major) to the host. */
+pepo_status pepo_get_message(pepo_ctx* ctx, int inst, int bond, int dir, double* out,
+                             int* chi_out);
+
+/* Number of bonds of instance inst (0 on a bad argument). */
+int pepo_num_bonds(const pepo_ctx* ctx, int inst);
+
+/* Number of kernel launches enqueued by this context so far. */
+long long pepo_launch_count(const pepo_ctx* ctx);
+
+/* Last error message of the context (static string if ctx is NULL). */
+const char* pepo_last_error(const pepo_ctx* ctx);
+
+/* Release host-side resources.  Does not free the arena (the caller owns it). */
+void pepo_destroy(pepo_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PEPO_H */

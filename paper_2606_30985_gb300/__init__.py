@@ -1,0 +1,290 @@
+"""GB300-native Heisenberg-picture PEPO evolution of the 2D transverse-field Ising model.
+
+Thin ctypes binding of ``libpepo.so`` (C ABI in ``include/pepo.h``).  Every step
+of the method runs in the library's CUDA kernels; this module only marshals
+arguments.  PyTorch supplies the device arena (one uint8 tensor) and the stream.
+There is no CPU fallback: if the library or a CUDA device is missing, the
+constructor raises.
+"""
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpepo.so")
+
+GATES = {"ZZ_X": 0, "XX_Z": 1}
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3}
+PAULI = {"X": 1, "Y": 2, "Z": 3}
+STATUS = {0: "ok", 1: "invalid argument", 2: "arena too small", 3: "CUDA error",
+          4: "numeric failure", 5: "call out of order"}
+
+
+class PepoError(RuntimeError):
+    pass
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int),
+                ("J", ctypes.c_double), ("h", ctypes.c_double), ("dt", ctypes.c_double),
+                ("trotter_order", ctypes.c_int),
+                ("obs_x", ctypes.c_int), ("obs_y", ctypes.c_int), ("obs_pauli", ctypes.c_int),
+                ("chi_max", ctypes.c_int), ("eps_cut", ctypes.c_double),
+                ("bp_alpha", ctypes.c_double), ("bp_tol", ctypes.c_double),
+                ("bp_max_sweeps", ctypes.c_int),
+                ("qr_n_thresh", ctypes.c_int), ("qr_ratio_thresh", ctypes.c_double),
+                ("pinv_rel", ctypes.c_double),
+                ("gates", ctypes.c_int), ("prec", ctypes.c_int), ("warm_start", ctypes.c_int),
+                ("inflight_sites", ctypes.c_int)]
+
+
+class _Diag(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_double), ("C_proj", ctypes.c_double), ("log_norm", ctypes.c_double),
+                ("gate_err", ctypes.c_double), ("bp_sweeps", ctypes.c_int),
+                ("bp_delta", ctypes.c_double), ("bp1_sweeps", ctypes.c_int),
+                ("bp1_delta", ctypes.c_double), ("entropy_frac_max", ctypes.c_double),
+                ("trap_type1", ctypes.c_int), ("trap_type2", ctypes.c_int),
+                ("norm_exploded", ctypes.c_int), ("flags", ctypes.c_int), ("steps", ctypes.c_int)]
+
+
+EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trotter_step",
+           "pepo_bp_converge", "pepo_correlator", "pepo_get_spectrum", "pepo_get_site",
+           "pepo_set_state", "pepo_get_message", "pepo_num_bonds", "pepo_launch_count",
+           "pepo_last_error", "pepo_destroy"]
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libpepo.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise PepoError("libpepo.so not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    CP = ctypes.POINTER(_Config)
+    lib.pepo_config_default.argtypes = [CP]
+    lib.pepo_config_default.restype = None
+    lib.pepo_required_bytes.argtypes = [CP, I]
+    lib.pepo_required_bytes.restype = S
+    lib.pepo_init.argtypes = [CP, I, P, S, P, ctypes.POINTER(P)]
+    lib.pepo_init.restype = I
+    lib.pepo_trotter_step.argtypes = [P, I]
+    lib.pepo_trotter_step.restype = I
+    lib.pepo_bp_converge.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(D)]
+    lib.pepo_bp_converge.restype = I
+    lib.pepo_correlator.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(_Diag)]
+    lib.pepo_correlator.restype = I
+    lib.pepo_get_spectrum.argtypes = [P, I, I, ctypes.POINTER(D), ctypes.POINTER(I)]
+    lib.pepo_get_spectrum.restype = I
+    lib.pepo_get_site.argtypes = [P, I, I, ctypes.POINTER(D), S, ctypes.POINTER(I)]
+    lib.pepo_get_site.restype = I
+    lib.pepo_set_state.argtypes = [P, I, ctypes.POINTER(D), S, ctypes.POINTER(I), ctypes.POINTER(D),
+                                   ctypes.POINTER(D)]
+    lib.pepo_set_state.restype = I
+    lib.pepo_get_message.argtypes = [P, I, I, I, ctypes.POINTER(D), ctypes.POINTER(I)]
+    lib.pepo_get_message.restype = I
+    lib.pepo_num_bonds.argtypes = [P, I]
+    lib.pepo_num_bonds.restype = I
+    lib.pepo_launch_count.argtypes = [P]
+    lib.pepo_launch_count.restype = ctypes.c_longlong
+    lib.pepo_last_error.argtypes = [P]
+    lib.pepo_last_error.restype = ctypes.c_char_p
+    lib.pepo_destroy.argtypes = [P]
+    lib.pepo_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+@dataclass
+class Config:
+    """One instance of the method (mirrors pepo_config; defaults of Sec. 6)."""
+    Lx: int = 3
+    Ly: int = 3
+    J: float = 1.0
+    h: float = 1.0
+    dt: float = 0.05
+    order: int = 1
+    obs: tuple = None
+    obs_pauli: str = "Z"
+    chi_max: int = 8
+    eps_cut: float = 1e-11
+    bp_alpha: float = 0.5
+    bp_tol: float = 1e-5
+    bp_max_sweeps: int = 100
+    qr_n_thresh: int = 150
+    qr_ratio_thresh: float = 150.0
+    pinv_rel: float = 1e-12
+    gateset: str = "ZZ_X"
+    precision: str = "fp32"
+    inflight_sites: int = 0
+
+    def to_c(self):
+        c = _Config()
+        obs = self.obs if self.obs is not None else ((self.Lx - 1) // 2, (self.Ly - 1) // 2)
+        c.Lx, c.Ly = self.Lx, self.Ly
+        c.J, c.h, c.dt = self.J, self.h, self.dt
+        c.trotter_order = self.order
+        c.obs_x, c.obs_y = obs
+        c.obs_pauli = PAULI[self.obs_pauli]
+        c.chi_max = self.chi_max
+        c.eps_cut = self.eps_cut
+        c.bp_alpha, c.bp_tol, c.bp_max_sweeps = self.bp_alpha, self.bp_tol, self.bp_max_sweeps
+        c.qr_n_thresh, c.qr_ratio_thresh = self.qr_n_thresh, self.qr_ratio_thresh
+        c.pinv_rel = self.pinv_rel
+        c.gates = GATES[self.gateset]
+        c.prec = PRECISIONS[self.precision]
+        c.warm_start = 0
+        c.inflight_sites = self.inflight_sites
+        return c
+
+
+def _cfg_array(cfgs):
+    arr = (_Config * len(cfgs))()
+    for i, c in enumerate(cfgs):
+        arr[i] = c.to_c()
+    return arr
+
+
+def required_bytes(cfgs):
+    """Device bytes pepo_init needs (host-only computation; 0 for an invalid config)."""
+    if isinstance(cfgs, Config):
+        cfgs = [cfgs]
+    lib = load_library()
+    return int(lib.pepo_required_bytes(_cfg_array(cfgs), len(cfgs)))
+
+
+def diag_to_dict(d):
+    return {name: getattr(d, name) for name, _ in _Diag._fields_}
+
+
+class Engine:
+    """A context of one or more instances living in one device arena."""
+
+    def __init__(self, cfgs, device="cuda:0"):
+        import torch
+        if isinstance(cfgs, Config):
+            cfgs = [cfgs]
+        self.cfgs = list(cfgs)
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise PepoError("a CUDA device is required (no CPU fallback)")
+        self.device = torch.device(device)
+        arr = _cfg_array(self.cfgs)
+        nbytes = int(self.lib.pepo_required_bytes(arr, len(self.cfgs)))
+        if nbytes == 0:
+            raise PepoError("invalid configuration")
+        with torch.cuda.device(self.device):
+            self.arena = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.stream = torch.cuda.current_stream(self.device)
+        self.arena_bytes = nbytes
+        ctx = ctypes.c_void_p()
+        st = self.lib.pepo_init(arr, len(self.cfgs), ctypes.c_void_p(self.arena.data_ptr()),
+                                nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx))
+        if st != 0:
+            raise PepoError("pepo_init failed: %s" % STATUS.get(st, st))
+        self.ctx = ctx
+
+    # -- helpers
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.pepo_last_error(self.ctx).decode()
+            raise PepoError("%s failed (%s): %s" % (what, STATUS.get(st, st), msg))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.pepo_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_inst(self):
+        return len(self.cfgs)
+
+    def launches(self):
+        return int(self.lib.pepo_launch_count(self.ctx))
+
+    # -- the four entry points of the method
+    def trotter_step(self, n=1):
+        self._check(self.lib.pepo_trotter_step(self.ctx, n), "pepo_trotter_step")
+
+    def bp_converge(self):
+        sw = (ctypes.c_int * self.n_inst)()
+        de = (ctypes.c_double * self.n_inst)()
+        self._check(self.lib.pepo_bp_converge(self.ctx, sw, de), "pepo_bp_converge")
+        return list(sw), list(de)
+
+    def correlator(self):
+        C = (ctypes.c_double * self.n_inst)()
+        D = (_Diag * self.n_inst)()
+        self._check(self.lib.pepo_correlator(self.ctx, C, D), "pepo_correlator")
+        return list(C), [diag_to_dict(d) for d in D]
+
+    # -- state access
+    def num_bonds(self, inst=0):
+        return int(self.lib.pepo_num_bonds(self.ctx, inst))
+
+    def spectrum(self, inst, bond):
+        cm = self.cfgs[inst].chi_max
+        lam = (ctypes.c_double * cm)()
+        chi = ctypes.c_int()
+        self._check(self.lib.pepo_get_spectrum(self.ctx, inst, bond, lam, ctypes.byref(chi)),
+                    "pepo_get_spectrum")
+        return np.array(lam[: chi.value])
+
+    def site(self, inst, v):
+        cm = self.cfgs[inst].chi_max
+        cap = 4 * cm ** 4
+        buf = np.zeros(cap)
+        dims = (ctypes.c_int * 4)()
+        self._check(self.lib.pepo_get_site(self.ctx, inst, v, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           cap, dims), "pepo_get_site")
+        d = [x for x in dims if x > 0]
+        n = 4 * int(np.prod(d)) if d else 4
+        return buf[:n].reshape(tuple(d) + (4,)), list(dims)
+
+    def message(self, inst, bond, direction):
+        cm = self.cfgs[inst].chi_max
+        buf = np.zeros(cm * cm)
+        chi = ctypes.c_int()
+        self._check(self.lib.pepo_get_message(self.ctx, inst, bond, direction,
+                                              buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              ctypes.byref(chi)), "pepo_get_message")
+        k = chi.value
+        return buf[: k * k].reshape(k, k)
+
+    def set_state(self, inst, sites, chi, lam, msgs):
+        """sites: list of arrays in canonical layout; chi: per bond; lam: [nb, chi_max];
+        msgs: [nb, 2, chi_max, chi_max]."""
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(s, dtype=np.float64).ravel() for s in sites]))
+        chi = np.ascontiguousarray(np.asarray(chi, dtype=np.int32))
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
+        msgs = np.ascontiguousarray(np.asarray(msgs, dtype=np.float64))
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.pepo_set_state(self.ctx, inst, flat.ctypes.data_as(dp), flat.size,
+                                            chi.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                            lam.ctypes.data_as(dp), msgs.ctypes.data_as(dp)),
+                    "pepo_set_state")
+
+    def run(self, nsteps, measure_every=1):
+        """Evolve nsteps, measuring C(t) (BP + correlator) every `measure_every` steps."""
+        out = []
+        self.bp_converge()
+        C, D = self.correlator()
+        out.append(D)
+        for s in range(1, nsteps + 1):
+            self.trotter_step(1)
+            if s % measure_every == 0 or s == nsteps:
+                self.bp_converge()
+                C, D = self.correlator()
+                out.append(D)
+        return out

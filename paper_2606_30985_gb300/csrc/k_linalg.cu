@@ -1,0 +1,760 @@
+// Small dense linear algebra of the bond update, FP64 unless noted.
+//
+//   k_env_factor   pivoted Cholesky square root L of a message M (L^T L = M):
+//                  the environment square root of Sec. 2.4 step 1 (Fig. 1
+//                  "pseudo_sqrt"); any factor with L^T L = M gives the same cv
+//                  Gram, so no eigensolver is needed.
+//   k_branch       Eq. 7 branch rule: Cholesky-QR when n > n_thr and
+//                  m / n > ratio_thr, Householder otherwise (Sec. 4.2).
+//   k_hh_level     Householder QR (TSQR tree, R only) of cv in its storage
+//                  precision with FP64 reductions (Sec. 4.2 Householder-QR).
+//   k_formG / k_formB   fold the gate's operator-Schmidt factors into the
+//                  R-factor: X = (F_kappa (x) 1) cv, G = X^T X or B = R-side of X.
+//   k_factor       rank-revealing factor T of X: pivoted Cholesky of G
+//                  (Cholesky-QR branch) or column-pivoted Householder of B.
+//   k_core         per bond: R1 R2^T, one-sided Jacobi SVD, truncation
+//                  (Eq. 9), lambda (Eq. 10), reconstruct matrices W1, W2
+//                  (Sec. 2.4 steps 5-8 in Q-less form), messages diag(lambda).
+#include "kernels.h"
+#include "linalg.h"
+
+namespace pepo {
+
+// ------------------------------------------------------------ block helpers
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; `red` must hold blockDim.x / 32 doubles.  All threads return it.
+__device__ inline double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+// Block-wide argmax over values[i] for i in [lo, hi); returns the index
+// (smallest index among ties).  `ri` needs blockDim.x / 32 ints, `rv` doubles.
+__device__ inline int block_argmax(const double* values, int lo, int hi, double* rv, int* ri) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double best = -1.0;
+  int bi = hi;
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double x = values[i];
+    if (x > best || (x == best && i < bi)) { best = x; bi = i; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  __syncthreads();
+  if (lane == 0) { rv[w] = best; ri[w] = bi; }
+  __syncthreads();
+  double b = -1.0;
+  int idx = hi;
+  for (int i = 0; i < nw; ++i)
+    if (rv[i] > b || (rv[i] == b && ri[i] < idx)) { b = rv[i]; idx = ri[i]; }
+  __syncthreads();
+  return idx;
+}
+
+// =============================================================== env factor
+// Pivoted (outer-product) Cholesky of the symmetrised message in shared memory.
+__global__ void __launch_bounds__(256)
+k_env_factor(const EnvFactorItem* __restrict__ items, int* ival, double rel) {
+  const EnvFactorItem it = items[blockIdx.x];
+  const int n = ival[it.chi_idx];
+  extern __shared__ __align__(16) double sm[];
+  double* A = sm;                 // n x n
+  double* dg = A + n * n;         // n
+  int* perm = reinterpret_cast<int*>(dg + n);
+  __shared__ double rv[8];
+  __shared__ int ri[8];
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int i = e / n, j = e - i * n;
+    A[e] = 0.5 * (it.M[i * it.ld + j] + it.M[j * it.ld + i]);
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = i;
+  __syncthreads();
+  double d0 = 0.0;
+  int rank = n;
+  for (int j = 0; j < n; ++j) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dg[i] = (i >= j) ? A[i * n + i] : -1.0;
+    __syncthreads();
+    int p = block_argmax(dg, j, n, rv, ri);
+    double dp = dg[p];
+    if (j == 0) d0 = dp;
+    if (!(dp > rel * d0) || !(dp > 0.0)) { rank = j; break; }
+    if (p != j) {  // symmetric swap of rows/cols j and p
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double t = A[j * n + k]; A[j * n + k] = A[p * n + k]; A[p * n + k] = t;
+      }
+      __syncthreads();
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double t = A[k * n + j]; A[k * n + j] = A[k * n + p]; A[k * n + p] = t;
+      }
+      if (threadIdx.x == 0) { int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
+      __syncthreads();
+    }
+    const double rjj = sqrt(A[j * n + j]);
+    __syncthreads();
+    for (int k = j + 1 + threadIdx.x; k < n; k += blockDim.x) A[j * n + k] /= rjj;
+    if (threadIdx.x == 0) A[j * n + j] = rjj;
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      int a = j + 1 + e / m, b = j + 1 + e % m;
+      A[a * n + b] -= A[j * n + a] * A[j * n + b];
+    }
+    __syncthreads();
+  }
+  // L[a][perm[q]] = R[a][q] (upper part), rows a < rank
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int a = e / n, q = e - a * n;
+    double v = (a < rank && q >= a) ? A[a * n + q] : 0.0;
+    it.L[a * it.ld + perm[q]] = v;
+  }
+  if (threadIdx.x == 0) ival[it.rank_idx] = rank;
+}
+
+cudaError_t launch_env_factor(const EnvFactorItem* items, int n_items, int chimax, int* ival,
+                              double rel, cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  size_t smem = sizeof(double) * ((size_t)chimax * chimax + chimax) + sizeof(int) * chimax;
+  cudaError_t e = cudaFuncSetAttribute(k_env_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_env_factor<<<n_items, 256, smem, s>>>(items, ival, rel);
+  return cudaGetLastError();
+}
+
+// =================================================================== branch
+__device__ inline void cv_shape(const TView& v, const int* ival, long long& m, int& n) {
+  m = 1;
+  for (int k = 0; k + 1 < v.nlegs; ++k) m *= ival[v.dim[k]];
+  n = 4 * (v.nlegs > 0 ? ival[v.dim[v.nlegs - 1]] : 1);
+}
+
+__global__ void k_branch(const SiteFacItem* __restrict__ items, int n_items, int* ival,
+                         int n_thr, double ratio_thr) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_items) return;
+  const SiteFacItem it = items[i];
+  long long m;
+  int n;
+  cv_shape(it.cv, ival, m, n);
+  ival[it.branch_idx] = (n > n_thr && (double)m / (double)n > ratio_thr) ? 1 : 0;
+}
+
+cudaError_t launch_branch(const SiteFacItem* items, int n_items, int* ival, int n_thr,
+                          double ratio_thr, cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  k_branch<<<ceil_div(n_items, 128), 128, 0, s>>>(items, n_items, ival, n_thr, ratio_thr);
+  return cudaGetLastError();
+}
+
+// ========================================================== Householder TSQR
+// Leaf rows L = max(4n, 256).  Level 0 factors each leaf in place; level l >= 1
+// gathers the R-blocks of four level-(l-1) blocks into the first one and
+// factors the stack.  R replaces the top rows of the block; entries below the
+// diagonal are zeroed (Q is never needed: the update is Q-less).
+__host__ __device__ inline long long hh_leaf_rows(int n) { return n * 4 > 256 ? (long long)n * 4 : 256; }
+
+template <typename T>
+__device__ void hh_block_qr(T* A, long long rows, int n, double* v, double* part, double* red) {
+  const int kmax = (int)(rows < n ? rows : n);
+  for (int j = 0; j < kmax; ++j) {
+    double s = 0.0;
+    for (long long i = j + threadIdx.x; i < rows; i += blockDim.x) {
+      double x = (double)A[i * n + j];
+      s = fma(x, x, s);
+    }
+    s = block_sum(s, red);
+    const double alpha = (double)A[(long long)j * n + j];
+    const double normx = sqrt(s);
+    __syncthreads();
+    if (normx == 0.0) continue;
+    const double beta = alpha >= 0.0 ? -normx : normx;
+    const double v0 = alpha - beta;
+    const double tau = (beta - alpha) / beta;
+    // v (unit leading entry) into shared memory; the column becomes (beta, 0, ...)
+    for (long long i = j + threadIdx.x; i < rows; i += blockDim.x) {
+      double vi = (i == j) ? 1.0 : (double)A[i * n + j] / v0;
+      v[i - j] = vi;
+    }
+    __syncthreads();
+    for (long long i = j + threadIdx.x; i < rows; i += blockDim.x) A[i * n + j] = (i == j) ? (T)beta : T(0);
+    const int nc = n - j - 1;
+    if (nc > 0) {
+      const int KC = nc < (int)blockDim.x ? nc : (int)blockDim.x;
+      const int RG = blockDim.x / KC;
+      const int t = threadIdx.x;
+      const int kk = t % KC, rg = t / KC;
+      for (int kb = 0; kb < nc; kb += KC) {
+        const int k = j + 1 + kb + kk;
+        double acc = 0.0;
+        if (rg < RG && kb + kk < nc) {
+          float accf = 0.f;
+          int run = 0;
+          for (long long i = j + rg; i < rows; i += RG) {
+            if (sizeof(T) == 4) {
+              accf = fmaf((float)v[i - j], (float)A[i * n + k], accf);
+              if (++run == 64) { acc += (double)accf; accf = 0.f; run = 0; }
+            } else {
+              acc = fma(v[i - j], (double)A[i * n + k], acc);
+            }
+          }
+          acc += (double)accf;
+        }
+        __syncthreads();
+        if (rg < RG) part[rg * KC + kk] = acc;
+        __syncthreads();
+        if (t < KC && kb + t < nc) {
+          double w = 0.0;
+          for (int g = 0; g < RG; ++g) w += part[g * KC + t];
+          part[RG * KC + t] = tau * w;
+        }
+        __syncthreads();
+        if (rg < RG && kb + kk < nc) {
+          const double tw = part[RG * KC + kk];
+          for (long long i = j + rg; i < rows; i += RG)
+            A[i * n + k] = (T)((double)A[i * n + k] - v[i - j] * tw);
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_hh_level(const SiteFacItem* __restrict__ items, int level, void* const* ptrs, const int* ival) {
+  const SiteFacItem it = items[blockIdx.y];
+  if (ival[it.branch_idx] != 0) return;
+  long long m;
+  int n;
+  cv_shape(it.cv, ival, m, n);
+  const long long L = hh_leaf_rows(n);
+  long long nb0 = (m + L - 1) / L;
+  // block size in rows at this level, and number of blocks
+  long long span = L, nblk = nb0;
+  for (int l = 0; l < level; ++l) {
+    if (nblk == 1) return;        // already reduced at an earlier level
+    span *= 4;
+    nblk = (nblk + 3) / 4;
+  }
+  const long long g = blockIdx.x;
+  if (g >= nblk) return;
+  T* A = static_cast<T*>(ptrs[it.cv.ref]);
+  extern __shared__ __align__(16) double sh[];
+  double* v = sh;                            // up to 4n (or L) rows
+  double* part = v + (L > 4 * n ? L : 4 * n);
+  __shared__ double red[8];
+  T* base = A + g * span * n;
+  long long rows;
+  if (level == 0) {
+    long long r0 = g * span;
+    rows = (m - r0) < span ? (m - r0) : span;
+  } else {
+    // gather the R rows of the four children into the first child's area
+    const long long cspan = span / 4;
+    rows = 0;
+    for (int c = 0; c < 4; ++c) {
+      const long long cr0 = g * span + c * cspan;
+      if (cr0 >= m) break;
+      long long crows_full = (m - cr0) < cspan ? (m - cr0) : cspan;
+      // rows of the child's R: min(rows of the child's own stack, n); the stack
+      // of a child has at most min(crows_full, ...) rows, and its R at most n
+      long long rr = crows_full < n ? crows_full : n;
+      if (c > 0) {
+        const T* src = A + cr0 * n;
+        for (long long e = threadIdx.x; e < rr * n; e += blockDim.x) base[rows * n + e] = src[e];
+        __syncthreads();
+      }
+      rows += rr;
+    }
+  }
+  hh_block_qr<T>(base, rows, n, v, part, red);
+}
+
+template <typename T>
+cudaError_t launch_hh_level(const SiteFacItem* items, int n_items, int level, int grid_x, int nmax,
+                            void* const* ptrs, const int* ival, cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  long long L = hh_leaf_rows(nmax);
+  size_t smem = sizeof(double) * ((size_t)(L > 4 * nmax ? L : 4 * nmax) + 256 + 256);
+  cudaError_t e = cudaFuncSetAttribute(k_hh_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_hh_level<T><<<dim3(grid_x, n_items), 256, smem, s>>>(items, level, ptrs, ival);
+  return cudaGetLastError();
+}
+
+// R (top min(m, n) rows of cv after the tree) -> FP64 C buffer, rows -> kfac
+template <typename T>
+__global__ void k_hh_extract(const SiteFacItem* __restrict__ items, void* const* ptrs, int* ival) {
+  const SiteFacItem it = items[blockIdx.x];
+  if (ival[it.branch_idx] != 0) return;
+  long long m;
+  int n;
+  cv_shape(it.cv, ival, m, n);
+  const int k = (int)(m < n ? m : n);
+  const T* A = static_cast<const T*>(ptrs[it.cv.ref]);
+  for (int e = threadIdx.x; e < k * n; e += blockDim.x) {
+    int a = e / n, q = e - a * n;
+    it.C[(long long)a * it.ldc + q] = (q >= a) ? (double)A[(long long)a * n + q] : 0.0;
+  }
+  if (threadIdx.x == 0) ival[it.kfac_idx] = k;
+}
+
+template <typename T>
+cudaError_t launch_hh_extract(const SiteFacItem* items, int n_items, void* const* ptrs, int* ival,
+                              cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  k_hh_extract<T><<<n_items, 256, 0, s>>>(items, ptrs, ival);
+  return cudaGetLastError();
+}
+
+// ============================================================ formG / formB
+// Cholesky branch: G[(c,k),(c',k')] = sum_{p,q} (F_k^T F_k')[p,q] C[(c,p),(c',q)].
+// Householder branch: B[(a,p'),(c,k)] = sum_p F_k[p',p] R[a,(c,p)].
+__global__ void k_form(const SiteFacItem* __restrict__ items, const int* ival) {
+  const SiteFacItem it = items[blockIdx.y];
+  long long m;
+  int n;
+  cv_shape(it.cv, ival, m, n);
+  const int chic = n / 4;
+  const int rg = ival[it.rg_idx];
+  const int r = rg * chic;
+  __shared__ double F[PEPO_RG * 16];
+  __shared__ double H[PEPO_RG * PEPO_RG * 16];
+  for (int e = threadIdx.x; e < rg * 16; e += blockDim.x) F[e] = it.F[e];
+  __syncthreads();
+  if (ival[it.branch_idx] == 1) {
+    for (int e = threadIdx.x; e < rg * rg * 16; e += blockDim.x) {
+      int k = e / (rg * 16), rest = e % (rg * 16);
+      int k2 = rest / 16, pq = rest % 16, p = pq / 4, q = pq % 4;
+      double h = 0.0;
+      for (int pp = 0; pp < 4; ++pp) h += F[k * 16 + pp * 4 + p] * F[k2 * 16 + pp * 4 + q];
+      H[e] = h;
+    }
+    __syncthreads();
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)chic * chic;
+         e += (long long)gridDim.x * blockDim.x) {
+      int c = (int)(e / chic), c2 = (int)(e % chic);
+      double Cb[16];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Cb[p * 4 + q] = it.C[(long long)(c * 4 + p) * it.ldc + c2 * 4 + q];
+      for (int k = 0; k < rg; ++k)
+        for (int k2 = 0; k2 < rg; ++k2) {
+          const double* h = H + (k * rg + k2) * 16;
+          double g = 0.0;
+#pragma unroll
+          for (int pq = 0; pq < 16; ++pq) g += h[pq] * Cb[pq];
+          it.T[(long long)(c * rg + k) * it.ldt + c2 * rg + k2] = g;
+        }
+    }
+  } else {
+    const int k = ival[it.kfac_idx];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)k * 4 * r;
+         e += (long long)gridDim.x * blockDim.x) {
+      int row = (int)(e / r), col = (int)(e % r);
+      int a = row / 4, pp = row % 4, c = col / rg, kk = col % rg;
+      double b = 0.0;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) b += F[kk * 16 + pp * 4 + p] * it.C[(long long)a * it.ldc + c * 4 + p];
+      it.T[(long long)row * it.ldt + col] = b;
+    }
+  }
+}
+
+cudaError_t launch_form(const SiteFacItem* items, int n_items, int grid_x, const int* ival,
+                        cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  k_form<<<dim3(grid_x, n_items), 256, 0, s>>>(items, ival);
+  return cudaGetLastError();
+}
+
+// =================================================================== factor
+// Cholesky branch: pivoted Cholesky of G (r x r, in place, row-major).
+// Householder branch: column-pivoted Householder QR of B (4k x r, in place).
+// Output: T (rank x r upper trapezoidal, pivoted column order) in place,
+// perm[q] = original column of pivoted column q, rank -> ival.
+__global__ void __launch_bounds__(512)
+k_factor(const SiteFacItem* __restrict__ items, int* ival) {
+  const SiteFacItem it = items[blockIdx.x];
+  long long m;
+  int n;
+  cv_shape(it.cv, ival, m, n);
+  const int chic = n / 4;
+  const int rg = ival[it.rg_idx];
+  const int r = rg * chic;
+  double* A = it.T;
+  const int ld = it.ldt;
+  extern __shared__ __align__(16) double sh[];
+  double* dg = sh;               // r: Schur diagonal / column norms^2
+  double* v = dg + r;            // 4k: Householder vector
+  double* w = v + 4 * n;         // r
+  int* perm = it.perm;
+  __shared__ double rv[16];
+  __shared__ int ri[16];
+  __shared__ double red[16];
+  for (int i = threadIdx.x; i < r; i += blockDim.x) perm[i] = i;
+  int rank = 0;
+  if (ival[it.branch_idx] == 1) {
+    for (int i = threadIdx.x; i < r; i += blockDim.x) dg[i] = A[(long long)i * ld + i];
+    __syncthreads();
+    double d0 = 0.0;
+    rank = r;
+    for (int j = 0; j < r; ++j) {
+      int p = block_argmax(dg, j, r, rv, ri);
+      double dp = dg[p];
+      if (j == 0) d0 = dp;
+      if (!(dp > it.rel * d0) || !(dp > 0.0)) { rank = j; break; }
+      if (p != j) {
+        for (int k = threadIdx.x; k < r; k += blockDim.x) {
+          double t = A[(long long)j * ld + k]; A[(long long)j * ld + k] = A[(long long)p * ld + k];
+          A[(long long)p * ld + k] = t;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < r; k += blockDim.x) {
+          double t = A[(long long)k * ld + j]; A[(long long)k * ld + j] = A[(long long)k * ld + p];
+          A[(long long)k * ld + p] = t;
+        }
+        if (threadIdx.x == 0) {
+          int t = perm[j]; perm[j] = perm[p]; perm[p] = t;
+          double td = dg[j]; dg[j] = dg[p]; dg[p] = td;
+        }
+        __syncthreads();
+      }
+      const double rjj = sqrt(A[(long long)j * ld + j]);
+      __syncthreads();
+      for (int k = j + 1 + threadIdx.x; k < r; k += blockDim.x) A[(long long)j * ld + k] /= rjj;
+      if (threadIdx.x == 0) A[(long long)j * ld + j] = rjj;
+      __syncthreads();
+      const int mm = r - j - 1;
+      for (long long e = threadIdx.x; e < (long long)mm * mm; e += blockDim.x) {
+        int a = j + 1 + (int)(e / mm), b = j + 1 + (int)(e % mm);
+        A[(long long)a * ld + b] -= A[(long long)j * ld + a] * A[(long long)j * ld + b];
+      }
+      __syncthreads();
+      for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) dg[i] = A[(long long)i * ld + i];
+      __syncthreads();
+    }
+  } else {
+    const int M = 4 * ival[it.kfac_idx];
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+      double s = 0.0;
+      for (int i = 0; i < M; ++i) { double x = A[(long long)i * ld + k]; s = fma(x, x, s); }
+      dg[k] = s;
+      w[k] = s;   // reference norms for the downdate safeguard
+    }
+    __syncthreads();
+    double n0 = 0.0;
+    const int kmax = M < r ? M : r;
+    rank = kmax;
+    for (int j = 0; j < kmax; ++j) {
+      int p = block_argmax(dg, j, r, rv, ri);
+      double dp = dg[p];
+      if (j == 0) n0 = dp;
+      if (!(dp > it.rel * it.rel * n0) || !(dp > 0.0)) { rank = j; break; }
+      if (p != j) {
+        for (int i = threadIdx.x; i < M; i += blockDim.x) {
+          double t = A[(long long)i * ld + j]; A[(long long)i * ld + j] = A[(long long)i * ld + p];
+          A[(long long)i * ld + p] = t;
+        }
+        if (threadIdx.x == 0) {
+          int t = perm[j]; perm[j] = perm[p]; perm[p] = t;
+          double td = dg[j]; dg[j] = dg[p]; dg[p] = td;
+          td = w[j]; w[j] = w[p]; w[p] = td;
+        }
+        __syncthreads();
+      }
+      double s = 0.0;
+      for (int i = j + threadIdx.x; i < M; i += blockDim.x) {
+        double x = A[(long long)i * ld + j];
+        s = fma(x, x, s);
+      }
+      s = block_sum(s, red);
+      const double alpha = A[(long long)j * ld + j];
+      const double normx = sqrt(s);
+      const double beta = alpha >= 0.0 ? -normx : normx;
+      const double v0 = alpha - beta;
+      const double tau = (beta - alpha) / beta;
+      for (int i = j + threadIdx.x; i < M; i += blockDim.x)
+        v[i - j] = (i == j) ? 1.0 : A[(long long)i * ld + j] / v0;
+      __syncthreads();
+      for (int i = j + threadIdx.x; i < M; i += blockDim.x) A[(long long)i * ld + j] = (i == j) ? beta : 0.0;
+      for (int k = j + 1 + threadIdx.x; k < r; k += blockDim.x) {
+        double acc = 0.0;
+        for (int i = j; i < M; ++i) acc = fma(v[i - j], A[(long long)i * ld + k], acc);
+        const double tw = tau * acc;
+        for (int i = j; i < M; ++i) A[(long long)i * ld + k] -= v[i - j] * tw;
+        const double rjk = A[(long long)j * ld + k];
+        double nd = dg[k] - rjk * rjk;
+        if (nd < 0.05 * w[k]) {  // cancellation: recompute the trailing norm
+          nd = 0.0;
+          for (int i = j + 1; i < M; ++i) { double x = A[(long long)i * ld + k]; nd = fma(x, x, nd); }
+          w[k] = nd;
+        }
+        dg[k] = nd;
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) ival[it.rank_idx] = rank;
+}
+
+cudaError_t launch_factor(const SiteFacItem* items, int n_items, int rmax, int nmax, int* ival,
+                          cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  size_t smem = sizeof(double) * ((size_t)2 * rmax + 4 * nmax);
+  cudaError_t e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_factor<<<n_items, 512, smem, s>>>(items, ival);
+  return cudaGetLastError();
+}
+
+// ===================================================================== core
+// One-sided Jacobi (Hestenes) on the columns of A (m x n, column-major, m >= n),
+// accumulating V (n x n, column-major).  Returns the sweep count; sets
+// *capped when the sweep budget ran out.
+__device__ int jacobi_svd(double* A, int m, int n, double* V, int max_sweeps, int* capped,
+                          double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = (e % (n + 1) == 0) ? 1.0 : 0.0;
+  __syncthreads();
+  if (n < 2) return 0;
+  const int np = (n % 2) ? n + 1 : n;   // players incl. a dummy
+  const double tol = 1e-15 * sqrt((double)m);
+  __shared__ int sh_rot;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) sh_rot = 0;
+    __syncthreads();
+    int rotated = 0;
+    for (int round = 0; round < np - 1; ++round) {
+      for (int pi = wid; pi < np / 2; pi += nw) {
+        int a, b;
+        if (pi == 0) { a = np - 1; b = round; }
+        else { a = (round + pi) % (np - 1); b = (round - pi + np - 1) % (np - 1); }
+        if (a >= n || b >= n) continue;
+        int p = a < b ? a : b, q = a < b ? b : a;
+        double* Ap = A + (long long)p * m;
+        double* Aq = A + (long long)q * m;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < m; i += 32) {
+          double x = Ap[i], y = Aq[i];
+          al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+        }
+        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+        if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
+          rotated = 1;
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          for (int i = lane; i < m; i += 32) {
+            double x = Ap[i], y = Aq[i];
+            Ap[i] = c * x - s * y;
+            Aq[i] = s * x + c * y;
+          }
+          double* Vp = V + (long long)p * n;
+          double* Vq = V + (long long)q * n;
+          for (int i = lane; i < n; i += 32) {
+            double x = Vp[i], y = Vq[i];
+            Vp[i] = c * x - s * y;
+            Vq[i] = s * x + c * y;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (rotated) atomicOr(&sh_rot, 1);
+    __syncthreads();
+    if (sh_rot == 0) break;
+    __syncthreads();
+  }
+  if (sweep >= max_sweeps && threadIdx.x == 0) *capped = 1;
+  (void)red;
+  return sweep;
+}
+
+__global__ void __launch_bounds__(1024)
+k_core(const CoreItem* __restrict__ items, int* ival) {
+  const CoreItem it = items[blockIdx.x];
+  const int chic = ival[it.chi_idx];
+  const int rg = ival[it.rg_idx];
+  const int r = rg * chic;
+  const int n = 4 * chic;
+  const int k1 = ival[it.rank1_idx], k2 = ival[it.rank2_idx];
+  const int rmax = it.rmax;
+  double* R2o = it.work;                          // k2 x r, original column order
+  double* Tc = it.work + (long long)rmax * rmax;  // column-major working matrix
+  double* V = Tc + (long long)rmax * rmax;        // Jacobi right vectors
+  double* Z = V + (long long)rmax * rmax;         // triangular-solve results
+  __shared__ double red[32];
+  __shared__ double sv[2 * 4 * 128 + 8];
+  __shared__ int order[4 * 128];
+  __shared__ int sh_capped;
+  if (threadIdx.x == 0) sh_capped = 0;
+  // R2 in original column order
+  for (long long e = threadIdx.x; e < (long long)k2 * r; e += blockDim.x) {
+    int b = (int)(e / r), q = (int)(e % r);
+    double x = (q >= b) ? it.T2[(long long)b * it.ldt2 + q] : 0.0;
+    R2o[(long long)b * r + it.perm2[q]] = x;
+  }
+  __syncthreads();
+  // Tcore = R1 R2^T (k1 x k2).  Work on the orientation with m >= n columns.
+  const bool tr = k1 < k2;             // if so, decompose Tcore^T
+  const int M = tr ? k2 : k1, N = tr ? k1 : k2;
+  for (long long e = threadIdx.x; e < (long long)k1 * k2; e += blockDim.x) {
+    int a = (int)(e / k2), b = (int)(e % k2);
+    double s = 0.0;
+    const double* t1 = it.T1 + (long long)a * it.ldt1;
+    const double* r2 = R2o + (long long)b * r;
+    for (int q = a; q < r; ++q) s = fma(t1[q], r2[it.perm1[q]], s);
+    // column-major M x N storage of Tcore (or its transpose)
+    if (!tr) Tc[(long long)b * M + a] = s; else Tc[(long long)a * M + b] = s;
+  }
+  __syncthreads();
+  jacobi_svd(Tc, M, N, V, 60, &sh_capped, red);
+  __syncthreads();
+  // singular values (column norms) and descending order
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    double s = 0.0;
+    const double* col = Tc + (long long)j * M;
+    for (int i = 0; i < M; ++i) s = fma(col[i], col[i], s);
+    sv[j] = sqrt(s);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    int rk = 0;
+    for (int i = 0; i < N; ++i) if (sv[i] > sv[j] || (sv[i] == sv[j] && i < j)) ++rk;
+    order[rk] = j;
+  }
+  __syncthreads();
+  const double s0 = sv[order[0]];
+  // truncation, Eq. 9
+  __shared__ int sh_chi;
+  __shared__ double sh_sum, sh_tot;
+  if (threadIdx.x == 0) {
+    int cnt = 0;
+    double tot = 0.0;
+    for (int i = 0; i < N; ++i) {
+      double s = sv[order[i]];
+      tot += s * s;
+      if (s >= it.eps_cut * s0 && s > 0.0) ++cnt;
+    }
+    int chi = cnt < it.chimax ? cnt : it.chimax;
+    if (chi < 1) chi = 1;
+    double kept = 0.0, ksum = 0.0;
+    for (int i = 0; i < chi; ++i) { double s = sv[order[i]]; kept += s * s; ksum += s; }
+    sh_chi = chi;
+    sh_sum = ksum;
+    sh_tot = tot;
+    *it.disc = tot > 0.0 ? (tot - kept) / tot : 0.0;
+    ival[it.new_idx] = chi;
+    *it.nsv = N;
+    if (!(s0 > 0.0) || !isfinite(s0)) atomicOr(it.flags, 2);
+    if (sh_capped) atomicOr(it.flags, 4);
+    const double nrm = sqrt(kept);
+    for (int i = 0; i < it.chimax; ++i) it.lam[i] = (i < chi) ? sv[order[i]] / nrm : 0.0;
+    for (int i = 0; i < N; ++i) it.svals[i] = sv[order[i]];
+    // stored psi = true psi * exp(-sigma); the raw sqrt(S) split gives both
+    // sites half of the pair's combined scale plus the normalisation of W
+    const double ls = 0.5 * log(ksum) + 0.5 * (*it.sigma1 + *it.sigma2);
+    *it.sigma1 = ls;
+    *it.sigma2 = ls;
+  }
+  __syncthreads();
+  const int chi = sh_chi;
+  const double inv = 1.0 / sqrt(sh_sum);
+  // messages diag(lambda)
+  for (int e = threadIdx.x; e < it.chimax * it.chimax; e += blockDim.x) {
+    int i = e / it.chimax, j = e % it.chimax;
+    double x = (i == j && i < chi) ? it.lam[i] : 0.0;
+    it.msg12[e] = x;
+    it.msg21[e] = x;
+  }
+  // For each side: Zs = T_s11^{-1} (singular vectors of that side) sqrt(s) / sqrt(sum s)
+  // side 1 vectors: left vectors of Tcore (rows of R1 space, length k1)
+  // side 2 vectors: right vectors (length k2)
+  for (int side = 0; side < 2; ++side) {
+    const int ks = side == 0 ? k1 : k2;
+    const double* Ts = side == 0 ? it.T1 : it.T2;
+    const int ldts = side == 0 ? it.ldt1 : it.ldt2;
+    const int* perms = side == 0 ? it.perm1 : it.perm2;
+    const double* Fs = side == 0 ? it.FA : it.FB;
+    double* W = side == 0 ? it.W1 : it.W2;
+    // vector of side `side` for singular index c' (c' < chi): length ks
+    // if (!tr): left vectors = columns of Tc / s (length M = k1), right = V (length N = k2)
+    // if (tr):  left vectors = V (length N = k1), right = columns of Tc / s (length M = k2)
+    const bool from_cols = (side == 0) != tr;
+    for (long long e = threadIdx.x; e < (long long)ks * chi; e += blockDim.x) {
+      int a = (int)(e / chi), c = (int)(e % chi);
+      int j = order[c];
+      double s = sv[j];
+      double x = from_cols ? (s > 0.0 ? Tc[(long long)j * M + a] / s : 0.0) : V[(long long)j * N + a];
+      Z[(long long)a * chi + c] = x * sqrt(s) * inv;
+    }
+    __syncthreads();
+    // back substitution with the leading ks x ks upper-triangular block of Ts
+    for (int c = threadIdx.x; c < chi; c += blockDim.x) {
+      for (int a = ks - 1; a >= 0; --a) {
+        double x = Z[(long long)a * chi + c];
+        const double* trow = Ts + (long long)a * ldts;
+        for (int b = a + 1; b < ks; ++b) x -= trow[b] * Z[(long long)b * chi + c];
+        Z[(long long)a * chi + c] = x / trow[a];
+      }
+    }
+    __syncthreads();
+    // Y[(c,kappa), c'] = Z[q, c'] at original column perm[q] (zero for q >= ks)
+    // W[(c,p), (c',p')] = sum_kappa F_kappa[p', p] Y[(c,kappa), c']
+    double* Y = R2o;   // reuse (r x chi)
+    for (long long e = threadIdx.x; e < (long long)r * chi; e += blockDim.x) Y[e] = 0.0;
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)ks * chi; e += blockDim.x) {
+      int q = (int)(e / chi), c = (int)(e % chi);
+      Y[(long long)perms[q] * chi + c] = Z[e];
+    }
+    __syncthreads();
+    const int np = 4 * chi;
+    for (long long e = threadIdx.x; e < (long long)n * np; e += blockDim.x) {
+      int row = (int)(e / np), col = (int)(e % np);
+      int cc = row / 4, p = row % 4, c2 = col / 4, p2 = col % 4;
+      double x = 0.0;
+      for (int kk = 0; kk < rg; ++kk) x += Fs[kk * 16 + p2 * 4 + p] * Y[(long long)(cc * rg + kk) * chi + c2];
+      W[(long long)row * it.ldw + col] = x;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_core(const CoreItem* items, int n_items, int* ival, cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  k_core<<<n_items, 1024, 0, s>>>(items, ival);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_hh_level<float>(const SiteFacItem*, int, int, int, int, void* const*,
+                                            const int*, cudaStream_t);
+template cudaError_t launch_hh_level<double>(const SiteFacItem*, int, int, int, int, void* const*,
+                                             const int*, cudaStream_t);
+template cudaError_t launch_hh_extract<float>(const SiteFacItem*, int, void* const*, int*,
+                                              cudaStream_t);
+template cudaError_t launch_hh_extract<double>(const SiteFacItem*, int, void* const*, int*,
+                                               cudaStream_t);
+
+}  // namespace pepo

@@ -1,0 +1,46 @@
+// Launch wrappers of the libpepo kernels (host-callable, internal API).
+#pragma once
+#include "common.cuh"
+
+namespace pepo {
+
+// ---- k_tensor.cu (storage type T = float or double) ----------------------
+template <typename T>
+cudaError_t launch_leg_contract(const LegItem* items, int n_items, int grid_x, int chimax,
+                                void* const* ptrs, const int* ival, cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy(const TView* items, const int* out_refs, int n_items, int grid_x,
+                        void* const* ptrs, const int* ival, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gram_rows(const GramRowsItem* items, int n_items, int tiles_max, int splits_max,
+                             int sym, void* const* ptrs, const int* ival, cudaStream_t s);
+cudaError_t launch_gram_rows_reduce(const GramRowsItem* items, int n_items, int fmax,
+                                    int splits_max, int sym, const int* ival, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gram_leg(const GramLegItem* items, int n_items, int splits_max,
+                            void* const* ptrs, const int* ival, cudaStream_t s);
+cudaError_t launch_gram_leg_reduce(const GramLegItem* items, int n_items, int chimax,
+                                   int splits_max, const int* ival, cudaStream_t s);
+template <typename T>
+cudaError_t launch_reconstruct(const ReconItem* items, int n_items, int grid_x, int ntile_max,
+                               void* const* ptrs, const int* ival, cudaStream_t s);
+template <typename T>
+cudaError_t launch_vec_contract(const VecItem* items, int n_items, int grid_x,
+                                void* const* ptrs, const int* ival, cudaStream_t s);
+
+// Split count shared by the Gram kernels and their reductions.
+__host__ __device__ inline int gram_rows_splits(long long K, int splits_max) {
+  long long s = (K + 511) / 512;
+  if (s < 1) s = 1;
+  return (int)(s < splits_max ? s : splits_max);
+}
+__host__ __device__ inline long long gram_leg_chunks(long long O, long long Q) {
+  return Q >= 16 ? O * ((Q + 15) / 16) : (O + (16 / Q) - 1) / (16 / Q);
+}
+__host__ __device__ inline int gram_leg_splits(long long chunks, int splits_max) {
+  long long s = (chunks + 31) / 32;
+  if (s < 1) s = 1;
+  return (int)(s < splits_max ? s : splits_max);
+}
+
+}  // namespace pepo

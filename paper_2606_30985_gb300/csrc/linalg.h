@@ -1,0 +1,21 @@
+// Launch wrappers of the FP64 linear-algebra kernels (internal API).
+#pragma once
+#include "common.cuh"
+
+namespace pepo {
+cudaError_t launch_env_factor(const EnvFactorItem* items, int n_items, int chimax, int* ival,
+                              double rel, cudaStream_t s);
+cudaError_t launch_branch(const SiteFacItem* items, int n_items, int* ival, int n_thr,
+                          double ratio_thr, cudaStream_t s);
+template <typename T>
+cudaError_t launch_hh_level(const SiteFacItem* items, int n_items, int level, int grid_x, int nmax,
+                            void* const* ptrs, const int* ival, cudaStream_t s);
+template <typename T>
+cudaError_t launch_hh_extract(const SiteFacItem* items, int n_items, void* const* ptrs, int* ival,
+                              cudaStream_t s);
+cudaError_t launch_form(const SiteFacItem* items, int n_items, int grid_x, const int* ival,
+                        cudaStream_t s);
+cudaError_t launch_factor(const SiteFacItem* items, int n_items, int rmax, int nmax, int* ival,
+                          cudaStream_t s);
+cudaError_t launch_core(const CoreItem* items, int n_items, int* ival, cudaStream_t s);
+}  // namespace pepo

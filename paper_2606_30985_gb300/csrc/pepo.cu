@@ -1,0 +1,1433 @@
+// libpepo host driver: geometry, arena layout, the static launch plan of one
+// Trotter step / BP sweep, and the C ABI of include/pepo.h.
+//
+// Plan.  Everything a step launches is decided at init from the geometry
+// alone (Sec. 2.3 four-colour schedule), because live sizes are read on the
+// device.  Per colour the bonds are cut into waves that fit the scratch slabs;
+// per wave the launch sequence is (Alg. 1 / Fig. 1, Q-less form):
+//   env factors -> absorb (leg contractions) -> Eq. 7 branch ->
+//   [Cholesky-QR: Gram -> reduce] | [Householder: TSQR levels -> extract] ->
+//   gate fold (formG / formB) -> rank-revealing factor -> bond core (SVD,
+//   truncation, lambda, W, messages) -> reconstruct into the next layout ->
+//   commit (pointer swap, chi_new).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bp.h"
+#include "kernels.h"
+#include "linalg.h"
+#include "pepo.h"
+
+using namespace pepo;
+
+namespace {
+
+constexpr int kChiMaxLimit = 128;
+constexpr int kGramSplits = 32;
+constexpr int kLegSplits = 64;
+constexpr size_t kAlign = 256;
+
+enum { LEG_U = 0, LEG_D = 1, LEG_L = 2, LEG_R = 3 };
+
+struct Leg {
+  int name;   // LEG_*
+  int bond;
+  int nbr;
+};
+
+struct SiteG {
+  int deg = 0;
+  Leg legs[4];          // canonical order
+  int pin = 0;          // Pauli index of the pinned single layer
+  std::vector<int> upd; // canonical leg indices of this site's updates, colour order
+};
+
+struct BondG {
+  int v1, v2, leg1, leg2, colour;   // leg1/leg2 canonical leg positions in v1/v2
+};
+
+// ------------------------------------------------------------- bump allocator
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(char* b) : base(b) {}
+  template <class T> T* take(size_t count) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += sizeof(T) * count;
+    return p;
+  }
+};
+
+// host staging of item arrays; device copy made once at init
+struct Staging {
+  std::vector<char> bytes;
+  template <class I> size_t push(const std::vector<I>& v) {
+    size_t o = (bytes.size() + 255) / 256 * 256;
+    bytes.resize(o + sizeof(I) * v.size());
+    if (!v.empty()) std::memcpy(bytes.data() + o, v.data(), sizeof(I) * v.size());
+    return o;
+  }
+};
+
+template <class I> struct DArr {
+  size_t off = 0;
+  int n = 0;
+  const I* d = nullptr;
+};
+
+struct GateWave {
+  DArr<EnvFactorItem> env;
+  DArr<LegItem> leg[3];
+  DArr<TView> copy;
+  DArr<int> copy_out;
+  DArr<SiteFacItem> fac;
+  DArr<GramRowsItem> gram;
+  DArr<CoreItem> core;
+  DArr<ReconItem> recon;
+  DArr<int> pairs;
+  DArr<int> moves;
+  int npairs = 0, nmoves = 0;
+};
+
+struct BpWave {
+  DArr<LegItem> leg[4][3];
+  DArr<GramLegItem> gram[4];
+};
+
+struct SlLevel {
+  DArr<VecItem> items;
+};
+
+struct Inst {
+  pepo_config cfg;
+  int N = 0, nb = 0;
+  std::vector<SiteG> sites;
+  std::vector<BondG> bonds;
+  std::vector<std::vector<int>> colours;
+  // ival indices
+  int chi0 = 0, pend0 = 0, grank0 = 0;
+  int site_ref0 = 0;
+  // device arrays
+  void* slab[1];       // unused
+  std::vector<void*> site_slab;
+  double *lam = nullptr, *msg = nullptr, *hat = nullptr, *vec = nullptr, *vhat = nullptr;
+  double *sigma = nullptr, *disc = nullptr, *svals = nullptr, *vs = nullptr, *fv = nullptr;
+  double *ze = nullptr, *z2e = nullptr, *bethe_out = nullptr, *ptm = nullptr, *FA = nullptr, *FB = nullptr;
+  int* nsv = nullptr;
+  // plan
+  std::vector<GateWave> gwaves[4];
+  std::vector<BpWave> bwaves;
+  std::vector<BpWave> fwaves;   // leg-0-only waves for f_v
+  SlLevel sl[4];                // levels 0..3 (0: copy items for one-leg sites)
+  DArr<MsgItem> msgs;
+  DArr<SiteScalarItem> sscal;
+  DArr<EdgeItem> escal;
+  DArr<BetheItem> bethe;
+  DArr<GateItem> gates;
+  // diagnostics
+  int steps = 0;
+  int last_sweeps = 0, last_sweeps1 = 0;
+  double last_delta = 0, last_delta1 = 0;
+  int cap[5] = {0, 0, 0, 0, 0};   // in-flight sites per degree class
+};
+
+}  // namespace
+
+struct pepo_ctx {
+  std::vector<Inst> inst;
+  int n_inst = 0;
+  int prec = PEPO_FP32;
+  size_t tsize = 4;
+  int chimax = 1;          // max over instances
+  cudaStream_t stream = nullptr;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  void** d_ptrs = nullptr;
+  int* d_ival = nullptr;
+  int n_ptrs = 0, n_ival = 0;
+  unsigned long long* d_delta2 = nullptr;
+  unsigned long long* d_delta1 = nullptr;
+  int* d_flags = nullptr;
+  char* d_items = nullptr;
+  long long launches = 0;
+  std::string err;
+  bool stepped = false;
+  int max_levels = 1;      // TSQR levels
+  int rmax = 4, nmax = 4;
+};
+
+namespace {
+
+const char* kStaticErr = "no context";
+
+pepo_status fail(pepo_ctx* c, pepo_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return st;
+}
+
+std::string validate(const pepo_config& c) {
+  if (c.Lx < 1 || c.Ly < 1 || c.Lx * c.Ly < 2) return "grid must have at least two sites";
+  if (c.Lx * c.Ly > 4096) return "grid too large";
+  if (c.obs_x < 0 || c.obs_x >= c.Lx || c.obs_y < 0 || c.obs_y >= c.Ly) return "observable site off the grid";
+  if (c.obs_pauli < 1 || c.obs_pauli > 3) return "obs_pauli must be 1 (X), 2 (Y) or 3 (Z)";
+  if (c.trotter_order != 1 && c.trotter_order != 2) return "trotter_order must be 1 or 2";
+  if (c.chi_max < 1 || c.chi_max > kChiMaxLimit) return "chi_max must be in [1, 128]";
+  if (!(c.eps_cut >= 0.0)) return "eps_cut must be >= 0";
+  if (!(c.bp_alpha > 0.0 && c.bp_alpha <= 1.0)) return "bp_alpha must be in (0, 1]";
+  if (!(c.bp_tol > 0.0)) return "bp_tol must be > 0";
+  if (c.bp_max_sweeps < 1) return "bp_max_sweeps must be >= 1";
+  if (c.gates != PEPO_GATES_ZZ_X && c.gates != PEPO_GATES_XX_Z) return "unknown gate set";
+  if (c.prec < PEPO_FP64 || c.prec > PEPO_BF16X3) return "unknown precision";
+  if (!std::isfinite(c.J) || !std::isfinite(c.h) || !std::isfinite(c.dt)) return "non-finite couplings";
+  if (c.inflight_sites < 0) return "inflight_sites must be >= 0";
+  return "";
+}
+
+void build_geometry(Inst& I) {
+  const pepo_config& c = I.cfg;
+  const int Lx = c.Lx, Ly = c.Ly;
+  I.N = Lx * Ly;
+  I.sites.assign(I.N, SiteG());
+  I.bonds.clear();
+  I.colours.assign(4, {});
+  // bond ids: horizontal y*(Lx-1)+x, then vertical Ly*(Lx-1) + y*Lx + x
+  for (int y = 0; y < Ly; ++y)
+    for (int x = 0; x + 1 < Lx; ++x) I.bonds.push_back({y * Lx + x, y * Lx + x + 1, 0, 0, x % 2});
+  for (int y = 0; y + 1 < Ly; ++y)
+    for (int x = 0; x < Lx; ++x) I.bonds.push_back({y * Lx + x, (y + 1) * Lx + x, 0, 0, 2 + y % 2});
+  I.nb = (int)I.bonds.size();
+  auto bond_id_h = [&](int x, int y) { return y * (Lx - 1) + x; };
+  auto bond_id_v = [&](int x, int y) { return Ly * (Lx - 1) + y * Lx + x; };
+  for (int y = 0; y < Ly; ++y)
+    for (int x = 0; x < Lx; ++x) {
+      SiteG& s = I.sites[y * Lx + x];
+      s.deg = 0;
+      if (y > 0) s.legs[s.deg++] = {LEG_U, bond_id_v(x, y - 1), (y - 1) * Lx + x};
+      if (y < Ly - 1) s.legs[s.deg++] = {LEG_D, bond_id_v(x, y), (y + 1) * Lx + x};
+      if (x > 0) s.legs[s.deg++] = {LEG_L, bond_id_h(x - 1, y), y * Lx + x - 1};
+      if (x < Lx - 1) s.legs[s.deg++] = {LEG_R, bond_id_h(x, y), y * Lx + x + 1};
+      s.pin = (x == c.obs_x && y == c.obs_y) ? c.obs_pauli : 0;
+    }
+  for (int b = 0; b < I.nb; ++b) {
+    BondG& g = I.bonds[b];
+    for (int k = 0; k < I.sites[g.v1].deg; ++k) if (I.sites[g.v1].legs[k].bond == b) g.leg1 = k;
+    for (int k = 0; k < I.sites[g.v2].deg; ++k) if (I.sites[g.v2].legs[k].bond == b) g.leg2 = k;
+    I.colours[g.colour].push_back(b);
+  }
+  for (int col = 0; col < 4; ++col)
+    for (int b : I.colours[col]) {
+      I.sites[I.bonds[b].v1].upd.push_back(I.bonds[b].leg1);
+      I.sites[I.bonds[b].v2].upd.push_back(I.bonds[b].leg2);
+    }
+}
+
+// layout with canonical leg `cut` innermost: list of canonical leg indices
+std::vector<int> layout_for(const SiteG& s, int cut) {
+  std::vector<int> L;
+  for (int k = 0; k < s.deg; ++k) if (k != cut) L.push_back(k);
+  L.push_back(cut);
+  return L;
+}
+
+size_t pow_sz(size_t b, int e) {
+  size_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// in-flight cap per degree class: all sites if their scratch fits in 40 GB
+void choose_caps(Inst& I, size_t tsize) {
+  int count[5] = {0, 0, 0, 0, 0};
+  for (auto& s : I.sites) count[s.deg]++;
+  const size_t chi = I.cfg.chi_max;
+  for (int d = 1; d <= 4; ++d) {
+    if (count[d] == 0) { I.cap[d] = 0; continue; }
+    size_t slab = 4 * pow_sz(chi, d) * tsize;
+    int cap = count[d];
+    if (I.cfg.inflight_sites > 0) cap = std::min(cap, I.cfg.inflight_sites);
+    else {
+      size_t budget = (size_t)40 << 30;   // scratch budget: keeps 10x10 chi=100 FP32 under 180 GB
+      size_t fit = budget / (2 * slab);
+      if (fit < 1) fit = 1;
+      if ((size_t)cap > fit) cap = (int)fit;
+    }
+    if (cap < 2) cap = std::min(2, count[d]);   // a bond may need two slots of one class
+    I.cap[d] = cap;
+  }
+}
+
+// ----------------------------------------------------------------- planning
+struct Planner {
+  pepo_ctx* c;
+  Carver* cv;        // nullptr base in the sizing pass
+  Staging st;
+  bool dry;
+  std::vector<void*> ptr_init;   // host copy of the pointer table
+  std::vector<int> ival_init;
+  int new_ival(int v) { ival_init.push_back(v); return (int)ival_init.size() - 1; }
+  int new_ptr(void* p) { ptr_init.push_back(p); return (int)ptr_init.size() - 1; }
+};
+
+template <class I> DArr<I> stage(Planner& P, const std::vector<I>& v) {
+  DArr<I> a;
+  a.off = P.st.push(v);
+  a.n = (int)v.size();
+  return a;
+}
+
+struct SlotWS {              // per in-flight site slot (gate update)
+  double* L[3];
+  int rank_idx[3];
+  int branch_idx, kfac_idx, rankT_idx;
+  double* C;
+  double* T;
+  int* perm;
+  double* partial;
+  double* W;
+};
+
+struct ScratchClass {
+  std::vector<int> refs;     // pointer-table refs of scratch slabs (2 per slot)
+};
+
+bool plan_instance(Planner& P, Inst& I, int inst_id) {
+  pepo_ctx* c = P.c;
+  Carver& cv = *P.cv;
+  const int chimax = I.cfg.chi_max;
+  const size_t ts = c->tsize;
+  const int nmax = 4 * chimax;           // columns of cv
+  const int rmax = PEPO_RG * chimax;     // columns of X
+  // ---- state arrays
+  I.site_slab.resize(I.N);
+  I.site_ref0 = (int)P.ptr_init.size();
+  for (int v = 0; v < I.N; ++v) {
+    size_t n = 4 * pow_sz(chimax, I.sites[v].deg);
+    void* p = cv.take<char>(n * ts);
+    I.site_slab[v] = p;
+    P.new_ptr(p);
+  }
+  I.chi0 = (int)P.ival_init.size();
+  for (int b = 0; b < I.nb; ++b) P.new_ival(1);
+  I.pend0 = (int)P.ival_init.size();
+  for (int b = 0; b < I.nb; ++b) P.new_ival(1);
+  I.grank0 = (int)P.ival_init.size();
+  for (int b = 0; b < I.nb; ++b) P.new_ival(1);
+  const size_t cm2 = (size_t)chimax * chimax;
+  I.lam = cv.take<double>(I.nb * (size_t)chimax);
+  I.msg = cv.take<double>(2 * I.nb * cm2);
+  I.hat = cv.take<double>(2 * I.nb * cm2);
+  I.vec = cv.take<double>(2 * I.nb * (size_t)chimax);
+  I.vhat = cv.take<double>(2 * I.nb * (size_t)chimax);
+  I.sigma = cv.take<double>(I.N);
+  I.disc = cv.take<double>(I.nb);
+  I.svals = cv.take<double>(I.nb * (size_t)rmax);
+  I.nsv = cv.take<int>(I.nb);
+  I.vs = cv.take<double>(I.N);
+  I.fv = cv.take<double>(I.N);
+  I.ze = cv.take<double>(I.nb);
+  I.z2e = cv.take<double>(I.nb);
+  I.bethe_out = cv.take<double>(8);
+  I.ptm = cv.take<double>(I.nb * (size_t)256);
+  I.FA = cv.take<double>(I.nb * (size_t)PEPO_RG * 16);
+  I.FB = cv.take<double>(I.nb * (size_t)PEPO_RG * 16);
+
+  auto chi_idx = [&](int b) { return I.chi0 + b; };
+  auto msg_in = [&](int v, int b) {   // message into v on bond b
+    return (I.bonds[b].v2 == v) ? 2 * b : 2 * b + 1;
+  };
+  auto msg_out = [&](int v, int b) { return (I.bonds[b].v1 == v) ? 2 * b : 2 * b + 1; };
+  auto mptr = [&](double* base, int id) { return base + (size_t)id * cm2; };
+
+  // ---- scratch slabs per degree class
+  choose_caps(I, ts);
+  ScratchClass sc[5];
+  int maxslots = 0;
+  for (int d = 1; d <= 4; ++d) {
+    for (int k = 0; k < 2 * I.cap[d]; ++k) {
+      void* p = cv.take<char>(4 * pow_sz(chimax, d) * ts);
+      sc[d].refs.push_back(P.new_ptr(p));
+    }
+    maxslots += I.cap[d];
+  }
+  // ---- per-slot workspaces (gate update and BP)
+  std::vector<SlotWS> slots(maxslots);
+  for (int k = 0; k < maxslots; ++k) {
+    SlotWS& w = slots[k];
+    for (int j = 0; j < 3; ++j) { w.L[j] = cv.take<double>(cm2); w.rank_idx[j] = P.new_ival(1); }
+    w.branch_idx = P.new_ival(0);
+    w.kfac_idx = P.new_ival(0);
+    w.rankT_idx = P.new_ival(0);
+    w.C = cv.take<double>((size_t)nmax * nmax);
+    w.T = cv.take<double>((size_t)4 * nmax * rmax);
+    w.perm = cv.take<int>(rmax);
+    size_t pg = (size_t)kGramSplits * nmax * nmax;
+    size_t pl = (size_t)kLegSplits * cm2;
+    w.partial = cv.take<double>(std::max(pg, pl));
+    w.W = cv.take<double>((size_t)nmax * nmax);
+  }
+  const int nbslots = maxslots;   // a wave never has more bonds than sites
+  std::vector<double*> corework(nbslots);
+  for (int k = 0; k < nbslots; ++k) corework[k] = cv.take<double>((size_t)4 * rmax * rmax);
+
+  // ---- gate tables
+  {
+    std::vector<GateItem> g(I.nb);
+    std::vector<int> first(I.N, -1), last(I.N, -1);
+    for (int col = 0; col < 4; ++col)
+      for (int b : I.colours[col]) {
+        for (int v : {I.bonds[b].v1, I.bonds[b].v2}) {
+          if (first[v] < 0) first[v] = b;
+          last[v] = b;
+        }
+      }
+    const bool second = I.cfg.trotter_order == 2;
+    for (int b = 0; b < I.nb; ++b) {
+      GateItem& it = g[b];
+      it.gateset = I.cfg.gates;
+      it.theta = I.cfg.J * I.cfg.dt;
+      it.phi = second ? 0.5 * I.cfg.h * I.cfg.dt : I.cfg.h * I.cfg.dt;
+      it.pre1 = first[I.bonds[b].v1] == b;
+      it.pre2 = first[I.bonds[b].v2] == b;
+      it.post1 = second && last[I.bonds[b].v1] == b;
+      it.post2 = second && last[I.bonds[b].v2] == b;
+      it.ptm = I.ptm + (size_t)b * 256;
+      it.FA = I.FA + (size_t)b * PEPO_RG * 16;
+      it.FB = I.FB + (size_t)b * PEPO_RG * 16;
+      it.rank = nullptr;   // patched below (needs the ival device base)
+      it.flags = nullptr;
+    }
+    I.gates = stage(P, g);
+  }
+
+  // ---- gate-update waves
+  const double rel_fac = (c->prec == PEPO_FP64) ? 1e-15 : 1e-13;
+  const double rel_env = I.cfg.pinv_rel;
+  for (int col = 0; col < 4; ++col) {
+    const auto& bl = I.colours[col];
+    size_t pos = 0;
+    while (pos < bl.size()) {
+      // greedy wave
+      int used[5] = {0, 0, 0, 0, 0};
+      std::vector<int> wb;
+      while (pos < bl.size()) {
+        int b = bl[pos];
+        int d1 = I.sites[I.bonds[b].v1].deg, d2 = I.sites[I.bonds[b].v2].deg;
+        int need1 = 1 + (d1 == d2 ? 1 : 0);
+        if (used[d1] + need1 > I.cap[d1] || (d1 != d2 && used[d2] + 1 > I.cap[d2])) break;
+        used[d1]++;
+        used[d2]++;
+        wb.push_back(b);
+        ++pos;
+      }
+      if (wb.empty()) return false;   // cannot happen: caps >= 1 per class
+      GateWave gw;
+      std::vector<EnvFactorItem> env;
+      std::vector<LegItem> leg[3];
+      std::vector<TView> cpy;
+      std::vector<int> cpy_out;
+      std::vector<SiteFacItem> fac;
+      std::vector<GramRowsItem> gram;
+      std::vector<CoreItem> core;
+      std::vector<ReconItem> recon;
+      std::vector<int> pairs, moves;
+      int cls_used[5] = {0, 0, 0, 0, 0};
+      int slot_base[5];
+      {
+        int acc = 0;
+        for (int d = 1; d <= 4; ++d) { slot_base[d] = acc; acc += I.cap[d]; }
+      }
+      for (size_t wbi = 0; wbi < wb.size(); ++wbi) {
+        const int b = wb[wbi];
+        const BondG& B = I.bonds[b];
+        int fac_index[2];
+        for (int side = 0; side < 2; ++side) {
+          const int v = side == 0 ? B.v1 : B.v2;
+          const int cutc = side == 0 ? B.leg1 : B.leg2;   // canonical leg index
+          const SiteG& S = I.sites[v];
+          const int d = S.deg;
+          const int k = cls_used[d]++;
+          const int slot = slot_base[d] + k;
+          SlotWS& W = slots[slot];
+          const int sref0 = sc[d].refs[2 * k], sref1 = sc[d].refs[2 * k + 1];
+          // current layout: cut innermost; next layout: next update's leg innermost
+          std::vector<int> lay = layout_for(S, cutc);
+          int ui = 0;
+          for (int q = 0; q < (int)S.upd.size(); ++q) if (S.upd[q] == cutc) ui = q;
+          const int nextc = S.upd[(ui + 1) % S.upd.size()];
+          std::vector<int> nlay = layout_for(S, nextc);
+          const int nenv = d - 1;
+          // env factors
+          for (int j = 0; j < nenv; ++j) {
+            const int bj = S.legs[lay[j]].bond;
+            EnvFactorItem e;
+            e.M = mptr(I.msg, msg_in(v, bj));
+            e.L = W.L[j];
+            e.ld = chimax;
+            e.chi_idx = chi_idx(bj);
+            e.rank_idx = W.rank_idx[j];
+            env.push_back(e);
+          }
+          // absorb chain
+          TView view;
+          view.nlegs = d;
+          for (int j = 0; j < d; ++j) view.dim[j] = chi_idx(S.legs[lay[j]].bond);
+          int cur_ref = I.site_ref0 + v;
+          int cv_ref;
+          if (nenv == 0) {
+            TView t = view;
+            t.ref = cur_ref;
+            cpy.push_back(t);
+            cpy_out.push_back(sref0);
+            cv_ref = sref0;
+          } else {
+            TView t = view;
+            for (int r = 0; r < nenv; ++r) {
+              LegItem li;
+              t.ref = cur_ref;
+              li.in = t;
+              li.out_ref = (r % 2 == 0) ? sref0 : sref1;
+              li.leg = r;
+              li.out_dim = W.rank_idx[r];
+              li.a_rows = W.rank_idx[r];
+              li.A = W.L[r];
+              li.lda = chimax;
+              leg[r].push_back(li);
+              t.dim[r] = W.rank_idx[r];
+              cur_ref = li.out_ref;
+            }
+            cv_ref = cur_ref;
+          }
+          TView cvv = view;
+          cvv.ref = cv_ref;
+          for (int j = 0; j < nenv; ++j) cvv.dim[j] = W.rank_idx[j];
+          SiteFacItem f;
+          f.cv = cvv;
+          f.branch_idx = W.branch_idx;
+          f.kfac_idx = W.kfac_idx;
+          f.rg_idx = I.grank0 + b;
+          f.F = (side == 0 ? I.FA : I.FB) + (size_t)b * PEPO_RG * 16;
+          f.C = W.C;
+          f.ldc = nmax;
+          f.T = W.T;
+          f.ldt = rmax;
+          f.perm = W.perm;
+          f.rank_idx = W.rankT_idx;
+          f.rel = rel_fac;
+          fac_index[side] = (int)fac.size();
+          fac.push_back(f);
+          GramRowsItem g;
+          g.x = cvv;
+          g.y_ref = cv_ref;
+          g.active = W.branch_idx;
+          g.partial = W.partial;
+          g.out = W.C;
+          g.ldo = nmax;
+          gram.push_back(g);
+          // reconstruct: input = site tensor (layout lay), output layout nlay
+          ReconItem rc;
+          rc.in = view;
+          rc.in.ref = I.site_ref0 + v;
+          const int out_ref = (cv_ref == sref0) ? sref1 : sref0;
+          rc.out_ref = out_ref;
+          rc.new_dim = I.pend0 + b;
+          for (int kk = 0; kk < d; ++kk) {
+            int canon = nlay[kk];
+            int pos_in = (int)(std::find(lay.begin(), lay.end(), canon) - lay.begin());
+            rc.out_perm[kk] = pos_in;
+          }
+          rc.W = W.W;
+          rc.ldw = nmax;
+          rc.scale_sq = nullptr;
+          recon.push_back(rc);
+          pairs.push_back(I.site_ref0 + v);
+          pairs.push_back(out_ref);
+        }
+        CoreItem ci;
+        const SiteFacItem& f1 = fac[fac_index[0]];
+        const SiteFacItem& f2 = fac[fac_index[1]];
+        ci.bond = b;
+        ci.chi_idx = chi_idx(b);
+        ci.new_idx = I.pend0 + b;
+        ci.rg_idx = I.grank0 + b;
+        ci.rank1_idx = f1.rank_idx;
+        ci.rank2_idx = f2.rank_idx;
+        ci.T1 = f1.T; ci.T2 = f2.T;
+        ci.ldt1 = f1.ldt; ci.ldt2 = f2.ldt;
+        ci.perm1 = f1.perm; ci.perm2 = f2.perm;
+        ci.FA = I.FA + (size_t)b * PEPO_RG * 16;
+        ci.FB = I.FB + (size_t)b * PEPO_RG * 16;
+        ci.work = corework[wbi];
+        ci.rmax = rmax;
+        ci.W1 = const_cast<double*>(recon[fac_index[0]].W);   // recon items follow fac items
+        ci.W2 = const_cast<double*>(recon[fac_index[1]].W);
+        ci.ldw = nmax;
+        ci.lam = I.lam + (size_t)b * chimax;
+        ci.msg12 = mptr(I.msg, 2 * b);
+        ci.msg21 = mptr(I.msg, 2 * b + 1);
+        ci.chimax = chimax;
+        ci.sigma1 = I.sigma + B.v1;
+        ci.sigma2 = I.sigma + B.v2;
+        ci.disc = I.disc + b;
+        ci.svals = I.svals + (size_t)b * rmax;
+        ci.nsv = I.nsv + b;
+        ci.flags = nullptr;   // patched
+        ci.eps_cut = I.cfg.eps_cut;
+        core.push_back(ci);
+        moves.push_back(chi_idx(b));
+        moves.push_back(I.pend0 + b);
+      }
+      gw.env = stage(P, env);
+      for (int r = 0; r < 3; ++r) gw.leg[r] = stage(P, leg[r]);
+      gw.copy = stage(P, cpy);
+      gw.copy_out = stage(P, cpy_out);
+      gw.fac = stage(P, fac);
+      gw.gram = stage(P, gram);
+      gw.core = stage(P, core);
+      gw.recon = stage(P, recon);
+      gw.pairs = stage(P, pairs);
+      gw.moves = stage(P, moves);
+      gw.npairs = (int)pairs.size() / 2;
+      gw.nmoves = (int)moves.size() / 2;
+      I.gwaves[col].push_back(gw);
+    }
+  }
+  (void)inst_id;
+
+  // ---- BP waves (double layer): sites grouped by class caps
+  auto make_bp_waves = [&](bool leg0_only, std::vector<BpWave>& out) {
+    std::vector<int> order(I.N);
+    for (int v = 0; v < I.N; ++v) order[v] = v;
+    size_t pos = 0;
+    while (pos < order.size()) {
+      int used[5] = {0, 0, 0, 0, 0};
+      std::vector<int> ws;
+      while (pos < order.size()) {
+        int v = order[pos];
+        int d = I.sites[v].deg;
+        if (used[d] + 1 > I.cap[d]) break;
+        used[d]++;
+        ws.push_back(v);
+        ++pos;
+      }
+      BpWave bw;
+      std::vector<LegItem> leg[4][3];
+      std::vector<GramLegItem> gram[4];
+      int cls_used[5] = {0, 0, 0, 0, 0};
+      int slot_base[5];
+      {
+        int acc = 0;
+        for (int d = 1; d <= 4; ++d) { slot_base[d] = acc; acc += I.cap[d]; }
+      }
+      for (int v : ws) {
+        const SiteG& S = I.sites[v];
+        const int d = S.deg;
+        const int k = cls_used[d]++;
+        const int slot = slot_base[d] + k;
+        const int sref0 = sc[d].refs[2 * k], sref1 = sc[d].refs[2 * k + 1];
+        std::vector<int> lay = layout_for(S, S.upd[0]);   // step-boundary layout
+        TView view;
+        view.nlegs = d;
+        view.ref = I.site_ref0 + v;
+        for (int j = 0; j < d; ++j) view.dim[j] = chi_idx(S.legs[lay[j]].bond);
+        const int nw = leg0_only ? 1 : d;
+        for (int w = 0; w < nw; ++w) {
+          int cur = I.site_ref0 + v;
+          int r = 0;
+          for (int j = 0; j < d; ++j) {
+            if (j == w) continue;
+            const int bj = S.legs[lay[j]].bond;
+            LegItem li;
+            li.in = view;
+            li.in.ref = cur;
+            li.out_ref = (r % 2 == 0) ? sref0 : sref1;
+            li.leg = j;
+            li.out_dim = chi_idx(bj);
+            li.a_rows = chi_idx(bj);
+            li.A = mptr(I.msg, msg_in(v, bj));
+            li.lda = chimax;
+            leg[w][r].push_back(li);
+            cur = li.out_ref;
+            ++r;
+          }
+          const int bw_ = S.legs[lay[w]].bond;
+          GramLegItem g;
+          g.x = view;
+          g.x.ref = cur;
+          g.y_ref = I.site_ref0 + v;
+          g.leg = w;
+          g.partial = slots[slot].partial;
+          g.out = mptr(I.hat, msg_out(v, bw_));
+          g.ldo = chimax;
+          gram[w].push_back(g);
+        }
+      }
+      for (int w = 0; w < 4; ++w) {
+        for (int r = 0; r < 3; ++r) bw.leg[w][r] = stage(P, leg[w][r]);
+        bw.gram[w] = stage(P, gram[w]);
+      }
+      out.push_back(bw);
+    }
+  };
+  make_bp_waves(false, I.bwaves);
+  make_bp_waves(true, I.fwaves);
+
+  // ---- single-layer plan: memoised contraction tree per site
+  {
+    std::vector<VecItem> lv[4];
+    for (int v = 0; v < I.N; ++v) {
+      const SiteG& S = I.sites[v];
+      const int d = S.deg;
+      std::vector<int> lay = layout_for(S, S.upd[0]);
+      std::vector<int> dimidx(d);
+      for (int j = 0; j < d; ++j) dimidx[j] = chi_idx(S.legs[lay[j]].bond);
+      if (d == 1) {
+        VecItem it;
+        it.in_ref = I.site_ref0 + v;
+        it.pin = S.pin;
+        it.in_d = nullptr;
+        it.ndims = 1;
+        it.dim[0] = dimidx[0];
+        it.leg = -1;
+        it.v = nullptr;
+        it.out = I.vhat + (size_t)msg_out(v, S.legs[lay[0]].bond) * chimax;
+        lv[0].push_back(it);
+        continue;
+      }
+      // node key: bitmask of contracted layout positions (contracted in
+      // descending position order, skipping the outgoing leg)
+      struct Node { double* buf; std::vector<int> legs; };
+      std::vector<std::pair<int, Node>> memo;
+      auto find = [&](int mask) -> Node* {
+        for (auto& m : memo) if (m.first == mask) return &m.second;
+        return nullptr;
+      };
+      for (int w = 0; w < d; ++w) {
+        int mask = 0;
+        Node cur{nullptr, {}};
+        for (int j = 0; j < d; ++j) cur.legs.push_back(j);
+        bool from_site = true;
+        std::vector<int> seq;
+        for (int j = d - 1; j >= 0; --j) if (j != w) seq.push_back(j);
+        for (size_t si = 0; si < seq.size(); ++si) {
+          const int j = seq[si];
+          const int nmask = mask | (1 << j);
+          Node* hit = find(nmask);
+          if (!hit) {
+            Node nn;
+            for (int l : cur.legs) if (l != j) nn.legs.push_back(l);
+            const bool final_ = (si + 1 == seq.size());
+            if (final_) nn.buf = nullptr;   // written into vhat (not memoised across w)
+            else nn.buf = cv.take<double>(pow_sz(chimax, (int)nn.legs.size()));
+            VecItem it;
+            it.in_ref = from_site ? I.site_ref0 + v : -1;
+            it.pin = S.pin;
+            it.in_d = from_site ? nullptr : cur.buf;
+            it.ndims = (int)cur.legs.size();
+            for (size_t q = 0; q < cur.legs.size(); ++q) it.dim[q] = dimidx[cur.legs[q]];
+            int posj = (int)(std::find(cur.legs.begin(), cur.legs.end(), j) - cur.legs.begin());
+            it.leg = posj;
+            const int bj = S.legs[lay[j]].bond;
+            it.v = I.vec + (size_t)msg_in(v, bj) * chimax;
+            if (final_) it.out = I.vhat + (size_t)msg_out(v, S.legs[lay[w]].bond) * chimax;
+            else it.out = nn.buf;
+            lv[si + 1].push_back(it);
+            if (!final_) { memo.push_back({nmask, nn}); hit = &memo.back().second; }
+            else { cur = nn; mask = nmask; from_site = false; continue; }
+          }
+          cur = *hit;
+          mask = nmask;
+          from_site = false;
+        }
+      }
+    }
+    for (int l = 0; l < 4; ++l) I.sl[l].items = stage(P, lv[l]);
+  }
+
+  // ---- message / scalar / Bethe items
+  {
+    std::vector<MsgItem> mi(2 * I.nb);
+    for (int id = 0; id < 2 * I.nb; ++id) {
+      MsgItem& m = mi[id];
+      m.inst = inst_id;
+      m.chi_idx = chi_idx(id / 2);
+      m.hat = mptr(I.hat, id);
+      m.msg = mptr(I.msg, id);
+      m.vhat = I.vhat + (size_t)id * chimax;
+      m.vec = I.vec + (size_t)id * chimax;
+      m.vinit_from = nullptr;
+    }
+    I.msgs = stage(P, mi);
+    std::vector<SiteScalarItem> ss(I.N);
+    for (int v = 0; v < I.N; ++v) {
+      const SiteG& S = I.sites[v];
+      std::vector<int> lay = layout_for(S, S.upd[0]);
+      const int b0 = S.legs[lay[0]].bond;
+      SiteScalarItem& s = ss[v];
+      s.chi_idx = chi_idx(b0);
+      s.hat = mptr(I.hat, msg_out(v, b0));
+      s.msg_in = mptr(I.msg, msg_in(v, b0));
+      s.vhat = I.vhat + (size_t)msg_out(v, b0) * chimax;
+      s.vec_in = I.vec + (size_t)msg_in(v, b0) * chimax;
+      s.vs = I.vs + v;
+      s.fv = I.fv + v;
+    }
+    I.sscal = stage(P, ss);
+    std::vector<EdgeItem> es(I.nb);
+    for (int b = 0; b < I.nb; ++b) {
+      EdgeItem& e = es[b];
+      e.chi_idx = chi_idx(b);
+      e.m12 = mptr(I.msg, 2 * b);
+      e.m21 = mptr(I.msg, 2 * b + 1);
+      e.v12 = I.vec + (size_t)(2 * b) * chimax;
+      e.v21 = I.vec + (size_t)(2 * b + 1) * chimax;
+      e.ze = I.ze + b;
+      e.z2e = I.z2e + b;
+    }
+    I.escal = stage(P, es);
+    std::vector<BetheItem> bi(1);
+    bi[0].nsites = I.N;
+    bi[0].nbonds = I.nb;
+    bi[0].vs = I.vs;
+    bi[0].fv = I.fv;
+    bi[0].sigma = I.sigma;
+    bi[0].ze = I.ze;
+    bi[0].z2e = I.z2e;
+    bi[0].out = I.bethe_out;
+    I.bethe = stage(P, bi);
+  }
+  (void)rel_env;
+  return true;
+}
+
+template <class I> void resolve(DArr<I>& a, char* dbase) {
+  a.d = reinterpret_cast<const I*>(dbase + a.off);
+}
+
+// patch device pointers that depend on ctx-level arrays, then resolve items
+void finalize_items(pepo_ctx* c, Planner& P) {
+  // patch flags / rank pointers inside staged bytes
+  for (int i = 0; i < c->n_inst; ++i) {
+    Inst& I = c->inst[i];
+    GateItem* g = reinterpret_cast<GateItem*>(P.st.bytes.data() + I.gates.off);
+    for (int b = 0; b < I.gates.n; ++b) {
+      g[b].rank = c->d_ival + I.grank0 + b;
+      g[b].flags = c->d_flags + i;
+    }
+    for (int col = 0; col < 4; ++col)
+      for (auto& w : I.gwaves[col]) {
+        CoreItem* ci = reinterpret_cast<CoreItem*>(P.st.bytes.data() + w.core.off);
+        for (int k = 0; k < w.core.n; ++k) ci[k].flags = c->d_flags + i;
+      }
+  }
+}
+
+void resolve_all(pepo_ctx* c) {
+  char* d = c->d_items;
+  for (auto& I : c->inst) {
+    for (int col = 0; col < 4; ++col)
+      for (auto& w : I.gwaves[col]) {
+        resolve(w.env, d);
+        for (int r = 0; r < 3; ++r) resolve(w.leg[r], d);
+        resolve(w.copy, d); resolve(w.copy_out, d); resolve(w.fac, d); resolve(w.gram, d);
+        resolve(w.core, d); resolve(w.recon, d); resolve(w.pairs, d); resolve(w.moves, d);
+      }
+    for (auto* ws : {&I.bwaves, &I.fwaves})
+      for (auto& w : *ws) {
+        for (int a = 0; a < 4; ++a) {
+          for (int r = 0; r < 3; ++r) resolve(w.leg[a][r], d);
+          resolve(w.gram[a], d);
+        }
+      }
+    for (int l = 0; l < 4; ++l) resolve(I.sl[l].items, d);
+    resolve(I.msgs, d); resolve(I.sscal, d); resolve(I.escal, d); resolve(I.bethe, d);
+    resolve(I.gates, d);
+  }
+}
+
+// full arena layout; base == nullptr computes the size only
+size_t layout_arena(pepo_ctx* c, char* base, Planner* keep) {
+  Carver cv(base);
+  Planner P;
+  P.c = c;
+  P.cv = &cv;
+  P.dry = base == nullptr;
+  for (int i = 0; i < c->n_inst; ++i) {
+    if (!plan_instance(P, c->inst[i], i)) return 0;
+  }
+  c->n_ptrs = (int)P.ptr_init.size();
+  c->n_ival = (int)P.ival_init.size();
+  c->d_ptrs = cv.take<void*>(c->n_ptrs);
+  c->d_ival = cv.take<int>(c->n_ival);
+  c->d_delta2 = cv.take<unsigned long long>(c->n_inst);
+  c->d_delta1 = cv.take<unsigned long long>(c->n_inst);
+  c->d_flags = cv.take<int>(c->n_inst);
+  c->d_items = cv.take<char>(P.st.bytes.size() + 256);
+  size_t total = cv.off + kAlign;
+  if (keep) *keep = std::move(P);
+  return total;
+}
+
+// every launch wrapper returns without launching when its item count is 0;
+// LAUNCH counts the launches that happen (n > 0)
+#define LAUNCH_N(n, expr)                                                               \
+  do {                                                                                  \
+    if ((n) > 0) {                                                                      \
+      cudaError_t _e = (expr);                                                          \
+      c->launches++;                                                                    \
+      if (_e != cudaSuccess)                                                            \
+        return fail(c, PEPO_E_CUDA, "%s: %s", #expr, cudaGetErrorString(_e));           \
+    }                                                                                   \
+  } while (0)
+
+template <typename T>
+pepo_status run_gate_wave(pepo_ctx* c, Inst& I, GateWave& w) {
+  cudaStream_t s = c->stream;
+  const int chimax = I.cfg.chi_max;
+  const int nmax = 4 * chimax, rmax = PEPO_RG * chimax;
+  const long long big = (long long)4 * pow_sz(chimax, 4);
+  int gx_leg = (int)std::min<long long>(std::max<long long>(1, big / (long long)(chimax * 64) + 1),
+                                        (long long)(2 * 152 * 4 / std::max(1, w.leg[0].n) + 1));
+  gx_leg = std::max(gx_leg, 8);
+  LAUNCH_N(w.env.n, launch_env_factor(w.env.d, w.env.n, chimax, c->d_ival, I.cfg.pinv_rel, s));
+  LAUNCH_N(w.copy.n, launch_copy<T>(w.copy.d, w.copy_out.d, w.copy.n, 64, c->d_ptrs, c->d_ival, s));
+  for (int r = 0; r < 3; ++r)
+    LAUNCH_N(w.leg[r].n, launch_leg_contract<T>(w.leg[r].d, w.leg[r].n, gx_leg, chimax, c->d_ptrs, c->d_ival, s));
+  LAUNCH_N(w.fac.n, launch_branch(w.fac.d, w.fac.n, c->d_ival, I.cfg.qr_n_thresh, I.cfg.qr_ratio_thresh, s));
+  {
+    int nt = ceil_div(nmax, 64);
+    LAUNCH_N(w.gram.n, launch_gram_rows<T>(w.gram.d, w.gram.n, nt * (nt + 1) / 2, kGramSplits, 1, c->d_ptrs,
+                               c->d_ival, s));
+    LAUNCH_N(w.gram.n, launch_gram_rows_reduce(w.gram.d, w.gram.n, nmax, kGramSplits, 1, c->d_ival, s));
+  }
+  {
+    const long long mmax = (long long)pow_sz(chimax, 3);
+    const long long L0 = 256;
+    long long nb0 = (mmax + L0 - 1) / L0;
+    int levels = 1;
+    long long nb = nb0;
+    while (nb > 1) { nb = (nb + 3) / 4; ++levels; }
+    long long g = nb0;
+    for (int l = 0; l < levels; ++l) {
+      LAUNCH_N(w.fac.n, launch_hh_level<T>(w.fac.d, w.fac.n, l, (int)std::max<long long>(g, 1), nmax, c->d_ptrs,
+                                c->d_ival, s));
+      g = (g + 3) / 4;
+    }
+    LAUNCH_N(w.fac.n, launch_hh_extract<T>(w.fac.d, w.fac.n, c->d_ptrs, c->d_ival, s));
+  }
+  LAUNCH_N(w.fac.n, launch_form(w.fac.d, w.fac.n, 16, c->d_ival, s));
+  LAUNCH_N(w.fac.n, launch_factor(w.fac.d, w.fac.n, rmax, nmax, c->d_ival, s));
+  LAUNCH_N(w.core.n, launch_core(w.core.d, w.core.n, c->d_ival, s));
+  {
+    long long rows = (long long)pow_sz(chimax, 3);
+    int gx = (int)std::min<long long>(std::max<long long>(1, (rows + 63) / 64 * ceil_div(nmax, 64)),
+                                      (long long)(2 * 152 * 4 / std::max(1, w.recon.n) + 1));
+    gx = std::max(gx, 4);
+    LAUNCH_N(w.recon.n, launch_reconstruct<T>(w.recon.d, w.recon.n, gx, 0, c->d_ptrs, c->d_ival, s));
+  }
+  LAUNCH_N(w.npairs, launch_commit(w.pairs.d, w.npairs, w.moves.d, w.nmoves, c->d_ptrs, c->d_ival, s));
+  return PEPO_OK;
+}
+
+template <typename T>
+pepo_status run_bp_waves(pepo_ctx* c, Inst& I, std::vector<BpWave>& waves) {
+  cudaStream_t s = c->stream;
+  const int chimax = I.cfg.chi_max;
+  const long long big = (long long)4 * pow_sz(chimax, 4);
+  for (auto& w : waves) {
+    for (int a = 0; a < 4; ++a) {
+      if (w.gram[a].n == 0) continue;
+      int gx = (int)std::min<long long>(std::max<long long>(1, big / (long long)(chimax * 64) + 1),
+                                        (long long)(2 * 152 * 4 / std::max(1, w.gram[a].n) + 1));
+      gx = std::max(gx, 8);
+      for (int r = 0; r < 3; ++r)
+        LAUNCH_N(w.leg[a][r].n, launch_leg_contract<T>(w.leg[a][r].d, w.leg[a][r].n, gx, chimax, c->d_ptrs, c->d_ival, s));
+      LAUNCH_N(w.gram[a].n, launch_gram_leg<T>(w.gram[a].d, w.gram[a].n, kLegSplits, c->d_ptrs, c->d_ival, s));
+      LAUNCH_N(w.gram[a].n, launch_gram_leg_reduce(w.gram[a].d, w.gram[a].n, chimax, kLegSplits, c->d_ival, s));
+    }
+  }
+  return PEPO_OK;
+}
+
+template <typename T>
+pepo_status run_sl_pass(pepo_ctx* c, Inst& I) {
+  for (int l = 0; l < 4; ++l) {
+    if (I.sl[l].items.n == 0) continue;
+    LAUNCH_N(I.sl[l].items.n, launch_vec_contract<T>(I.sl[l].items.d, I.sl[l].items.n, 256, c->d_ptrs, c->d_ival, c->stream));
+  }
+  return PEPO_OK;
+}
+
+template <typename T>
+pepo_status do_steps(pepo_ctx* c, int n) {
+  for (int step = 0; step < n; ++step)
+    for (auto& I : c->inst) {
+      for (int col = 0; col < 4; ++col)
+        for (auto& w : I.gwaves[col]) {
+          pepo_status st = run_gate_wave<T>(c, I, w);
+          if (st != PEPO_OK) return st;
+        }
+      I.steps++;
+    }
+  c->stepped = true;
+  return PEPO_OK;
+}
+
+double bits_to_double(unsigned long long u) {
+  double d;
+  std::memcpy(&d, &u, sizeof d);
+  return d;
+}
+
+template <typename T>
+pepo_status do_bp(pepo_ctx* c, int* sweeps_out, double* delta_out) {
+  cudaStream_t s = c->stream;
+  std::vector<int> done(c->n_inst, 0), sweeps(c->n_inst, 0);
+  std::vector<double> delta(c->n_inst, INFINITY);
+  std::vector<unsigned long long> hd(c->n_inst);
+  int maxs = 0;
+  for (auto& I : c->inst) maxs = std::max(maxs, I.cfg.bp_max_sweeps);
+  for (int sw = 1; sw <= maxs; ++sw) {
+    bool any = false;
+    if (cudaMemsetAsync(c->d_delta2, 0, sizeof(unsigned long long) * c->n_inst, s) != cudaSuccess)
+      return fail(c, PEPO_E_CUDA, "memset delta");
+    for (int i = 0; i < c->n_inst; ++i) {
+      Inst& I = c->inst[i];
+      if (done[i] || sw > I.cfg.bp_max_sweeps) continue;
+      any = true;
+      pepo_status st = run_bp_waves<T>(c, I, I.bwaves);
+      if (st != PEPO_OK) return st;
+      LAUNCH_N(I.msgs.n, launch_bp_finish(I.msgs.d, I.msgs.n, c->d_ival, I.cfg.chi_max, I.cfg.bp_alpha,
+                              c->d_delta2, c->d_flags, s));
+    }
+    if (!any) break;
+    if (cudaMemcpyAsync(hd.data(), c->d_delta2, sizeof(unsigned long long) * c->n_inst,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return fail(c, PEPO_E_CUDA, "BP delta readback: %s", cudaGetErrorString(cudaGetLastError()));
+    for (int i = 0; i < c->n_inst; ++i) {
+      Inst& I = c->inst[i];
+      if (done[i] || sw > I.cfg.bp_max_sweeps) continue;
+      sweeps[i] = sw;
+      delta[i] = bits_to_double(hd[i]);
+      if (delta[i] < I.cfg.bp_tol || sw == I.cfg.bp_max_sweeps) done[i] = 1;
+    }
+  }
+  for (int i = 0; i < c->n_inst; ++i) {
+    c->inst[i].last_sweeps = sweeps[i];
+    c->inst[i].last_delta = delta[i];
+    if (sweeps_out) sweeps_out[i] = sweeps[i];
+    if (delta_out) delta_out[i] = delta[i];
+  }
+  return PEPO_OK;
+}
+
+template <typename T>
+pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
+  cudaStream_t s = c->stream;
+  for (auto& I : c->inst) LAUNCH_N(I.msgs.n, launch_sl_init(I.msgs.d, I.msgs.n, c->d_ival, I.cfg.chi_max, s));
+  std::vector<int> done(c->n_inst, 0), sweeps(c->n_inst, 0);
+  std::vector<double> delta(c->n_inst, INFINITY);
+  std::vector<unsigned long long> hd(c->n_inst);
+  int maxs = 0;
+  for (auto& I : c->inst) maxs = std::max(maxs, I.cfg.bp_max_sweeps);
+  for (int sw = 1; sw <= maxs; ++sw) {
+    bool any = false;
+    if (cudaMemsetAsync(c->d_delta1, 0, sizeof(unsigned long long) * c->n_inst, s) != cudaSuccess)
+      return fail(c, PEPO_E_CUDA, "memset delta");
+    for (int i = 0; i < c->n_inst; ++i) {
+      Inst& I = c->inst[i];
+      if (done[i] || sw > I.cfg.bp_max_sweeps) continue;
+      any = true;
+      pepo_status st = run_sl_pass<T>(c, I);
+      if (st != PEPO_OK) return st;
+      LAUNCH_N(I.msgs.n, launch_sl_finish(I.msgs.d, I.msgs.n, c->d_ival, I.cfg.bp_alpha, c->d_delta1, s));
+    }
+    if (!any) break;
+    if (cudaMemcpyAsync(hd.data(), c->d_delta1, sizeof(unsigned long long) * c->n_inst,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return fail(c, PEPO_E_CUDA, "single-layer delta readback");
+    for (int i = 0; i < c->n_inst; ++i) {
+      Inst& I = c->inst[i];
+      if (done[i] || sw > I.cfg.bp_max_sweeps) continue;
+      sweeps[i] = sw;
+      delta[i] = bits_to_double(hd[i]);
+      if (delta[i] < I.cfg.bp_tol || sw == I.cfg.bp_max_sweeps) done[i] = 1;
+    }
+  }
+  // final estimates from the converged messages, then the Bethe sums
+  for (auto& I : c->inst) {
+    pepo_status st = run_sl_pass<T>(c, I);
+    if (st != PEPO_OK) return st;
+    st = run_bp_waves<T>(c, I, I.fwaves);
+    if (st != PEPO_OK) return st;
+    LAUNCH_N(I.sscal.n, launch_site_scalars(I.sscal.d, I.sscal.n, c->d_ival, I.cfg.chi_max, s));
+    LAUNCH_N(I.escal.n, launch_edge_scalars(I.escal.d, I.escal.n, c->d_ival, I.cfg.chi_max, s));
+    LAUNCH_N(1, launch_bethe(I.bethe.d, 1, s));
+  }
+  std::vector<int> flags(c->n_inst);
+  if (cudaMemcpyAsync(flags.data(), c->d_flags, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "flags readback");
+  for (int i = 0; i < c->n_inst; ++i) {
+    Inst& I = c->inst[i];
+    double out[8];
+    std::vector<double> disc(I.nb), lam((size_t)I.nb * I.cfg.chi_max);
+    std::vector<int> chi(I.nb);
+    if (cudaMemcpyAsync(out, I.bethe_out, sizeof(out), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(disc.data(), I.disc, sizeof(double) * I.nb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(lam.data(), I.lam, sizeof(double) * lam.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(chi.data(), c->d_ival + I.chi0, sizeof(int) * I.nb, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return fail(c, PEPO_E_CUDA, "result readback");
+    if (cudaStreamSynchronize(s) != cudaSuccess)
+      return fail(c, PEPO_E_CUDA, "correlator: %s", cudaGetErrorString(cudaGetLastError()));
+    I.last_sweeps1 = sweeps[i];
+    I.last_delta1 = delta[i];
+    if (C_out) C_out[i] = out[0];
+    if (diag_out) {
+      pepo_diag& d = diag_out[i];
+      std::memset(&d, 0, sizeof d);
+      d.C = out[0];
+      d.C_proj = out[1];
+      d.log_norm = out[4];
+      double ge = 0.0;
+      if (I.steps > 0) for (double x : disc) ge += x;
+      d.gate_err = ge;
+      d.bp_sweeps = I.last_sweeps;
+      d.bp_delta = I.last_delta;
+      d.bp1_sweeps = sweeps[i];
+      d.bp1_delta = delta[i];
+      double ef = 0.0;
+      for (int b = 0; b < I.nb; ++b) {
+        if (chi[b] < 2) continue;
+        double S = 0.0;
+        for (int k = 0; k < chi[b]; ++k) {
+          double l2 = lam[(size_t)b * I.cfg.chi_max + k];
+          l2 *= l2;
+          if (l2 > 0.0) S -= l2 * std::log(l2);
+        }
+        ef = std::max(ef, S / std::log((double)chi[b]));
+      }
+      d.entropy_frac_max = ef;
+      d.trap_type1 = (I.last_sweeps >= 30 && I.last_delta < I.cfg.bp_tol) ? 1 : 0;
+      d.trap_type2 = (I.last_sweeps >= I.cfg.bp_max_sweeps && !(I.last_delta < I.cfg.bp_tol)) ? 1 : 0;
+      d.norm_exploded = (out[4] >= std::log(2.0)) ? 1 : 0;
+      d.flags = flags[i];
+      d.steps = I.steps;
+    }
+  }
+  return PEPO_OK;
+}
+
+// canonical position of each layout leg for site v at step boundaries
+std::vector<int> boundary_layout(const SiteG& S) { return layout_for(S, S.upd[0]); }
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+void pepo_config_default(pepo_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->Lx = 3;
+  cfg->Ly = 3;
+  cfg->J = 1.0;
+  cfg->h = 1.0;
+  cfg->dt = 0.05;
+  cfg->trotter_order = 1;
+  cfg->obs_x = 1;
+  cfg->obs_y = 1;
+  cfg->obs_pauli = 3;
+  cfg->chi_max = 8;
+  cfg->eps_cut = 1e-11;
+  cfg->bp_alpha = 0.5;
+  cfg->bp_tol = 1e-5;
+  cfg->bp_max_sweeps = 100;
+  cfg->qr_n_thresh = 150;
+  cfg->qr_ratio_thresh = 150.0;
+  cfg->pinv_rel = 1e-12;
+  cfg->gates = PEPO_GATES_ZZ_X;
+  cfg->prec = PEPO_FP32;
+  cfg->warm_start = 0;
+  cfg->inflight_sites = 0;
+}
+
+static bool setup_ctx(pepo_ctx* c, const pepo_config* cfgs, int n_inst, std::string& why) {
+  c->n_inst = n_inst;
+  c->inst.assign(n_inst, Inst());
+  c->prec = cfgs[0].prec;
+  for (int i = 0; i < n_inst; ++i) {
+    why = validate(cfgs[i]);
+    if (!why.empty()) { why = "instance " + std::to_string(i) + ": " + why; return false; }
+    if (cfgs[i].prec != c->prec) { why = "all instances must share one precision"; return false; }
+    c->inst[i].cfg = cfgs[i];
+    build_geometry(c->inst[i]);
+    c->chimax = std::max(c->chimax, cfgs[i].chi_max);
+  }
+  c->tsize = (c->prec == PEPO_FP64) ? 8 : 4;
+  return true;
+}
+
+size_t pepo_required_bytes(const pepo_config* cfgs, int n_inst) {
+  if (!cfgs || n_inst < 1) return 0;
+  pepo_ctx c;
+  std::string why;
+  if (!setup_ctx(&c, cfgs, n_inst, why)) return 0;
+  return layout_arena(&c, nullptr, nullptr);
+}
+
+pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena, size_t arena_bytes,
+                      void* cuda_stream, pepo_ctx** out) {
+  if (!out) return PEPO_E_INVALID;
+  *out = nullptr;
+  if (!cfgs || n_inst < 1 || !dev_arena) return PEPO_E_INVALID;
+  if (reinterpret_cast<uintptr_t>(dev_arena) % kAlign != 0) return PEPO_E_INVALID;
+  pepo_ctx* c = new pepo_ctx();
+  std::string why;
+  if (!setup_ctx(c, cfgs, n_inst, why)) { delete c; return PEPO_E_INVALID; }
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  size_t need = layout_arena(c, nullptr, nullptr);
+  if (need == 0) { delete c; return PEPO_E_INVALID; }
+  if (arena_bytes < need) { delete c; return PEPO_E_OOM; }
+  // real layout
+  for (auto& I : c->inst) {
+    for (int col = 0; col < 4; ++col) I.gwaves[col].clear();
+    I.bwaves.clear();
+    I.fwaves.clear();
+  }
+  Planner P;
+  c->arena = static_cast<char*>(dev_arena);
+  c->arena_bytes = arena_bytes;
+  layout_arena(c, c->arena, &P);
+  finalize_items(c, P);
+  cudaStream_t s = c->stream;
+  bool ok = cudaMemcpyAsync(c->d_ptrs, P.ptr_init.data(), sizeof(void*) * P.ptr_init.size(),
+                            cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(c->d_ival, P.ival_init.data(), sizeof(int) * P.ival_init.size(),
+                             cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(c->d_items, P.st.bytes.data(), P.st.bytes.size(), cudaMemcpyHostToDevice,
+                             s) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->d_flags, 0, sizeof(int) * n_inst, s) == cudaSuccess;
+  resolve_all(c);
+  // initial state (Sec. 2.3): chi = 1 everywhere, observable Pauli at c, I elsewhere
+  for (auto& I : c->inst) {
+    const int chimax = I.cfg.chi_max;
+    for (int v = 0; v < I.N && ok; ++v) {
+      double e[4] = {0, 0, 0, 0};
+      e[I.sites[v].pin] = 1.0;
+      if (c->tsize == 8) {
+        ok = cudaMemcpyAsync(I.site_slab[v], e, sizeof e, cudaMemcpyHostToDevice, s) == cudaSuccess;
+      } else {
+        float f[4] = {(float)e[0], (float)e[1], (float)e[2], (float)e[3]};
+        ok = cudaMemcpyAsync(I.site_slab[v], f, sizeof f, cudaMemcpyHostToDevice, s) == cudaSuccess;
+      }
+    }
+    std::vector<double> lam((size_t)I.nb * chimax, 0.0), msg((size_t)2 * I.nb * chimax * chimax, 0.0);
+    for (int b = 0; b < I.nb; ++b) lam[(size_t)b * chimax] = 1.0;
+    for (int id = 0; id < 2 * I.nb; ++id) msg[(size_t)id * chimax * chimax] = 1.0;
+    ok = ok && cudaMemcpyAsync(I.lam, lam.data(), sizeof(double) * lam.size(), cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(I.msg, msg.data(), sizeof(double) * msg.size(), cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(I.sigma, 0, sizeof(double) * I.N, s) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(I.disc, 0, sizeof(double) * I.nb, s) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(I.vec, 0, sizeof(double) * 2 * I.nb * chimax, s) == cudaSuccess;
+    if (ok && launch_gates(I.gates.d, I.gates.n, s) != cudaSuccess) ok = false;
+    c->launches++;
+  }
+  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    delete c;
+    return PEPO_E_CUDA;
+  }
+  int flags = 0;
+  cudaMemcpy(&flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost);
+  if (flags & 8) { delete c; return PEPO_E_INVALID; }   // gate rank above the bound
+  *out = c;
+  return PEPO_OK;
+}
+
+pepo_status pepo_trotter_step(pepo_ctx* c, int n_steps) {
+  if (!c) return PEPO_E_INVALID;
+  if (n_steps < 0) return fail(c, PEPO_E_INVALID, "n_steps must be >= 0");
+  return c->tsize == 8 ? do_steps<double>(c, n_steps) : do_steps<float>(c, n_steps);
+}
+
+pepo_status pepo_bp_converge(pepo_ctx* c, int* sweeps_out, double* delta_out) {
+  if (!c) return PEPO_E_INVALID;
+  return c->tsize == 8 ? do_bp<double>(c, sweeps_out, delta_out) : do_bp<float>(c, sweeps_out, delta_out);
+}
+
+pepo_status pepo_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
+  if (!c) return PEPO_E_INVALID;
+  return c->tsize == 8 ? do_correlator<double>(c, C_out, diag_out) : do_correlator<float>(c, C_out, diag_out);
+}
+
+pepo_status pepo_get_spectrum(pepo_ctx* c, int inst, int bond, double* lam_out, int* chi_out) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
+  Inst& I = c->inst[inst];
+  if (bond < 0 || bond >= I.nb || !lam_out || !chi_out) return fail(c, PEPO_E_INVALID, "bad bond");
+  if (cudaMemcpyAsync(lam_out, I.lam + (size_t)bond * I.cfg.chi_max, sizeof(double) * I.cfg.chi_max,
+                      cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(chi_out, c->d_ival + I.chi0 + bond, sizeof(int), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "spectrum readback");
+  return PEPO_OK;
+}
+
+// layout <-> canonical conversion helpers (host side, not on the hot path)
+static void layout_strides(const std::vector<int>& dims_layout, std::vector<size_t>& st) {
+  st.assign(dims_layout.size(), 0);
+  size_t s = 4;
+  for (int k = (int)dims_layout.size() - 1; k >= 0; --k) { st[k] = s; s *= dims_layout[k]; }
+}
+
+pepo_status pepo_get_site(pepo_ctx* c, int inst, int site, double* out, size_t count, int* dims_out) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
+  Inst& I = c->inst[inst];
+  if (site < 0 || site >= I.N || !out || !dims_out) return fail(c, PEPO_E_INVALID, "bad site");
+  std::vector<int> chi(I.nb);
+  void* ptr = nullptr;
+  double sigma = 0.0;
+  if (cudaMemcpyAsync(chi.data(), c->d_ival + I.chi0, sizeof(int) * I.nb, cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&ptr, c->d_ptrs + I.site_ref0 + site, sizeof(void*), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&sigma, I.sigma + site, sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "site readback");
+  const SiteG& S = I.sites[site];
+  std::vector<int> lay = boundary_layout(S);
+  std::vector<int> dl(S.deg), dc(S.deg);
+  size_t n = 4;
+  for (int k = 0; k < S.deg; ++k) { dl[k] = chi[S.legs[lay[k]].bond]; dc[k] = chi[S.legs[k].bond]; n *= dc[k]; }
+  for (int k = 0; k < 4; ++k) dims_out[k] = 0;
+  for (int k = 0; k < S.deg; ++k) dims_out[S.legs[k].name] = dc[k];
+  if (count < n) return fail(c, PEPO_E_INVALID, "output too small (%zu < %zu)", count, n);
+  std::vector<double> raw(n);
+  if (c->tsize == 8) {
+    if (cudaMemcpy(raw.data(), ptr, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(c, PEPO_E_CUDA, "site copy");
+  } else {
+    std::vector<float> f(n);
+    if (cudaMemcpy(f.data(), ptr, sizeof(float) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(c, PEPO_E_CUDA, "site copy");
+    for (size_t i = 0; i < n; ++i) raw[i] = f[i];
+  }
+  std::vector<size_t> sl;
+  layout_strides(dl, sl);
+  const double scale = std::exp(sigma);
+  // canonical index iteration
+  std::vector<int> idx(S.deg, 0);
+  for (size_t e = 0; e < n / 4; ++e) {
+    size_t rem = e;
+    for (int k = S.deg - 1; k >= 0; --k) { idx[k] = (int)(rem % dc[k]); rem /= dc[k]; }
+    size_t src = 0;
+    for (int k = 0; k < S.deg; ++k) {
+      int canon = lay[k];
+      src += (size_t)idx[canon] * sl[k];
+    }
+    for (int p = 0; p < 4; ++p) out[e * 4 + p] = raw[src + p] * scale;
+  }
+  return PEPO_OK;
+}
+
+pepo_status pepo_set_state(pepo_ctx* c, int inst, const double* sites, size_t count, const int* chi,
+                           const double* lam, const double* msgs) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
+  Inst& I = c->inst[inst];
+  if (!sites || !chi || !lam || !msgs) return fail(c, PEPO_E_INVALID, "null argument");
+  const int chimax = I.cfg.chi_max;
+  for (int b = 0; b < I.nb; ++b)
+    if (chi[b] < 1 || chi[b] > chimax) return fail(c, PEPO_E_INVALID, "chi of bond %d out of range", b);
+  // site pointers (the table may have been permuted by earlier steps)
+  std::vector<void*> ptrs(I.N);
+  if (cudaMemcpy(ptrs.data(), c->d_ptrs + I.site_ref0, sizeof(void*) * I.N, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "pointer readback");
+  size_t off = 0;
+  for (int v = 0; v < I.N; ++v) {
+    const SiteG& S = I.sites[v];
+    std::vector<int> lay = boundary_layout(S);
+    std::vector<int> dl(S.deg), dc(S.deg);
+    size_t n = 4;
+    for (int k = 0; k < S.deg; ++k) { dl[k] = chi[S.legs[lay[k]].bond]; dc[k] = chi[S.legs[k].bond]; n *= dc[k]; }
+    if (off + n > count) return fail(c, PEPO_E_INVALID, "site data too short");
+    std::vector<size_t> sl;
+    layout_strides(dl, sl);
+    std::vector<double> buf(n);
+    std::vector<int> idx(S.deg, 0);
+    for (size_t e = 0; e < n / 4; ++e) {
+      size_t rem = e;
+      for (int k = S.deg - 1; k >= 0; --k) { idx[k] = (int)(rem % dc[k]); rem /= dc[k]; }
+      size_t dst = 0;
+      for (int k = 0; k < S.deg; ++k) dst += (size_t)idx[lay[k]] * sl[k];
+      for (int p = 0; p < 4; ++p) buf[dst + p] = sites[off + e * 4 + p];
+    }
+    off += n;
+    cudaError_t e;
+    if (c->tsize == 8) e = cudaMemcpy(ptrs[v], buf.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+    else {
+      std::vector<float> f(buf.begin(), buf.end());
+      e = cudaMemcpy(ptrs[v], f.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return fail(c, PEPO_E_CUDA, "site upload");
+  }
+  std::vector<int> chiv(chi, chi + I.nb);
+  if (cudaMemcpy(c->d_ival + I.chi0, chiv.data(), sizeof(int) * I.nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_ival + I.pend0, chiv.data(), sizeof(int) * I.nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(I.lam, lam, sizeof(double) * I.nb * chimax, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(I.msg, msgs, sizeof(double) * 2 * I.nb * chimax * chimax, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(I.sigma, 0, sizeof(double) * I.N) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "state upload");
+  return PEPO_OK;
+}
+
+pepo_status pepo_get_message(pepo_ctx* c, int inst, int bond, int dir, double* out, int* chi_out) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
+  Inst& I = c->inst[inst];
+  if (bond < 0 || bond >= I.nb || (dir != 0 && dir != 1) || !out || !chi_out)
+    return fail(c, PEPO_E_INVALID, "bad message");
+  const int chimax = I.cfg.chi_max;
+  std::vector<double> m((size_t)chimax * chimax);
+  int chi = 0;
+  if (cudaMemcpyAsync(m.data(), I.msg + (size_t)(2 * bond + dir) * chimax * chimax,
+                      sizeof(double) * m.size(), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&chi, c->d_ival + I.chi0 + bond, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "message readback");
+  for (int i = 0; i < chi; ++i)
+    for (int j = 0; j < chi; ++j) out[i * chi + j] = m[(size_t)i * chimax + j];
+  *chi_out = chi;
+  return PEPO_OK;
+}
+
+int pepo_num_bonds(const pepo_ctx* c, int inst) {
+  if (!c || inst < 0 || inst >= c->n_inst) return 0;
+  return c->inst[inst].nb;
+}
+
+long long pepo_launch_count(const pepo_ctx* c) { return c ? c->launches : 0; }
+
+const char* pepo_last_error(const pepo_ctx* c) { return c ? c->err.c_str() : kStaticErr; }
+
+void pepo_destroy(pepo_ctx* c) { delete c; }
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads, exports every
+entry point that include/pepo.h declares, and its host-side sizing logic
+accepts / rejects configurations (no compute call needs a GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2606_30985_gb300 as pkg
+from paper_2606_30985_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return pkg.load_library()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "pepo.h")).read()
+    return sorted(set(re.findall(r"\b(pepo_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_method_entry_points():
+    names = declared_symbols()
+    for required in ("pepo_init", "pepo_trotter_step", "pepo_bp_converge", "pepo_correlator"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    assert sorted(declared_symbols()) == sorted(pkg.EXPORTS)
+
+
+def test_config_default_matches_paper_defaults(lib):
+    c = pkg._Config()
+    lib.pepo_config_default(ctypes.byref(c))
+    assert c.eps_cut == 1e-11 and c.bp_tol == 1e-5 and c.bp_max_sweeps == 100
+    assert c.qr_n_thresh == 150 and c.qr_ratio_thresh == 150.0
+    assert c.gates == 0 and c.trotter_order == 1
+
+
+def test_required_bytes_valid_and_invalid(lib):
+    small = pkg.required_bytes(pkg.Config(Lx=3, Ly=3, chi_max=8, precision="fp64"))
+    assert small > 0
+    # larger chi and FP64 storage need more memory
+    assert pkg.required_bytes(pkg.Config(Lx=3, Ly=3, chi_max=16, precision="fp64")) > small
+    assert pkg.required_bytes(pkg.Config(Lx=1, Ly=1)) == 0           # one site
+    assert pkg.required_bytes(pkg.Config(Lx=3, Ly=3, chi_max=200)) == 0  # beyond the kernel bound
+    assert pkg.required_bytes(pkg.Config(Lx=3, Ly=3, obs=(5, 0))) == 0
+    assert pkg.required_bytes(pkg.Config(Lx=3, Ly=3, order=3)) == 0
+    # mixed precisions in one context are rejected
+    assert pkg.required_bytes([pkg.Config(precision="fp32"), pkg.Config(precision="fp64")]) == 0
+
+
+def test_required_bytes_follow_the_memory_model(lib):
+    # Eq. 17: the site tensors alone are (4 chi^2 + 2 (k+l-4) chi^3 + (k-2)(l-2) chi^4) * 4 * 4 B
+    k = l = 10
+    chi = 100
+    m_psi = (4 * chi ** 2 + 2 * (k + l - 4) * chi ** 3 + (k - 2) * (l - 2) * chi ** 4) * 4 * 4
+    need = pkg.required_bytes(pkg.Config(Lx=k, Ly=l, chi_max=chi))
+    assert m_psi < need < 180e9
