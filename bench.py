@@ -1,0 +1,347 @@
+"""Benchmark: Trotter steps/s of the PEPO method at 10x10, chi_max = 100.
+
+One step = one pass of the whole hot path on every instance: the Trotter
+layer (all bond updates of the four colours), double-layer BP to tolerance,
+single-layer BP and the Bethe correlator.  The workload is the 10x10
+(J = 1, h = 2, dt = 0.05, Strang split, Z at (3, 4)) lattice with every bond at
+chi_max = 100, started from a seeded synthetic saturated state (FP32 storage).
+
+Output: one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead (see cpu_baseline below).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(Lx=10, Ly=10, J=1.0, h=2.0, dt=0.05, order=2, obs=(3, 4), chi_max=100,
+                bp_alpha=0.5, bp_tol=1e-5, bp_max_sweeps=100, precision="fp32")
+SEED = 0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pepo", choices=["pepo", "reference"])
+    ap.add_argument("--chi", type=int, default=None, help="override chi_max (smaller test runs)")
+    ap.add_argument("--grid", type=int, default=None, help="override the grid side")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args):
+    w = dict(WORKLOAD)
+    if args.chi:
+        w["chi_max"] = args.chi
+    if args.grid:
+        w["Lx"] = w["Ly"] = args.grid
+        w["obs"] = (min(3, args.grid - 1), min(4, args.grid - 1))
+    return w
+
+
+def workload_name(w):
+    return "%dx%d TFIM chi_max=%d saturated Trotter step (gates + BP + Bethe C(t))" % (
+        w["Lx"], w["Ly"], w["chi_max"])
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    def __init__(self, index, path):
+        self.path = path
+        self.proc = None
+        try:
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# --------------------------------------------------------------- CPU oracle
+def oracle_message_sample(w, seed=SEED):
+    """Time one interior double-layer BP message (the dominant unit of the
+    step) with the oracle, on the workload's synthetic state at full chi."""
+    from oracle import bp as obp
+    from oracle import gates as og
+    from oracle.pepo import Network
+    from workloads.synthetic import saturated_state, site_legs
+
+    Lx, Ly, chi = w["Lx"], w["Ly"], w["chi_max"]
+    x, y = min(3, Lx - 2), min(4, Ly - 2)
+    v = y * Lx + x
+    rng_state = saturated_state_one_site(Lx, Ly, chi, seed, v)
+    net = Network.__new__(Network)
+    net.N = Lx * Ly
+    legs = site_legs(Lx, Ly, v)
+    names = ["U", "D", "L", "R"]
+    net.legs = [[] for _ in range(net.N)]
+    net.legs[v] = [(names[i], nb) for i, (nb, _) in enumerate(legs)]
+    psi = rng_state["psi"]
+    paulis = np.stack(og.PAULI_BY_INDEX)                       # [p, s, s']
+    net.O = [None] * net.N
+    net.O[v] = np.tensordot(psi, paulis, axes=([psi.ndim - 1], [0]))  # Pauli -> 2x2 pair
+    M = {}
+    for (nb, b) in legs:
+        M[(nb, v)] = np.diag(rng_state["lam"]).astype(np.complex128)
+    t0 = time.perf_counter()
+    obp.double_message(net, v, 0, M)
+    return time.perf_counter() - t0
+
+
+def saturated_state_one_site(Lx, Ly, chi, seed, v):
+    from workloads.synthetic import saturated_state
+    st = saturated_state(Lx, Ly, 1, seed=seed)   # cheap call only to mirror the recipe
+    del st
+    rng = np.random.default_rng(seed + 1000 + v)
+    lam = np.exp(-0.06 * np.arange(chi))
+    lam /= np.linalg.norm(lam)
+    shape = (chi,) * 4 + (4,)
+    psi = rng.standard_normal(shape)
+    sq = np.sqrt(lam)
+    for k in range(4):
+        sh = [1] * 5
+        sh[k] = chi
+        psi *= sq.reshape(sh)
+    return {"psi": psi, "lam": lam}
+
+
+def extrapolate_step(t_msg, w, sweeps):
+    """Oracle step time from one interior message: per sweep, 4 messages per
+    interior site (edge / corner messages are 1/chi, 1/chi^2 as large); a site
+    update of the bond layer costs about 3.5 interior messages (absorb, QR,
+    Q M, deabsorb at the same sizes); the correlator adds one message per site."""
+    Lx, Ly = w["Lx"], w["Ly"]
+    n_int = max(0, (Lx - 2) * (Ly - 2))
+    per_sweep = 4 * n_int
+    bond_layer = 4 * n_int * 3.5
+    return t_msg * (per_sweep * max(1, sweeps) + bond_layer + n_int)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local):
+    import torch
+    import paper_2606_30985_gb300 as pkg
+    from workloads.synthetic import saturated_state
+
+    torch.cuda.set_device(local)
+    w = workload(args)
+    cfg = pkg.Config(**{k: v for k, v in w.items()})
+    eng = pkg.Engine(cfg, device="cuda:%d" % local)
+    st = saturated_state(w["Lx"], w["Ly"], w["chi_max"], seed=SEED + rank, dtype=np.float32)
+    t_up = time.perf_counter()
+    eng.set_state(0, st["sites"], st["chi"], st["lam"], st["msgs"])
+    torch.cuda.synchronize()
+    upload_s = time.perf_counter() - t_up
+    state_bytes = sum(s.size for s in st["sites"]) * 4
+    del st
+
+    def one_step():
+        eng.trotter_step(1)
+        sw, de = eng.bp_converge()
+        C, D = eng.correlator()
+        return sw[0], D[0]
+
+    for _ in range(args.warmup):
+        one_step()
+    dist = world > 1 and torch.distributed.is_initialized()
+    stream = torch.cuda.current_stream()
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % rank)
+                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks.csv")
+    eng.reset_timing()
+    eng.set_timing(True)
+    l0 = eng.launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sweeps, diags = [], []
+    h0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        s, d = one_step()
+        sweeps.append(s)
+        diags.append(d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - h0
+    if dist:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    eng.set_timing(False)
+    launches = eng.launches() - l0
+    ms = e0.elapsed_time(e1)
+    timing = eng.timing()
+    # max over ranks
+    if dist:
+        t = torch.tensor([ms, wall], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, wall = float(t[0]), float(t[1])
+    steps_total = args.steps * world
+    value = steps_total / (ms / 1e3)
+    hbm, bf16, src = peaks()
+    top = max(timing.items(), key=lambda kv: kv[1]["ms"])
+    name, tk = top
+    avg_ms = tk["ms"] / max(1, tk["launches"])
+    if tk["flops"] > 0 and tk["bytes"] / tk["flops"] < 1.0 / 283 and False:
+        bound = "tensor"
+    bound = "hbm"
+    achieved = (tk["bytes"] / max(1, tk["launches"])) / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    bond_classes = ["leg_contract", "gram_rows", "gram_rows_reduce", "reconstruct", "householder_tsqr",
+                    "factor", "core_svd", "env_factor"]
+    # bond-update FLOPs: algorithmic FLOPs of the bond-update kernels over their time
+    bu_ms = sum(timing[k]["ms"] for k in bond_classes if k in timing)
+    out = {
+        "metric": "Trotter steps/s at 10x10 chi=100 (gates + BP + Bethe C(t))",
+        "value": value,
+        "unit": "steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded saturated state, every bond at chi_max)",
+        "config": {"workload": workload_name(w), "grid": "%dx%d" % (w["Lx"], w["Ly"]),
+                   "chi_max": w["chi_max"], "J": w["J"], "h": w["h"], "dt": w["dt"],
+                   "trotter_order": w["order"], "obs": list(w["obs"]), "bp_alpha": w["bp_alpha"],
+                   "bp_tol": w["bp_tol"], "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (%.1f GB of site tensors)" % (state_bytes / 1e9),
+                   "bp_sweeps": sweeps},
+        "roofline": {"bound": bound, "kernel": name, "achieved": achieved, "peak": hbm,
+                     "peak_source": src, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "avg_launch_ms": avg_ms,
+                     "algorithmic_bytes_per_launch": tk["bytes"] / max(1, tk["launches"])},
+        "bond_update_tflops": (sum(timing[k]["flops"] for k in bond_classes if k in timing) / 1e12
+                               / (bu_ms / 1e3)) if bu_ms > 0 else None,
+        "kernel_ms": {k: round(v["ms"], 3) for k, v in timing.items() if v["launches"]},
+        "clocks": clk,
+        "e2e": {"value": steps_total / wall, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 8 * 14 + 8, "state_upload_s": upload_s},
+        "gpu_launches": launches,
+        "C_last": diags[-1]["C"],
+    }
+    eng.close()
+    return out
+
+
+def cpu_baseline(w, sweeps):
+    t = oracle_message_sample(w)
+    step = extrapolate_step(t, w, sweeps)
+    return {"value": 1.0 / step, "unit": "steps/s", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle",
+            "sample": "one interior double-layer BP message at chi=%d (%.1f s), extrapolated to a "
+                      "full step with %d sweeps" % (w["chi_max"], t, max(1, sweeps))}
+
+
+def run_reference(args, rank, world):
+    w = workload(args)
+    sweeps = 10
+    for _ in range(args.warmup):
+        oracle_message_sample(w)
+    ts = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ts.append(oracle_message_sample(w))
+    wall = time.perf_counter() - t0
+    step = extrapolate_step(float(np.mean(ts)), w, sweeps)
+    value = 1.0 / step
+    return {"impl": "reference", "metric": "Trotter steps/s at 10x10 chi=100 (gates + BP + Bethe C(t))",
+            "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": workload_name(w)},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": len(os.sched_getaffinity(0)),
+                             "kind": "oracle",
+                             "sample": "per step: one interior double-layer BP message at chi=%d "
+                                       "(oracle, complex128), extrapolated to a full step with %d "
+                                       "BP sweeps; sample wall %.1f s" % (w["chi_max"], sweeps, wall)},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_gpu(args, rank, world, local)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            try:
+                sw = int(np.median(out["config"]["bp_sweeps"]))
+                out["cpu_baseline"] = cpu_baseline(workload(args), sw)
+            except Exception as e:   # the baseline is reported, never required
+                out["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

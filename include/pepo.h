@@ -175,6 +175,20 @@ pepo_status pepo_get_message(pepo_ctx* ctx, int inst, int bond, int dir, double*
 /* Number of bonds of instance inst (0 on a bad argument). */
 int pepo_num_bonds(const pepo_ctx* ctx, int inst);
 
+/* Kernel-class timing (off by default).  When enabled, every launch is
+ * bracketed by CUDA events on the context's stream and credited with its
+ * algorithmic bytes and FLOPs, computed from the live bond dimensions read at
+ * the start of each call (exact whenever chi does not change inside the call,
+ * e.g. in the saturated regime).  Classes are numbered 0 .. pepo_timing_classes()-1. */
+pepo_status pepo_set_timing(pepo_ctx* ctx, int enable);
+int pepo_timing_classes(void);
+const char* pepo_timing_class_name(int kclass);
+/* Totals since the last reset: launches, milliseconds, algorithmic bytes and
+ * FLOPs of one class.  Synchronises the stream. */
+pepo_status pepo_get_timing(pepo_ctx* ctx, int kclass, long long* launches, double* ms,
+                            double* bytes, double* flops);
+pepo_status pepo_reset_timing(pepo_ctx* ctx);
+
 /* Number of kernel launches enqueued by this context so far. */
 long long pepo_launch_count(const pepo_ctx* ctx);
 

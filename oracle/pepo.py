@@ -102,6 +102,41 @@ class Network:
         return n
 
 
+def from_pauli(Lx, Ly, obs_xy, obs_pauli, sites, chi, msgs, sites_subset=None):
+    """Network from Pauli-basis arrays (canonical [U, D, L, R, p] layout).
+
+    O_v = sum_p psi_v[..., p] P_p (Sec. 2.3: psi holds Pauli coefficients).
+    chi / msgs are indexed by the library's bond numbering (horizontal bonds
+    first); msgs[b, 0] is the message first site -> second site.  With
+    sites_subset only those site tensors are converted (others left None).
+    """
+    net = Network(Lx, Ly, obs_xy, obs_pauli)
+    P = np.stack(G.PAULI_BY_INDEX)
+    bid = {}
+    for y in range(Ly):
+        for x in range(Lx - 1):
+            bid[(y * Lx + x, y * Lx + x + 1)] = y * (Lx - 1) + x
+    for y in range(Ly - 1):
+        for x in range(Lx):
+            bid[(y * Lx + x, (y + 1) * Lx + x)] = Ly * (Lx - 1) + y * Lx + x
+    for v in range(net.N):
+        if sites_subset is not None and v not in sites_subset:
+            net.O[v] = None
+            continue
+        psi = np.asarray(sites[v], dtype=np.float64)
+        net.O[v] = np.tensordot(psi, P, axes=([psi.ndim - 1], [0])).astype(np.complex128)
+    for (a, b), k in bid.items():
+        c = int(chi[k])
+        net.M[(a, b)] = np.asarray(msgs[k][0][:c, :c], dtype=np.complex128)
+        net.M[(b, a)] = np.asarray(msgs[k][1][:c, :c], dtype=np.complex128)
+    return net
+
+
+def apply_site_gate(net, v, g):
+    """O_v -> g^dagger O_v g on one site."""
+    net.O[v] = np.einsum("ab,...bc,cd->...ad", g.conj().T, net.O[v], g)
+
+
 def apply_site_gates(net, g):
     """O_v -> g^dagger O_v g on every site (Fig. 1, apply_unary_gate)."""
     gd = g.conj().T

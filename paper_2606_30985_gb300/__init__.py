@@ -51,8 +51,9 @@ class _Diag(ctypes.Structure):
 
 EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trotter_step",
            "pepo_bp_converge", "pepo_correlator", "pepo_get_spectrum", "pepo_get_site",
-           "pepo_set_state", "pepo_get_message", "pepo_num_bonds", "pepo_launch_count",
-           "pepo_last_error", "pepo_destroy"]
+           "pepo_set_state", "pepo_get_message", "pepo_num_bonds", "pepo_set_timing",
+           "pepo_timing_classes", "pepo_timing_class_name", "pepo_get_timing", "pepo_reset_timing",
+           "pepo_launch_count", "pepo_last_error", "pepo_destroy"]
 
 _lib = None
 
@@ -90,6 +91,17 @@ def load_library(path=LIB_PATH):
     lib.pepo_get_message.restype = I
     lib.pepo_num_bonds.argtypes = [P, I]
     lib.pepo_num_bonds.restype = I
+    lib.pepo_set_timing.argtypes = [P, I]
+    lib.pepo_set_timing.restype = I
+    lib.pepo_timing_classes.argtypes = []
+    lib.pepo_timing_classes.restype = I
+    lib.pepo_timing_class_name.argtypes = [I]
+    lib.pepo_timing_class_name.restype = ctypes.c_char_p
+    lib.pepo_get_timing.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
+                                    ctypes.POINTER(D), ctypes.POINTER(D)]
+    lib.pepo_get_timing.restype = I
+    lib.pepo_reset_timing.argtypes = [P]
+    lib.pepo_reset_timing.restype = I
     lib.pepo_launch_count.argtypes = [P]
     lib.pepo_launch_count.restype = ctypes.c_longlong
     lib.pepo_last_error.argtypes = [P]
@@ -213,6 +225,24 @@ class Engine:
     def launches(self):
         return int(self.lib.pepo_launch_count(self.ctx))
 
+    def set_timing(self, on=True):
+        self._check(self.lib.pepo_set_timing(self.ctx, 1 if on else 0), "pepo_set_timing")
+
+    def reset_timing(self):
+        self._check(self.lib.pepo_reset_timing(self.ctx), "pepo_reset_timing")
+
+    def timing(self):
+        """{class: dict(launches, ms, bytes, flops)} since the last reset."""
+        out = {}
+        for k in range(self.lib.pepo_timing_classes()):
+            n = ctypes.c_longlong()
+            ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            self._check(self.lib.pepo_get_timing(self.ctx, k, ctypes.byref(n), ctypes.byref(ms),
+                                                 ctypes.byref(by), ctypes.byref(fl)), "pepo_get_timing")
+            out[self.lib.pepo_timing_class_name(k).decode()] = dict(
+                launches=n.value, ms=ms.value, bytes=by.value, flops=fl.value)
+        return out
+
     # -- the four entry points of the method
     def trotter_step(self, n=1):
         self._check(self.lib.pepo_trotter_step(self.ctx, n), "pepo_trotter_step")
@@ -278,13 +308,14 @@ class Engine:
     def run(self, nsteps, measure_every=1):
         """Evolve nsteps, measuring C(t) (BP + correlator) every `measure_every` steps."""
         out = []
+        pick = (lambda D: D[0]) if self.n_inst == 1 else (lambda D: D)
         self.bp_converge()
         C, D = self.correlator()
-        out.append(D)
+        out.append(pick(D))
         for s in range(1, nsteps + 1):
             self.trotter_step(1)
             if s % measure_every == 0 or s == nsteps:
                 self.bp_converge()
                 C, D = self.correlator()
-                out.append(D)
+                out.append(pick(D))
         return out

@@ -158,6 +158,16 @@ struct pepo_ctx {
   long long launches = 0;
   std::string err;
   bool stepped = false;
+  // kernel-class timing
+  bool timing = false;
+  std::vector<char> host_items;          // host copy of the item arrays
+  std::vector<int> ival_snap;            // live sizes at the start of the call
+  struct Rec { int cls; cudaEvent_t a, b; double bytes, flops; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_next = 0;
+  struct Tot { long long n = 0; double ms = 0, bytes = 0, flops = 0; };
+  std::vector<Tot> tot;
   int max_levels = 1;      // TSQR levels
   int rmax = 4, nmax = 4;
 };
@@ -878,17 +888,125 @@ size_t layout_arena(pepo_ctx* c, char* base, Planner* keep) {
   return total;
 }
 
-// every launch wrapper returns without launching when its item count is 0;
-// LAUNCH counts the launches that happen (n > 0)
-#define LAUNCH_N(n, expr)                                                               \
+// ------------------------------------------------------------ kernel timing
+enum KClass {
+  K_LEG = 0, K_GRAM_ROWS, K_GRAM_ROWS_RED, K_GRAM_LEG, K_GRAM_LEG_RED, K_RECON, K_HH, K_FACTOR,
+  K_CORE, K_ENV, K_VEC, K_MSG, K_OTHER, K_NCLASS
+};
+const char* kClassNames[K_NCLASS] = {
+  "leg_contract", "gram_rows", "gram_rows_reduce", "gram_leg", "gram_leg_reduce", "reconstruct",
+  "householder_tsqr", "factor", "core_svd", "env_factor", "vec_contract", "msg_finish", "other"};
+
+struct Work { double bytes = 0, flops = 0; };
+
+inline int iv(const pepo_ctx* c, int idx) { return c->ival_snap[idx]; }
+
+void view_dims(const pepo_ctx* c, const TView& v, long long* d) {
+  for (int k = 0; k < PEPO_MAXLEG; ++k) d[k] = k < v.nlegs ? iv(c, v.dim[k]) : 1;
+}
+
+// algorithmic bytes / FLOPs of one launch from its host item copies
+Work work_of(const pepo_ctx* c, int cls, const void* items, int n) {
+  Work w;
+  if (c->ival_snap.empty() || !items) return w;
+  const double ts = (double)c->tsize;
+  for (int i = 0; i < n; ++i) {
+    long long d[PEPO_MAXLEG];
+    if (cls == K_LEG) {
+      const LegItem& it = static_cast<const LegItem*>(items)[i];
+      view_dims(c, it.in, d);
+      double in = 4;
+      for (int k = 0; k < it.in.nlegs; ++k) in *= d[k];
+      double out = in / d[it.leg] * iv(c, it.out_dim);
+      w.bytes += (in + out) * ts;
+      w.flops += 2.0 * out * d[it.leg];
+    } else if (cls == K_GRAM_ROWS) {
+      const GramRowsItem& it = static_cast<const GramRowsItem*>(items)[i];
+      if (it.active >= 0 && iv(c, it.active) == 0) continue;
+      view_dims(c, it.x, d);
+      double F = 4.0 * d[it.x.nlegs - 1], K = 1;
+      for (int k = 0; k + 1 < it.x.nlegs; ++k) K *= d[k];
+      w.bytes += K * F * ts;
+      w.flops += K * F * (F + 1);
+    } else if (cls == K_GRAM_LEG) {
+      const GramLegItem& it = static_cast<const GramLegItem*>(items)[i];
+      view_dims(c, it.x, d);
+      double tot = 4;
+      for (int k = 0; k < it.x.nlegs; ++k) tot *= d[k];
+      double F = d[it.leg];
+      w.bytes += 2.0 * tot * ts;
+      w.flops += 2.0 * tot * F;
+    } else if (cls == K_RECON) {
+      const ReconItem& it = static_cast<const ReconItem*>(items)[i];
+      view_dims(c, it.in, d);
+      double nin = 4.0 * d[it.in.nlegs - 1], nout = 4.0 * iv(c, it.new_dim), R = 1;
+      for (int k = 0; k + 1 < it.in.nlegs; ++k) R *= d[k];
+      w.bytes += R * (nin + nout) * ts;
+      w.flops += 2.0 * R * nin * nout;
+    }
+  }
+  return w;
+}
+
+template <class I> const void* hitems(const pepo_ctx* c, const DArr<I>& a) {
+  return c->host_items.empty() ? nullptr : c->host_items.data() + a.off;
+}
+
+cudaEvent_t next_event(pepo_ctx* c) {
+  if (c->pool_next == c->pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->pool.push_back(e);
+  }
+  return c->pool[c->pool_next++];
+}
+
+void timing_begin(pepo_ctx* c) {
+  if (!c->timing) return;
+  c->ival_snap.assign(c->n_ival, 0);
+  cudaMemcpyAsync(c->ival_snap.data(), c->d_ival, sizeof(int) * c->n_ival, cudaMemcpyDeviceToHost,
+                  c->stream);
+  cudaStreamSynchronize(c->stream);
+}
+
+void timing_harvest(pepo_ctx* c) {
+  if (c->pending.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& r : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      auto& t = c->tot[r.cls];
+      t.n++;
+      t.ms += ms;
+      t.bytes += r.bytes;
+      t.flops += r.flops;
+    }
+  }
+  c->pending.clear();
+  c->pool_next = 0;
+}
+
+// Every launch wrapper returns without launching when its item count is 0;
+// LAUNCH_T counts (and, in timing mode, brackets with events) the launches
+// that happen.
+#define LAUNCH_T(cls, hptr, n, expr)                                                    \
   do {                                                                                  \
     if ((n) > 0) {                                                                      \
+      cudaEvent_t _a = nullptr, _b = nullptr;                                           \
+      if (c->timing) { _a = next_event(c); _b = next_event(c); cudaEventRecord(_a, c->stream); } \
       cudaError_t _e = (expr);                                                          \
       c->launches++;                                                                    \
       if (_e != cudaSuccess)                                                            \
         return fail(c, PEPO_E_CUDA, "%s: %s", #expr, cudaGetErrorString(_e));           \
+      if (c->timing && _a && _b) {                                                      \
+        cudaEventRecord(_b, c->stream);                                                 \
+        Work _w = work_of(c, (cls), (hptr), (n));                                       \
+        c->pending.push_back({(cls), _a, _b, _w.bytes, _w.flops});                      \
+        if (c->pending.size() > 4000) timing_harvest(c);                                \
+      }                                                                                 \
     }                                                                                   \
   } while (0)
+#define LAUNCH_N(n, expr) LAUNCH_T(K_OTHER, nullptr, n, expr)
 
 template <typename T>
 pepo_status run_gate_wave(pepo_ctx* c, Inst& I, GateWave& w) {
@@ -899,16 +1017,16 @@ pepo_status run_gate_wave(pepo_ctx* c, Inst& I, GateWave& w) {
   int gx_leg = (int)std::min<long long>(std::max<long long>(1, big / (long long)(chimax * 64) + 1),
                                         (long long)(2 * 152 * 4 / std::max(1, w.leg[0].n) + 1));
   gx_leg = std::max(gx_leg, 8);
-  LAUNCH_N(w.env.n, launch_env_factor(w.env.d, w.env.n, chimax, c->d_ival, I.cfg.pinv_rel, s));
+  LAUNCH_T(K_ENV, nullptr, w.env.n, launch_env_factor(w.env.d, w.env.n, chimax, c->d_ival, I.cfg.pinv_rel, s));
   LAUNCH_N(w.copy.n, launch_copy<T>(w.copy.d, w.copy_out.d, w.copy.n, 64, c->d_ptrs, c->d_ival, s));
   for (int r = 0; r < 3; ++r)
-    LAUNCH_N(w.leg[r].n, launch_leg_contract<T>(w.leg[r].d, w.leg[r].n, gx_leg, chimax, c->d_ptrs, c->d_ival, s));
+    LAUNCH_T(K_LEG, hitems(c, w.leg[r]), w.leg[r].n, launch_leg_contract<T>(w.leg[r].d, w.leg[r].n, gx_leg, chimax, c->d_ptrs, c->d_ival, s));
   LAUNCH_N(w.fac.n, launch_branch(w.fac.d, w.fac.n, c->d_ival, I.cfg.qr_n_thresh, I.cfg.qr_ratio_thresh, s));
   {
     int nt = ceil_div(nmax, 64);
-    LAUNCH_N(w.gram.n, launch_gram_rows<T>(w.gram.d, w.gram.n, nt * (nt + 1) / 2, kGramSplits, 1, c->d_ptrs,
+    LAUNCH_T(K_GRAM_ROWS, hitems(c, w.gram), w.gram.n, launch_gram_rows<T>(w.gram.d, w.gram.n, nt * (nt + 1) / 2, kGramSplits, 1, c->d_ptrs,
                                c->d_ival, s));
-    LAUNCH_N(w.gram.n, launch_gram_rows_reduce(w.gram.d, w.gram.n, nmax, kGramSplits, 1, c->d_ival, s));
+    LAUNCH_T(K_GRAM_ROWS_RED, nullptr, w.gram.n, launch_gram_rows_reduce(w.gram.d, w.gram.n, nmax, kGramSplits, 1, c->d_ival, s));
   }
   {
     const long long mmax = (long long)pow_sz(chimax, 3);
@@ -919,21 +1037,21 @@ pepo_status run_gate_wave(pepo_ctx* c, Inst& I, GateWave& w) {
     while (nb > 1) { nb = (nb + 3) / 4; ++levels; }
     long long g = nb0;
     for (int l = 0; l < levels; ++l) {
-      LAUNCH_N(w.fac.n, launch_hh_level<T>(w.fac.d, w.fac.n, l, (int)std::max<long long>(g, 1), nmax, c->d_ptrs,
+      LAUNCH_T(K_HH, nullptr, w.fac.n, launch_hh_level<T>(w.fac.d, w.fac.n, l, (int)std::max<long long>(g, 1), nmax, c->d_ptrs,
                                 c->d_ival, s));
       g = (g + 3) / 4;
     }
-    LAUNCH_N(w.fac.n, launch_hh_extract<T>(w.fac.d, w.fac.n, c->d_ptrs, c->d_ival, s));
+    LAUNCH_T(K_HH, nullptr, w.fac.n, launch_hh_extract<T>(w.fac.d, w.fac.n, c->d_ptrs, c->d_ival, s));
   }
-  LAUNCH_N(w.fac.n, launch_form(w.fac.d, w.fac.n, 16, c->d_ival, s));
-  LAUNCH_N(w.fac.n, launch_factor(w.fac.d, w.fac.n, rmax, nmax, c->d_ival, s));
-  LAUNCH_N(w.core.n, launch_core(w.core.d, w.core.n, c->d_ival, s));
+  LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_form(w.fac.d, w.fac.n, 16, c->d_ival, s));
+  LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_factor(w.fac.d, w.fac.n, rmax, nmax, c->d_ival, s));
+  LAUNCH_T(K_CORE, nullptr, w.core.n, launch_core(w.core.d, w.core.n, c->d_ival, s));
   {
     long long rows = (long long)pow_sz(chimax, 3);
     int gx = (int)std::min<long long>(std::max<long long>(1, (rows + 63) / 64 * ceil_div(nmax, 64)),
                                       (long long)(2 * 152 * 4 / std::max(1, w.recon.n) + 1));
     gx = std::max(gx, 4);
-    LAUNCH_N(w.recon.n, launch_reconstruct<T>(w.recon.d, w.recon.n, gx, 0, c->d_ptrs, c->d_ival, s));
+    LAUNCH_T(K_RECON, hitems(c, w.recon), w.recon.n, launch_reconstruct<T>(w.recon.d, w.recon.n, gx, 0, c->d_ptrs, c->d_ival, s));
   }
   LAUNCH_N(w.npairs, launch_commit(w.pairs.d, w.npairs, w.moves.d, w.nmoves, c->d_ptrs, c->d_ival, s));
   return PEPO_OK;
@@ -951,9 +1069,9 @@ pepo_status run_bp_waves(pepo_ctx* c, Inst& I, std::vector<BpWave>& waves) {
                                         (long long)(2 * 152 * 4 / std::max(1, w.gram[a].n) + 1));
       gx = std::max(gx, 8);
       for (int r = 0; r < 3; ++r)
-        LAUNCH_N(w.leg[a][r].n, launch_leg_contract<T>(w.leg[a][r].d, w.leg[a][r].n, gx, chimax, c->d_ptrs, c->d_ival, s));
-      LAUNCH_N(w.gram[a].n, launch_gram_leg<T>(w.gram[a].d, w.gram[a].n, kLegSplits, c->d_ptrs, c->d_ival, s));
-      LAUNCH_N(w.gram[a].n, launch_gram_leg_reduce(w.gram[a].d, w.gram[a].n, chimax, kLegSplits, c->d_ival, s));
+        LAUNCH_T(K_LEG, hitems(c, w.leg[a][r]), w.leg[a][r].n, launch_leg_contract<T>(w.leg[a][r].d, w.leg[a][r].n, gx, chimax, c->d_ptrs, c->d_ival, s));
+      LAUNCH_T(K_GRAM_LEG, hitems(c, w.gram[a]), w.gram[a].n, launch_gram_leg<T>(w.gram[a].d, w.gram[a].n, kLegSplits, c->d_ptrs, c->d_ival, s));
+      LAUNCH_T(K_GRAM_LEG_RED, nullptr, w.gram[a].n, launch_gram_leg_reduce(w.gram[a].d, w.gram[a].n, chimax, kLegSplits, c->d_ival, s));
     }
   }
   return PEPO_OK;
@@ -963,7 +1081,7 @@ template <typename T>
 pepo_status run_sl_pass(pepo_ctx* c, Inst& I) {
   for (int l = 0; l < 4; ++l) {
     if (I.sl[l].items.n == 0) continue;
-    LAUNCH_N(I.sl[l].items.n, launch_vec_contract<T>(I.sl[l].items.d, I.sl[l].items.n, 256, c->d_ptrs, c->d_ival, c->stream));
+    LAUNCH_T(K_VEC, nullptr, I.sl[l].items.n, launch_vec_contract<T>(I.sl[l].items.d, I.sl[l].items.n, 256, c->d_ptrs, c->d_ival, c->stream));
   }
   return PEPO_OK;
 }
@@ -1007,7 +1125,7 @@ pepo_status do_bp(pepo_ctx* c, int* sweeps_out, double* delta_out) {
       any = true;
       pepo_status st = run_bp_waves<T>(c, I, I.bwaves);
       if (st != PEPO_OK) return st;
-      LAUNCH_N(I.msgs.n, launch_bp_finish(I.msgs.d, I.msgs.n, c->d_ival, I.cfg.chi_max, I.cfg.bp_alpha,
+      LAUNCH_T(K_MSG, nullptr, I.msgs.n, launch_bp_finish(I.msgs.d, I.msgs.n, c->d_ival, I.cfg.chi_max, I.cfg.bp_alpha,
                               c->d_delta2, c->d_flags, s));
     }
     if (!any) break;
@@ -1051,7 +1169,7 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
       any = true;
       pepo_status st = run_sl_pass<T>(c, I);
       if (st != PEPO_OK) return st;
-      LAUNCH_N(I.msgs.n, launch_sl_finish(I.msgs.d, I.msgs.n, c->d_ival, I.cfg.bp_alpha, c->d_delta1, s));
+      LAUNCH_T(K_MSG, nullptr, I.msgs.n, launch_sl_finish(I.msgs.d, I.msgs.n, c->d_ival, I.cfg.bp_alpha, c->d_delta1, s));
     }
     if (!any) break;
     if (cudaMemcpyAsync(hd.data(), c->d_delta1, sizeof(unsigned long long) * c->n_inst,
@@ -1212,6 +1330,8 @@ pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena, size
   c->arena_bytes = arena_bytes;
   layout_arena(c, c->arena, &P);
   finalize_items(c, P);
+  c->host_items = P.st.bytes;
+  c->tot.assign(K_NCLASS, pepo_ctx::Tot());
   cudaStream_t s = c->stream;
   bool ok = cudaMemcpyAsync(c->d_ptrs, P.ptr_init.data(), sizeof(void*) * P.ptr_init.size(),
                             cudaMemcpyHostToDevice, s) == cudaSuccess;
@@ -1260,17 +1380,25 @@ pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena, size
 pepo_status pepo_trotter_step(pepo_ctx* c, int n_steps) {
   if (!c) return PEPO_E_INVALID;
   if (n_steps < 0) return fail(c, PEPO_E_INVALID, "n_steps must be >= 0");
-  return c->tsize == 8 ? do_steps<double>(c, n_steps) : do_steps<float>(c, n_steps);
+  timing_begin(c);
+  pepo_status st = c->tsize == 8 ? do_steps<double>(c, n_steps) : do_steps<float>(c, n_steps);
+  return st;
 }
 
 pepo_status pepo_bp_converge(pepo_ctx* c, int* sweeps_out, double* delta_out) {
   if (!c) return PEPO_E_INVALID;
-  return c->tsize == 8 ? do_bp<double>(c, sweeps_out, delta_out) : do_bp<float>(c, sweeps_out, delta_out);
+  timing_begin(c);
+  pepo_status st = c->tsize == 8 ? do_bp<double>(c, sweeps_out, delta_out) : do_bp<float>(c, sweeps_out, delta_out);
+  timing_harvest(c);
+  return st;
 }
 
 pepo_status pepo_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
   if (!c) return PEPO_E_INVALID;
-  return c->tsize == 8 ? do_correlator<double>(c, C_out, diag_out) : do_correlator<float>(c, C_out, diag_out);
+  timing_begin(c);
+  pepo_status st = c->tsize == 8 ? do_correlator<double>(c, C_out, diag_out) : do_correlator<float>(c, C_out, diag_out);
+  timing_harvest(c);
+  return st;
 }
 
 pepo_status pepo_get_spectrum(pepo_ctx* c, int inst, int bond, double* lam_out, int* chi_out) {
@@ -1428,6 +1556,41 @@ long long pepo_launch_count(const pepo_ctx* c) { return c ? c->launches : 0; }
 
 const char* pepo_last_error(const pepo_ctx* c) { return c ? c->err.c_str() : kStaticErr; }
 
-void pepo_destroy(pepo_ctx* c) { delete c; }
+void pepo_destroy(pepo_ctx* c) {
+  if (!c) return;
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  delete c;
+}
+
+pepo_status pepo_set_timing(pepo_ctx* c, int enable) {
+  if (!c) return PEPO_E_INVALID;
+  timing_harvest(c);
+  c->timing = enable != 0;
+  return PEPO_OK;
+}
+
+int pepo_timing_classes(void) { return K_NCLASS; }
+
+const char* pepo_timing_class_name(int k) { return (k >= 0 && k < K_NCLASS) ? kClassNames[k] : ""; }
+
+pepo_status pepo_get_timing(pepo_ctx* c, int k, long long* launches, double* ms, double* bytes,
+                            double* flops) {
+  if (!c) return PEPO_E_INVALID;
+  if (k < 0 || k >= K_NCLASS) return fail(c, PEPO_E_INVALID, "bad kernel class");
+  timing_harvest(c);
+  const auto& t = c->tot[k];
+  if (launches) *launches = t.n;
+  if (ms) *ms = t.ms;
+  if (bytes) *bytes = t.bytes;
+  if (flops) *flops = t.flops;
+  return PEPO_OK;
+}
+
+pepo_status pepo_reset_timing(pepo_ctx* c) {
+  if (!c) return PEPO_E_INVALID;
+  timing_harvest(c);
+  c->tot.assign(K_NCLASS, pepo_ctx::Tot());
+  return PEPO_OK;
+}
 
 }  // extern "C"
