@@ -539,6 +539,20 @@ __device__ int jacobi_svd(double* A, int m, int n, double* V, int max_sweeps, in
   if (n < 2) return 0;
   const int np = (n % 2) ? n + 1 : n;   // players incl. a dummy
   const double tol = 1e-15 * sqrt((double)m);
+  // columns below 1e-30 of the total squared norm are numerically zero: rotating
+  // them only stirs rounding noise and never converges
+  double fro = 0.0;
+  for (long long e = threadIdx.x; e < (long long)m * n; e += blockDim.x) fro = fma(A[e], A[e], fro);
+  {
+    fro = warp_sum(fro);
+    __shared__ double fr[32];
+    if (lane == 0) fr[wid] = fro;
+    __syncthreads();
+    fro = 0.0;
+    for (int i = 0; i < nw; ++i) fro += fr[i];
+    __syncthreads();
+  }
+  const double negligible = 1e-30 * fro;
   __shared__ int sh_rot;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
@@ -560,7 +574,7 @@ __device__ int jacobi_svd(double* A, int m, int n, double* V, int max_sweeps, in
           al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
         }
         al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-        if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
+        if (ga != 0.0 && al > negligible && be > negligible && fabs(ga) > tol * sqrt(al * be)) {
           rotated = 1;
           const double zeta = (be - al) / (2.0 * ga);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
