@@ -1,10 +1,6 @@
 // HBM-bound tensor kernels of the bond update and of BP.
 //
-//   k_leg_contract   absorb a chi x chi (or k x chi) matrix into one leg of a
-//                    site tensor (Sec. 2.4 step 1; Eq. 11 products)
 //   k_gram_rows      cv^T cv with FP64 accumulation (Eq. 7, Cholesky-QR Gram)
-//   k_gram_leg       contraction of two tensors over every index but one leg
-//                    (Eq. 11 message with the Pauli leg traced)
 //   k_reconstruct    psi_new = psi W written in the next update's layout
 //                    (Sec. 2.4 steps 6-7 in Q-less form, Alg. 1 lines 9-12)
 //   k_vec_contract   one-leg vector contraction (single-layer BP, Sec. 2.5)
@@ -29,88 +25,6 @@ template <> struct Flush<double> {
 __device__ inline void load_dims(const TView& v, const int* ival, int* d) {
 #pragma unroll
   for (int k = 0; k < PEPO_MAXLEG; ++k) d[k] = (k < v.nlegs) ? ival[v.dim[k]] : 1;
-}
-
-// ============================================================ leg contraction
-constexpr int LC_THREADS = 256;
-constexpr int LC_BQ = 64;
-constexpr int LC_RG = LC_THREADS / LC_BQ;   // 4 row groups
-constexpr int LC_RMAX = 32;                 // rows per thread: chi <= 128
-
-template <typename T>
-__global__ void __launch_bounds__(LC_THREADS)
-k_leg_contract(const LegItem* __restrict__ items, void* const* ptrs, const int* __restrict__ ival) {
-  const LegItem it = items[blockIdx.y];
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  int d[PEPO_MAXLEG];
-  load_dims(it.in, ival, d);
-  const int k = it.leg;
-  const int Jin = d[k];
-  const int Jout = ival[it.out_dim];
-  long long O = 1, Q = 4;
-  for (int i = 0; i < k; ++i) O *= d[i];
-  for (int i = k + 1; i < it.in.nlegs; ++i) Q *= d[i];
-  T* As = reinterpret_cast<T*>(smem_raw);          // [Jout][Jin]
-  T* tile = As + Jout * Jin;                       // [Jin][LC_BQ]
-  for (int e = threadIdx.x; e < Jout * Jin; e += blockDim.x) {
-    int i = e / Jin, j = e - i * Jin;
-    As[e] = (T)it.A[(long long)i * it.lda + j];
-  }
-  long long G, nqb, units;
-  if (Q >= LC_BQ) { G = 1; nqb = (Q + LC_BQ - 1) / LC_BQ; units = O * nqb; }
-  else { G = LC_BQ / Q; nqb = 1; units = (O + G - 1) / G; }
-  const T* __restrict__ in = static_cast<const T*>(ptrs[it.in.ref]);
-  T* __restrict__ out = static_cast<T*>(ptrs[it.out_ref]);
-  const int col = threadIdx.x % LC_BQ, rg = threadIdx.x / LC_BQ;
-  const int nr = (Jout > rg) ? (Jout - rg + LC_RG - 1) / LC_RG : 0;
-  __syncthreads();
-  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-    long long o0, q0;
-    int width;
-    if (G == 1) { o0 = u / nqb; q0 = (u - o0 * nqb) * LC_BQ; width = (int)min((long long)LC_BQ, Q - q0); }
-    else { o0 = u * G; q0 = 0; width = (int)(min(G, O - o0) * Q); }
-    for (int e = threadIdx.x; e < Jin * LC_BQ; e += blockDim.x) {
-      int j = e / LC_BQ, c = e - j * LC_BQ;
-      T v = T(0);
-      if (c < width) {
-        long long o = (G == 1) ? o0 : o0 + c / Q;
-        long long q = (G == 1) ? q0 + c : c % Q;
-        v = in[(o * Jin + j) * Q + q];
-      }
-      tile[e] = v;
-    }
-    __syncthreads();
-    T acc[LC_RMAX];
-#pragma unroll
-    for (int r = 0; r < LC_RMAX; ++r) acc[r] = T(0);
-    for (int j = 0; j < Jin; ++j) {
-      const T x = tile[j * LC_BQ + col];
-#pragma unroll
-      for (int r = 0; r < LC_RMAX; ++r)
-        if (r < nr) acc[r] += As[(rg + r * LC_RG) * Jin + j] * x;
-    }
-    if (col < width) {
-      long long o = (G == 1) ? o0 : o0 + col / Q;
-      long long q = (G == 1) ? q0 + col : col % Q;
-#pragma unroll
-      for (int r = 0; r < LC_RMAX; ++r)
-        if (r < nr) out[(o * Jout + (rg + r * LC_RG)) * Q + q] = acc[r];
-    }
-    __syncthreads();
-  }
-}
-
-template <typename T>
-cudaError_t launch_leg_contract(const LegItem* items, int n_items, int grid_x, int chimax,
-                                void* const* ptrs, const int* ival, cudaStream_t s) {
-  if (n_items == 0) return cudaSuccess;
-  size_t smem = sizeof(T) * ((size_t)chimax * chimax + (size_t)chimax * LC_BQ);
-  cudaError_t e = cudaFuncSetAttribute(k_leg_contract<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid(grid_x, n_items);
-  k_leg_contract<T><<<grid, LC_THREADS, smem, s>>>(items, ptrs, ival);
-  return cudaGetLastError();
 }
 
 // ======================================================================= copy
@@ -271,158 +185,6 @@ cudaError_t launch_gram_rows_reduce(const GramRowsItem* items, int n_items, int 
   return cudaGetLastError();
 }
 
-// ============================================================ Gram (free leg)
-// X, Y viewed as [O][F][Q].  A chunk is 16 (o, q) pairs: one o and 16
-// consecutive q when Q >= 16, else floor(16 / Q) consecutive o with all q.
-constexpr int GL_T = 64;
-constexpr int GL_BK = 16;
-
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_gram_leg(const GramLegItem* __restrict__ items, int splits_max, void* const* ptrs,
-           const int* __restrict__ ival) {
-  const GramLegItem it = items[blockIdx.z];
-  int d[PEPO_MAXLEG];
-  load_dims(it.x, ival, d);
-  const int k = it.leg;
-  const int F = d[k];
-  long long O = 1, Q = 4;
-  for (int i = 0; i < k; ++i) O *= d[i];
-  for (int i = k + 1; i < it.x.nlegs; ++i) Q *= d[i];
-  const long long NC = gram_leg_chunks(O, Q);
-  const int S = gram_leg_splits(NC, splits_max);
-  const int s = blockIdx.x % splits_max;
-  const int t = blockIdx.x / splits_max;
-  const int nt = ceil_div(F, GL_T);
-  if (s >= S || t >= nt * nt) return;
-  const int ti = t / nt, tj = t - ti * nt;
-  const long long c0 = NC * s / S, c1 = NC * (s + 1) / S;
-  const T* __restrict__ X = static_cast<const T*>(ptrs[it.x.ref]);
-  const T* __restrict__ Y = static_cast<const T*>(ptrs[it.y_ref]);
-  __shared__ __align__(16) T Xs[GL_BK][GL_T];
-  __shared__ __align__(16) T Ys[GL_BK][GL_T];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const bool wideQ = Q >= GL_BK;
-  const long long qpc = wideQ ? (Q + GL_BK - 1) / GL_BK : 0;  // chunks per o
-  const int opc = wideQ ? 1 : (int)(GL_BK / Q);               // o per chunk
-  T acc[4][4];
-  double acc64[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) { acc[a][b] = T(0); acc64[a][b] = 0.0; }
-  int run = 0;
-  for (long long c = c0; c < c1; ++c) {
-    long long o0, q0;
-    if (wideQ) { o0 = c / qpc; q0 = (c - o0 * qpc) * GL_BK; }
-    else { o0 = c * opc; q0 = 0; }
-    for (int e = threadIdx.x; e < GL_BK * GL_T; e += blockDim.x) {
-      int f, kk;
-      long long o, q;
-      bool ok;
-      if (wideQ) {
-        f = e / GL_BK; kk = e - f * GL_BK;
-        o = o0; q = q0 + kk; ok = q < Q;
-      } else {
-        int Qi = (int)Q;
-        int qq = e % Qi;
-        int rest = e / Qi;
-        f = rest % GL_T;
-        int ol = rest / GL_T;
-        kk = ol * Qi + qq;
-        o = o0 + ol; q = qq;
-        ok = (ol < opc) && (o < O);
-        if (ol >= opc) { kk = -1; }
-      }
-      if (kk < 0) continue;
-      int fi = ti * GL_T + f, fj = tj * GL_T + f;
-      long long base = o * F;
-      Xs[kk][f] = (ok && fi < F) ? X[(base + fi) * Q + q] : T(0);
-      Ys[kk][f] = (ok && fj < F) ? Y[(base + fj) * Q + q] : T(0);
-    }
-    if (!wideQ) {
-      // unused trailing rows of the chunk (opc * Q < 16) must be zero
-      int used = opc * (int)Q;
-      for (int e = threadIdx.x; e < (GL_BK - used) * GL_T; e += blockDim.x) {
-        int kk = used + e / GL_T, f = e % GL_T;
-        Xs[kk][f] = T(0);
-        Ys[kk][f] = T(0);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GL_BK; ++kk) {
-      T xa[4], yb[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) xa[a] = Xs[kk][ty * 4 + a];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) yb[b] = Ys[kk][tx * 4 + b];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(xa[a], yb[b], acc[a][b]);
-    }
-    __syncthreads();
-    if (Flush<T>::kFlush) {
-      run += GL_BK;
-      if (run >= GR_FLUSH) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) { acc64[a][b] += (double)acc[a][b]; acc[a][b] = T(0); }
-        run = 0;
-      }
-    }
-  }
-  double* P = it.partial + (long long)s * F * F;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int fi = ti * GL_T + ty * 4 + a;
-    if (fi >= F) continue;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      int fj = tj * GL_T + tx * 4 + b;
-      if (fj < F) P[(long long)fi * F + fj] = acc64[a][b] + (double)acc[a][b];
-    }
-  }
-}
-
-__global__ void k_gram_leg_reduce(const GramLegItem* __restrict__ items, int splits_max,
-                                  const int* __restrict__ ival) {
-  const GramLegItem it = items[blockIdx.y];
-  int d[PEPO_MAXLEG];
-  load_dims(it.x, ival, d);
-  const int k = it.leg;
-  const int F = d[k];
-  long long O = 1, Q = 4;
-  for (int i = 0; i < k; ++i) O *= d[i];
-  for (int i = k + 1; i < it.x.nlegs; ++i) Q *= d[i];
-  const int S = gram_leg_splits(gram_leg_chunks(O, Q), splits_max);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < F * F; e += gridDim.x * blockDim.x) {
-    double sum = 0.0;
-    for (int s = 0; s < S; ++s) sum += it.partial[(long long)s * F * F + e];
-    int fi = e / F, fj = e - fi * F;
-    it.out[(long long)fi * it.ldo + fj] = sum;
-  }
-}
-
-template <typename T>
-cudaError_t launch_gram_leg(const GramLegItem* items, int n_items, int splits_max,
-                            void* const* ptrs, const int* ival, cudaStream_t s) {
-  if (n_items == 0) return cudaSuccess;
-  // F <= 128 -> at most 4 tiles
-  dim3 grid(4 * splits_max, 1, n_items);
-  k_gram_leg<T><<<grid, 256, 0, s>>>(items, splits_max, ptrs, ival);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gram_leg_reduce(const GramLegItem* items, int n_items, int chimax,
-                                   int splits_max, const int* ival, cudaStream_t s) {
-  if (n_items == 0) return cudaSuccess;
-  int gx = ceil_div(chimax * chimax, 256);
-  k_gram_leg_reduce<<<dim3(gx, n_items), 256, 0, s>>>(items, splits_max, ival);
-  return cudaGetLastError();
-}
 
 // ================================================================ reconstruct
 // out[r, (c', p')] = sum_{(c,p)} in[r, (c,p)] W[(c,p), (c',p')], stored in the
@@ -579,14 +341,10 @@ cudaError_t launch_vec_contract(const VecItem* items, int n_items, int grid_x, v
 
 // ============================================================ instantiations
 #define PEPO_INST(T)                                                                              \
-  template cudaError_t launch_leg_contract<T>(const LegItem*, int, int, int, void* const*,        \
-                                              const int*, cudaStream_t);                          \
   template cudaError_t launch_copy<T>(const TView*, const int*, int, int, void* const*,           \
                                       const int*, cudaStream_t);                                  \
   template cudaError_t launch_gram_rows<T>(const GramRowsItem*, int, int, int, int, void* const*, \
                                            const int*, cudaStream_t);                             \
-  template cudaError_t launch_gram_leg<T>(const GramLegItem*, int, int, void* const*,             \
-                                          const int*, cudaStream_t);                              \
   template cudaError_t launch_reconstruct<T>(const ReconItem*, int, int, int, void* const*,       \
                                              const int*, cudaStream_t);                           \
   template cudaError_t launch_vec_contract<T>(const VecItem*, int, int, void* const*, const int*, \

@@ -96,8 +96,9 @@ struct GateWave {
 };
 
 struct BpWave {
-  DArr<LegItem> leg[4][3];
-  DArr<GramLegItem> gram[4];
+  DArr<EnvFactorItem> env;
+  DArr<LegItem> leg[12];
+  DArr<GramLegItem> gram[12];
 };
 
 struct SlLevel {
@@ -297,8 +298,8 @@ template <class I> DArr<I> stage(Planner& P, const std::vector<I>& v) {
 }
 
 struct SlotWS {              // per in-flight site slot (gate update)
-  double* L[3];
-  int rank_idx[3];
+  double* L[4];
+  int rank_idx[4];
   int branch_idx, kfac_idx, rankT_idx;
   double* C;
   double* T;
@@ -374,7 +375,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
   std::vector<SlotWS> slots(maxslots);
   for (int k = 0; k < maxslots; ++k) {
     SlotWS& w = slots[k];
-    for (int j = 0; j < 3; ++j) { w.L[j] = cv.take<double>(cm2); w.rank_idx[j] = P.new_ival(1); }
+    for (int j = 0; j < 4; ++j) { w.L[j] = cv.take<double>(cm2); w.rank_idx[j] = P.new_ival(1); }
     w.branch_idx = P.new_ival(0);
     w.kfac_idx = P.new_ival(0);
     w.rankT_idx = P.new_ival(0);
@@ -615,15 +616,29 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
   (void)inst_id;
 
   // ---- BP waves (double layer): sites grouped by class caps
-  auto make_bp_waves = [&](bool leg0_only, std::vector<BpWave>& out) {
-    std::vector<int> order(I.N);
-    for (int v = 0; v < I.N; ++v) order[v] = v;
+  // Double-layer BP plan (Eq. 11): every incoming message M_{u->v} is factored
+  // as L^T L (pivoted Cholesky); absorbing L on both layers of the other legs
+  // turns each outgoing message into the symmetric Gram of one tensor.  The
+  // four messages of an interior site share intermediates: X01 = psi L0 L1
+  // serves the messages to legs 3 and 2, X23 = psi L2 L3 those to legs 1 and 0
+  // (8 leg contractions, 4 Grams).  Each op occupies one of 12 fixed launch
+  // slots; sites of lower degree use a subset.
+  struct BpOp { int slot; int kind; int src; int dst; int leg; };   // kind 0 contract, 1 gram
+  // src / dst: 0 = psi, 1 = S0, 2 = S1
+  const std::vector<BpOp> ops4 = {{0, 0, 0, 1, 0}, {1, 0, 1, 2, 1}, {2, 0, 2, 1, 2}, {3, 1, 1, 0, 3},
+                                  {4, 0, 2, 1, 3}, {5, 1, 1, 0, 2}, {6, 0, 0, 1, 2}, {7, 0, 1, 2, 3},
+                                  {8, 0, 2, 1, 0}, {9, 1, 1, 0, 1}, {10, 0, 2, 1, 1}, {11, 1, 1, 0, 0}};
+  const std::vector<BpOp> ops3 = {{0, 0, 0, 1, 0}, {1, 0, 1, 2, 1}, {3, 1, 2, 0, 2}, {6, 0, 0, 1, 2},
+                                  {8, 0, 1, 2, 0}, {9, 1, 2, 0, 1}, {10, 0, 1, 2, 1}, {11, 1, 2, 0, 0}};
+  const std::vector<BpOp> ops2 = {{0, 0, 0, 1, 0}, {3, 1, 1, 0, 1}, {6, 0, 0, 1, 1}, {9, 1, 1, 0, 0}};
+  const std::vector<BpOp> ops1 = {{3, 1, 0, 0, 0}};
+  auto make_bp_waves = [&](bool fv_only, std::vector<BpWave>& out) {
     size_t pos = 0;
-    while (pos < order.size()) {
+    while (pos < (size_t)I.N) {
       int used[5] = {0, 0, 0, 0, 0};
       std::vector<int> ws;
-      while (pos < order.size()) {
-        int v = order[pos];
+      while (pos < (size_t)I.N) {
+        int v = (int)pos;
         int d = I.sites[v].deg;
         if (used[d] + 1 > I.cap[d]) break;
         used[d]++;
@@ -631,8 +646,9 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
         ++pos;
       }
       BpWave bw;
-      std::vector<LegItem> leg[4][3];
-      std::vector<GramLegItem> gram[4];
+      std::vector<EnvFactorItem> env;
+      std::vector<LegItem> leg[12];
+      std::vector<GramLegItem> gram[12];
       int cls_used[5] = {0, 0, 0, 0, 0};
       int slot_base[5];
       {
@@ -644,47 +660,56 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
         const int d = S.deg;
         const int k = cls_used[d]++;
         const int slot = slot_base[d] + k;
-        const int sref0 = sc[d].refs[2 * k], sref1 = sc[d].refs[2 * k + 1];
+        SlotWS& W = slots[slot];
+        const int refs[3] = {I.site_ref0 + v, sc[d].refs[2 * k], sc[d].refs[2 * k + 1]};
         std::vector<int> lay = layout_for(S, S.upd[0]);   // step-boundary layout
-        TView view;
-        view.nlegs = d;
-        view.ref = I.site_ref0 + v;
-        for (int j = 0; j < d; ++j) view.dim[j] = chi_idx(S.legs[lay[j]].bond);
-        const int nw = leg0_only ? 1 : d;
-        for (int w = 0; w < nw; ++w) {
-          int cur = I.site_ref0 + v;
-          int r = 0;
-          for (int j = 0; j < d; ++j) {
-            if (j == w) continue;
-            const int bj = S.legs[lay[j]].bond;
+        for (int j = 0; j < d; ++j) {
+          const int bj = S.legs[lay[j]].bond;
+          EnvFactorItem e;
+          e.M = mptr(I.msg, msg_in(v, bj));
+          e.L = W.L[j];
+          e.ld = chimax;
+          e.chi_idx = chi_idx(bj);
+          e.rank_idx = W.rank_idx[j];
+          env.push_back(e);
+        }
+        const std::vector<BpOp>& ops = d == 4 ? ops4 : d == 3 ? ops3 : d == 2 ? ops2 : ops1;
+        int contracted[3] = {0, 0, 0};   // bitmask of absorbed legs held by psi / S0 / S1
+        for (const BpOp& op : ops) {
+          if (fv_only && op.slot > 3) break;
+          TView view;
+          view.nlegs = d;
+          view.ref = refs[op.src];
+          for (int j = 0; j < d; ++j)
+            view.dim[j] = (contracted[op.src] >> j & 1) ? W.rank_idx[j] : chi_idx(S.legs[lay[j]].bond);
+          if (op.kind == 0) {
             LegItem li;
             li.in = view;
-            li.in.ref = cur;
-            li.out_ref = (r % 2 == 0) ? sref0 : sref1;
-            li.leg = j;
-            li.out_dim = chi_idx(bj);
-            li.a_rows = chi_idx(bj);
-            li.A = mptr(I.msg, msg_in(v, bj));
+            li.out_ref = refs[op.dst];
+            li.leg = op.leg;
+            li.out_dim = W.rank_idx[op.leg];
+            li.a_rows = W.rank_idx[op.leg];
+            li.A = W.L[op.leg];
             li.lda = chimax;
-            leg[w][r].push_back(li);
-            cur = li.out_ref;
-            ++r;
+            leg[op.slot].push_back(li);
+            contracted[op.dst] = contracted[op.src] | (1 << op.leg);
+          } else {
+            const int bw_ = S.legs[lay[op.leg]].bond;
+            GramLegItem g;
+            g.x = view;
+            g.y_ref = view.ref;
+            g.leg = op.leg;
+            g.partial = W.partial;
+            g.out = mptr(I.hat, msg_out(v, bw_));
+            g.ldo = chimax;
+            gram[op.slot].push_back(g);
           }
-          const int bw_ = S.legs[lay[w]].bond;
-          GramLegItem g;
-          g.x = view;
-          g.x.ref = cur;
-          g.y_ref = I.site_ref0 + v;
-          g.leg = w;
-          g.partial = slots[slot].partial;
-          g.out = mptr(I.hat, msg_out(v, bw_));
-          g.ldo = chimax;
-          gram[w].push_back(g);
         }
       }
-      for (int w = 0; w < 4; ++w) {
-        for (int r = 0; r < 3; ++r) bw.leg[w][r] = stage(P, leg[w][r]);
-        bw.gram[w] = stage(P, gram[w]);
+      bw.env = stage(P, env);
+      for (int sl = 0; sl < 12; ++sl) {
+        bw.leg[sl] = stage(P, leg[sl]);
+        bw.gram[sl] = stage(P, gram[sl]);
       }
       out.push_back(bw);
     }
@@ -782,7 +807,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
     for (int v = 0; v < I.N; ++v) {
       const SiteG& S = I.sites[v];
       std::vector<int> lay = layout_for(S, S.upd[0]);
-      const int b0 = S.legs[lay[0]].bond;
+      const int b0 = S.legs[lay[S.deg - 1]].bond;   // the message the f_v plan computes
       SiteScalarItem& s = ss[v];
       s.chi_idx = chi_idx(b0);
       s.hat = mptr(I.hat, msg_out(v, b0));
@@ -854,8 +879,9 @@ void resolve_all(pepo_ctx* c) {
       }
     for (auto* ws : {&I.bwaves, &I.fwaves})
       for (auto& w : *ws) {
-        for (int a = 0; a < 4; ++a) {
-          for (int r = 0; r < 3; ++r) resolve(w.leg[a][r], d);
+        resolve(w.env, d);
+        for (int a = 0; a < 12; ++a) {
+          resolve(w.leg[a], d);
           resolve(w.gram[a], d);
         }
       }
@@ -1061,17 +1087,20 @@ template <typename T>
 pepo_status run_bp_waves(pepo_ctx* c, Inst& I, std::vector<BpWave>& waves) {
   cudaStream_t s = c->stream;
   const int chimax = I.cfg.chi_max;
-  const long long big = (long long)4 * pow_sz(chimax, 4);
   for (auto& w : waves) {
-    for (int a = 0; a < 4; ++a) {
-      if (w.gram[a].n == 0) continue;
-      int gx = (int)std::min<long long>(std::max<long long>(1, big / (long long)(chimax * 64) + 1),
-                                        (long long)(2 * 152 * 4 / std::max(1, w.gram[a].n) + 1));
-      gx = std::max(gx, 8);
-      for (int r = 0; r < 3; ++r)
-        LAUNCH_T(K_LEG, hitems(c, w.leg[a][r]), w.leg[a][r].n, launch_leg_contract<T>(w.leg[a][r].d, w.leg[a][r].n, gx, chimax, c->d_ptrs, c->d_ival, s));
-      LAUNCH_T(K_GRAM_LEG, hitems(c, w.gram[a]), w.gram[a].n, launch_gram_leg<T>(w.gram[a].d, w.gram[a].n, kLegSplits, c->d_ptrs, c->d_ival, s));
-      LAUNCH_T(K_GRAM_LEG_RED, nullptr, w.gram[a].n, launch_gram_leg_reduce(w.gram[a].d, w.gram[a].n, chimax, kLegSplits, c->d_ival, s));
+    LAUNCH_T(K_ENV, nullptr, w.env.n, launch_env_factor(w.env.d, w.env.n, chimax, c->d_ival, I.cfg.pinv_rel, s));
+    for (int a = 0; a < 12; ++a) {
+      if (w.leg[a].n > 0) {
+        int gx = std::max(8, 2 * 152 * 4 / std::max(1, w.leg[a].n));
+        LAUNCH_T(K_LEG, hitems(c, w.leg[a]), w.leg[a].n,
+                 launch_leg_contract<T>(w.leg[a].d, w.leg[a].n, gx, chimax, c->d_ptrs, c->d_ival, s));
+      }
+      if (w.gram[a].n > 0) {
+        LAUNCH_T(K_GRAM_LEG, hitems(c, w.gram[a]), w.gram[a].n,
+                 launch_gram_leg<T>(w.gram[a].d, w.gram[a].n, kLegSplits, c->d_ptrs, c->d_ival, s));
+        LAUNCH_T(K_GRAM_LEG_RED, nullptr, w.gram[a].n,
+                 launch_gram_leg_reduce(w.gram[a].d, w.gram[a].n, chimax, kLegSplits, c->d_ival, s));
+      }
     }
   }
   return PEPO_OK;
