@@ -65,6 +65,30 @@ struct GramLegItem {
   double* partial;         // [splits][chimax * chimax]
   double* out;             // chi x chi, leading dimension ldo
   int ldo;
+  // optional square-root weights per layout leg (nullptr: weight 1); element
+  // (.., j_u, ..) of X and Y is scaled by prod_{u != leg} sw[u][j_u] on load
+  const double* sw[PEPO_MAXLEG];
+};
+
+// Eigen-decomposition of a (symmetrised) message M = V diag(D) V^T by one-sided
+// Jacobi (FP64); writes Vt (row i = eigenvector i, leading dimension ld) and
+// sqrt(D).  Used to rotate a site tensor into the message eigenbasis (Eq. 11).
+struct EnvEigItem {
+  const double* M;
+  int ld;
+  int chi_idx;
+  double* work;            // 2 * chimax^2 doubles
+  double* Vt;              // chi x chi, leading dimension ld
+  double* sqrtD;           // chi
+};
+
+// Back-rotation of one weighted Gram: out = V G V^T (G from the rotated tensor).
+struct RotItem {
+  const double* G;         // chi x chi, leading dimension ld
+  const double* Vt;        // chi x chi, leading dimension ld
+  double* out;             // chi x chi, leading dimension ld
+  int ld;
+  int chi_idx;
 };
 
 // Reconstruct (Sec. 2.4 step 6, Q-less): out = in * W where `in` is viewed as

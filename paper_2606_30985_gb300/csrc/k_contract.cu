@@ -137,6 +137,18 @@ cudaError_t launch_leg_contract(const LegItem* items, int n_items, int grid_x, i
 constexpr int GL_BK = 16;
 constexpr int GL_FLUSH = 256;
 
+// product of the square-root weights sw[u][j_u] over layout legs u in [lo, hi)
+// for the row-major multi-index `idx` of those legs
+__device__ inline double leg_weight(const GramLegItem& it, const int* d, int lo, int hi, long long idx) {
+  double w = 1.0;
+  for (int u = hi - 1; u >= lo; --u) {
+    const long long j = idx % d[u];
+    idx /= d[u];
+    if (it.sw[u]) w *= it.sw[u][j];
+  }
+  return w;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gram_leg(const GramLegItem* __restrict__ items, int splits_max, void* const* ptrs,
@@ -157,6 +169,8 @@ k_gram_leg(const GramLegItem* __restrict__ items, int splits_max, void* const* p
   const T* __restrict__ X = static_cast<const T*>(ptrs[it.x.ref]);
   const T* __restrict__ Y = static_cast<const T*>(ptrs[it.y_ref]);
   const bool same = it.x.ref == it.y_ref;
+  bool weighted = false;
+  for (int u = 0; u < it.x.nlegs; ++u) weighted |= (u != k && it.sw[u] != nullptr);
   __shared__ __align__(16) T Xs[GL_BK][128];
   __shared__ __align__(16) T Ys[GL_BK][128];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -188,13 +202,20 @@ k_gram_leg(const GramLegItem* __restrict__ items, int splits_max, void* const* p
     }
     __syncthreads();
     if (wideQ) {
+      const double wo = weighted ? leg_weight(it, d, 0, k, o0) : 1.0;
       for (int e = threadIdx.x; e < GL_BK * F; e += blockDim.x) {
         int f = e / GL_BK, kk = e - f * GL_BK;
         long long q = q0 + kk;
         if (q < Q) {
           long long idx = (o0 * F + f) * Q + q;
-          Xs[kk][f] = X[idx];
-          if (!same) Ys[kk][f] = Y[idx];
+          if (weighted) {
+            const T w = (T)(wo * leg_weight(it, d, k + 1, it.x.nlegs, q >> 2));
+            Xs[kk][f] = X[idx] * w;
+            if (!same) Ys[kk][f] = Y[idx] * w;
+          } else {
+            Xs[kk][f] = X[idx];
+            if (!same) Ys[kk][f] = Y[idx];
+          }
         }
       }
     } else {
@@ -205,8 +226,14 @@ k_gram_leg(const GramLegItem* __restrict__ items, int splits_max, void* const* p
         long long o = o0 + ol;
         if (o < O) {
           long long idx = (o * F + f) * Q + qq;
-          Xs[ol * Qi + qq][f] = X[idx];
-          if (!same) Ys[ol * Qi + qq][f] = Y[idx];
+          if (weighted) {
+            const T w = (T)(leg_weight(it, d, 0, k, o) * leg_weight(it, d, k + 1, it.x.nlegs, qq >> 2));
+            Xs[ol * Qi + qq][f] = X[idx] * w;
+            if (!same) Ys[ol * Qi + qq][f] = Y[idx] * w;
+          } else {
+            Xs[ol * Qi + qq][f] = X[idx];
+            if (!same) Ys[ol * Qi + qq][f] = Y[idx];
+          }
         }
       }
     }

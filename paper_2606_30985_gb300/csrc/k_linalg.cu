@@ -534,7 +534,10 @@ cudaError_t launch_factor(const SiteFacItem* items, int n_items, int rmax, int n
 __device__ int jacobi_svd(double* A, int m, int n, double* V, int max_sweeps, int* capped,
                           double* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = (e % (n + 1) == 0) ? 1.0 : 0.0;
+  // V == nullptr: rotations are not accumulated (the caller recovers the other
+  // side's vectors from a copy of the input)
+  if (V)
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = (e % (n + 1) == 0) ? 1.0 : 0.0;
   __syncthreads();
   if (n < 2) return 0;
   const int np = (n % 2) ? n + 1 : n;   // players incl. a dummy
@@ -584,12 +587,14 @@ __device__ int jacobi_svd(double* A, int m, int n, double* V, int max_sweeps, in
             Ap[i] = c * x - s * y;
             Aq[i] = s * x + c * y;
           }
-          double* Vp = V + (long long)p * n;
-          double* Vq = V + (long long)q * n;
-          for (int i = lane; i < n; i += 32) {
-            double x = Vp[i], y = Vq[i];
-            Vp[i] = c * x - s * y;
-            Vq[i] = s * x + c * y;
+          if (V) {
+            double* Vp = V + (long long)p * n;
+            double* Vq = V + (long long)q * n;
+            for (int i = lane; i < n; i += 32) {
+              double x = Vp[i], y = Vq[i];
+              Vp[i] = c * x - s * y;
+              Vq[i] = s * x + c * y;
+            }
           }
         }
       }
@@ -643,7 +648,9 @@ k_core(const CoreItem* __restrict__ items, int* ival) {
     if (!tr) Tc[(long long)b * M + a] = s; else Tc[(long long)a * M + b] = s;
   }
   __syncthreads();
-  jacobi_svd(Tc, M, N, V, 60, &sh_capped, red);
+  for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) V[e] = Tc[e];   // copy of Tcore
+  __syncthreads();
+  jacobi_svd(Tc, M, N, nullptr, 60, &sh_capped, red);
   __syncthreads();
   // singular values (column norms) and descending order
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
@@ -720,7 +727,17 @@ k_core(const CoreItem* __restrict__ items, int* ival) {
       int a = (int)(e / chi), c = (int)(e % chi);
       int j = order[c];
       double s = sv[j];
-      double x = from_cols ? (s > 0.0 ? Tc[(long long)j * M + a] / s : 0.0) : V[(long long)j * N + a];
+      double x;
+      if (from_cols) {
+        x = s > 0.0 ? Tc[(long long)j * M + a] / s : 0.0;
+      } else {
+        // other side: (copy^T u_j)_a / s_j, copy = Tcore column-major M x N, u_j = column j / s_j
+        double acc = 0.0;
+        const double* col = V + (long long)a * M;      // column a of the copy
+        const double* uj = Tc + (long long)j * M;
+        for (int i = 0; i < M; ++i) acc = fma(col[i], uj[i], acc);
+        x = s > 0.0 ? acc / (s * s) : 0.0;
+      }
       Z[(long long)a * chi + c] = x * sqrt(s) * inv;
     }
     __syncthreads();
@@ -771,4 +788,75 @@ template cudaError_t launch_hh_extract<float>(const SiteFacItem*, int, void* con
 template cudaError_t launch_hh_extract<double>(const SiteFacItem*, int, void* const*, int*,
                                                cudaStream_t);
 
+}  // namespace pepo
+
+namespace pepo {
+// ============================================================ message eigen
+// M (symmetrised, PSD) -> one-sided Jacobi on its columns: M V = U S with
+// S = |eigenvalues| and V the eigenvectors (U = V up to signs of numerically
+// zero eigenvalues).  Outputs Vt (row i = column i of V) and sqrt(S).
+__global__ void __launch_bounds__(1024)
+k_env_eig(const EnvEigItem* __restrict__ items, const int* ival) {
+  const EnvEigItem it = items[blockIdx.x];
+  const int n = ival[it.chi_idx];
+  double* A = it.work;                      // n x n column-major
+  double* V = it.work + (long long)n * n;   // n x n column-major
+  __shared__ double red[32];
+  __shared__ int capped;
+  if (threadIdx.x == 0) capped = 0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int i = e / n, j = e - i * n;   // A column j, row i
+    A[(long long)j * n + i] = 0.5 * (it.M[i * it.ld + j] + it.M[j * it.ld + i]);
+  }
+  __syncthreads();
+  jacobi_svd(A, n, n, V, 60, &capped, red);
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s = fma(A[(long long)j * n + i], A[(long long)j * n + i], s);
+    it.sqrtD[j] = sqrt(sqrt(s));   // sqrt of the eigenvalue |lambda_j| = ||A v_j||
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int i = e / n, j = e - i * n;
+    it.Vt[i * it.ld + j] = V[(long long)i * n + j];   // row i of Vt = column i of V
+  }
+}
+
+cudaError_t launch_env_eig(const EnvEigItem* items, int n_items, const int* ival, cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  k_env_eig<<<n_items, 1024, 0, s>>>(items, ival);
+  return cudaGetLastError();
+}
+
+// out = V G V^T = Vt^T G Vt
+__global__ void k_rotate_back(const RotItem* __restrict__ items, const int* ival) {
+  const RotItem it = items[blockIdx.x];
+  const int n = ival[it.chi_idx];
+  extern __shared__ __align__(16) double sm[];
+  double* T = sm;   // n x n: T = G Vt
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int i = e / n, j = e - i * n;
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s = fma(it.G[i * it.ld + k], it.Vt[k * it.ld + j], s);
+    T[e] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int i = e / n, j = e - i * n;
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s = fma(it.Vt[k * it.ld + i], T[k * n + j], s);
+    it.out[i * it.ld + j] = s;
+  }
+}
+
+cudaError_t launch_rotate_back(const RotItem* items, int n_items, int chimax, const int* ival,
+                               cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  size_t smem = sizeof(double) * (size_t)chimax * chimax;
+  cudaError_t e = cudaFuncSetAttribute(k_rotate_back, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_rotate_back<<<n_items, 256, smem, s>>>(items, ival);
+  return cudaGetLastError();
+}
 }  // namespace pepo

@@ -19,3 +19,9 @@ cudaError_t launch_factor(const SiteFacItem* items, int n_items, int rmax, int n
                           cudaStream_t s);
 cudaError_t launch_core(const CoreItem* items, int n_items, int* ival, cudaStream_t s);
 }  // namespace pepo
+
+namespace pepo {
+cudaError_t launch_env_eig(const EnvEigItem* items, int n_items, const int* ival, cudaStream_t s);
+cudaError_t launch_rotate_back(const RotItem* items, int n_items, int chimax, const int* ival,
+                               cudaStream_t s);
+}  // namespace pepo

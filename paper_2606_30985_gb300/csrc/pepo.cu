@@ -96,9 +96,10 @@ struct GateWave {
 };
 
 struct BpWave {
-  DArr<EnvFactorItem> env;
-  DArr<LegItem> leg[12];
-  DArr<GramLegItem> gram[12];
+  DArr<EnvEigItem> eig;
+  DArr<LegItem> leg[4];
+  DArr<GramLegItem> gram;
+  DArr<RotItem> rot;
 };
 
 struct SlLevel {
@@ -300,6 +301,7 @@ template <class I> DArr<I> stage(Planner& P, const std::vector<I>& v) {
 struct SlotWS {              // per in-flight site slot (gate update)
   double* L[4];
   int rank_idx[4];
+  double* sqrtD[4];
   int branch_idx, kfac_idx, rankT_idx;
   double* C;
   double* T;
@@ -375,7 +377,11 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
   std::vector<SlotWS> slots(maxslots);
   for (int k = 0; k < maxslots; ++k) {
     SlotWS& w = slots[k];
-    for (int j = 0; j < 4; ++j) { w.L[j] = cv.take<double>(cm2); w.rank_idx[j] = P.new_ival(1); }
+    for (int j = 0; j < 4; ++j) {
+      w.L[j] = cv.take<double>(cm2);
+      w.rank_idx[j] = P.new_ival(1);
+      w.sqrtD[j] = cv.take<double>(chimax);
+    }
     w.branch_idx = P.new_ival(0);
     w.kfac_idx = P.new_ival(0);
     w.rankT_idx = P.new_ival(0);
@@ -616,22 +622,12 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
   (void)inst_id;
 
   // ---- BP waves (double layer): sites grouped by class caps
-  // Double-layer BP plan (Eq. 11): every incoming message M_{u->v} is factored
-  // as L^T L (pivoted Cholesky); absorbing L on both layers of the other legs
-  // turns each outgoing message into the symmetric Gram of one tensor.  The
-  // four messages of an interior site share intermediates: X01 = psi L0 L1
-  // serves the messages to legs 3 and 2, X23 = psi L2 L3 those to legs 1 and 0
-  // (8 leg contractions, 4 Grams).  Each op occupies one of 12 fixed launch
-  // slots; sites of lower degree use a subset.
-  struct BpOp { int slot; int kind; int src; int dst; int leg; };   // kind 0 contract, 1 gram
-  // src / dst: 0 = psi, 1 = S0, 2 = S1
-  const std::vector<BpOp> ops4 = {{0, 0, 0, 1, 0}, {1, 0, 1, 2, 1}, {2, 0, 2, 1, 2}, {3, 1, 1, 0, 3},
-                                  {4, 0, 2, 1, 3}, {5, 1, 1, 0, 2}, {6, 0, 0, 1, 2}, {7, 0, 1, 2, 3},
-                                  {8, 0, 2, 1, 0}, {9, 1, 1, 0, 1}, {10, 0, 2, 1, 1}, {11, 1, 1, 0, 0}};
-  const std::vector<BpOp> ops3 = {{0, 0, 0, 1, 0}, {1, 0, 1, 2, 1}, {3, 1, 2, 0, 2}, {6, 0, 0, 1, 2},
-                                  {8, 0, 1, 2, 0}, {9, 1, 2, 0, 1}, {10, 0, 1, 2, 1}, {11, 1, 2, 0, 0}};
-  const std::vector<BpOp> ops2 = {{0, 0, 0, 1, 0}, {3, 1, 1, 0, 1}, {6, 0, 0, 1, 1}, {9, 1, 1, 0, 0}};
-  const std::vector<BpOp> ops1 = {{3, 1, 0, 0, 0}};
+  // Double-layer BP plan (Eq. 11).  Every incoming message is eigen-decomposed,
+  // M_{u->v} = V_u diag(D_u) V_u^T; the site tensor is rotated into the
+  // eigenbases of all its legs, psi' = psi x_u V_u^T (deg leg contractions);
+  // then each outgoing message is the Gram of psi' over every index but one
+  // leg, weighted by prod_{u != w} D_u (applied as sqrt(D) on load), rotated
+  // back with V_w.  One launch computes the Grams of all legs of the wave.
   auto make_bp_waves = [&](bool fv_only, std::vector<BpWave>& out) {
     size_t pos = 0;
     while (pos < (size_t)I.N) {
@@ -646,9 +642,10 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
         ++pos;
       }
       BpWave bw;
-      std::vector<EnvFactorItem> env;
-      std::vector<LegItem> leg[12];
-      std::vector<GramLegItem> gram[12];
+      std::vector<EnvEigItem> eig;
+      std::vector<LegItem> leg[4];
+      std::vector<GramLegItem> gram;
+      std::vector<RotItem> rot;
       int cls_used[5] = {0, 0, 0, 0, 0};
       int slot_base[5];
       {
@@ -663,54 +660,59 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
         SlotWS& W = slots[slot];
         const int refs[3] = {I.site_ref0 + v, sc[d].refs[2 * k], sc[d].refs[2 * k + 1]};
         std::vector<int> lay = layout_for(S, S.upd[0]);   // step-boundary layout
+        TView view;
+        view.nlegs = d;
+        for (int j = 0; j < d; ++j) view.dim[j] = chi_idx(S.legs[lay[j]].bond);
         for (int j = 0; j < d; ++j) {
           const int bj = S.legs[lay[j]].bond;
-          EnvFactorItem e;
+          EnvEigItem e;
           e.M = mptr(I.msg, msg_in(v, bj));
-          e.L = W.L[j];
           e.ld = chimax;
           e.chi_idx = chi_idx(bj);
-          e.rank_idx = W.rank_idx[j];
-          env.push_back(e);
+          e.work = W.T + (size_t)j * 2 * cm2;
+          e.Vt = W.L[j];
+          e.sqrtD = W.sqrtD[j];
+          eig.push_back(e);
         }
-        const std::vector<BpOp>& ops = d == 4 ? ops4 : d == 3 ? ops3 : d == 2 ? ops2 : ops1;
-        int contracted[3] = {0, 0, 0};   // bitmask of absorbed legs held by psi / S0 / S1
-        for (const BpOp& op : ops) {
-          if (fv_only && op.slot > 3) break;
-          TView view;
-          view.nlegs = d;
-          view.ref = refs[op.src];
-          for (int j = 0; j < d; ++j)
-            view.dim[j] = (contracted[op.src] >> j & 1) ? W.rank_idx[j] : chi_idx(S.legs[lay[j]].bond);
-          if (op.kind == 0) {
-            LegItem li;
-            li.in = view;
-            li.out_ref = refs[op.dst];
-            li.leg = op.leg;
-            li.out_dim = W.rank_idx[op.leg];
-            li.a_rows = W.rank_idx[op.leg];
-            li.A = W.L[op.leg];
-            li.lda = chimax;
-            leg[op.slot].push_back(li);
-            contracted[op.dst] = contracted[op.src] | (1 << op.leg);
-          } else {
-            const int bw_ = S.legs[lay[op.leg]].bond;
-            GramLegItem g;
-            g.x = view;
-            g.y_ref = view.ref;
-            g.leg = op.leg;
-            g.partial = W.partial;
-            g.out = mptr(I.hat, msg_out(v, bw_));
-            g.ldo = chimax;
-            gram[op.slot].push_back(g);
-          }
+        int cur = refs[0];
+        for (int j = 0; j < d; ++j) {
+          LegItem li;
+          li.in = view;
+          li.in.ref = cur;
+          li.out_ref = refs[1 + (j % 2)];
+          li.leg = j;
+          li.out_dim = view.dim[j];
+          li.a_rows = view.dim[j];
+          li.A = W.L[j];
+          li.lda = chimax;
+          leg[j].push_back(li);
+          cur = li.out_ref;
+        }
+        for (int w = fv_only ? d - 1 : 0; w < d; ++w) {
+          const int bw_ = S.legs[lay[w]].bond;
+          GramLegItem g;
+          g.x = view;
+          g.x.ref = cur;
+          g.y_ref = cur;
+          g.leg = w;
+          g.partial = W.partial + (size_t)w * kLegSplits * cm2;
+          g.out = W.C + (size_t)w * cm2;
+          g.ldo = chimax;
+          for (int u = 0; u < PEPO_MAXLEG; ++u) g.sw[u] = (u < d && u != w) ? W.sqrtD[u] : nullptr;
+          gram.push_back(g);
+          RotItem r;
+          r.G = g.out;
+          r.Vt = W.L[w];
+          r.out = mptr(I.hat, msg_out(v, bw_));
+          r.ld = chimax;
+          r.chi_idx = chi_idx(bw_);
+          rot.push_back(r);
         }
       }
-      bw.env = stage(P, env);
-      for (int sl = 0; sl < 12; ++sl) {
-        bw.leg[sl] = stage(P, leg[sl]);
-        bw.gram[sl] = stage(P, gram[sl]);
-      }
+      bw.eig = stage(P, eig);
+      for (int j = 0; j < 4; ++j) bw.leg[j] = stage(P, leg[j]);
+      bw.gram = stage(P, gram);
+      bw.rot = stage(P, rot);
       out.push_back(bw);
     }
   };
@@ -879,11 +881,10 @@ void resolve_all(pepo_ctx* c) {
       }
     for (auto* ws : {&I.bwaves, &I.fwaves})
       for (auto& w : *ws) {
-        resolve(w.env, d);
-        for (int a = 0; a < 12; ++a) {
-          resolve(w.leg[a], d);
-          resolve(w.gram[a], d);
-        }
+        resolve(w.eig, d);
+        for (int a = 0; a < 4; ++a) resolve(w.leg[a], d);
+        resolve(w.gram, d);
+        resolve(w.rot, d);
       }
     for (int l = 0; l < 4; ++l) resolve(I.sl[l].items, d);
     resolve(I.msgs, d); resolve(I.sscal, d); resolve(I.escal, d); resolve(I.bethe, d);
@@ -1088,20 +1089,17 @@ pepo_status run_bp_waves(pepo_ctx* c, Inst& I, std::vector<BpWave>& waves) {
   cudaStream_t s = c->stream;
   const int chimax = I.cfg.chi_max;
   for (auto& w : waves) {
-    LAUNCH_T(K_ENV, nullptr, w.env.n, launch_env_factor(w.env.d, w.env.n, chimax, c->d_ival, I.cfg.pinv_rel, s));
-    for (int a = 0; a < 12; ++a) {
-      if (w.leg[a].n > 0) {
-        int gx = std::max(8, 2 * 152 * 4 / std::max(1, w.leg[a].n));
-        LAUNCH_T(K_LEG, hitems(c, w.leg[a]), w.leg[a].n,
-                 launch_leg_contract<T>(w.leg[a].d, w.leg[a].n, gx, chimax, c->d_ptrs, c->d_ival, s));
-      }
-      if (w.gram[a].n > 0) {
-        LAUNCH_T(K_GRAM_LEG, hitems(c, w.gram[a]), w.gram[a].n,
-                 launch_gram_leg<T>(w.gram[a].d, w.gram[a].n, kLegSplits, c->d_ptrs, c->d_ival, s));
-        LAUNCH_T(K_GRAM_LEG_RED, nullptr, w.gram[a].n,
-                 launch_gram_leg_reduce(w.gram[a].d, w.gram[a].n, chimax, kLegSplits, c->d_ival, s));
-      }
+    LAUNCH_T(K_ENV, nullptr, w.eig.n, launch_env_eig(w.eig.d, w.eig.n, c->d_ival, s));
+    for (int a = 0; a < 4; ++a) {
+      int gx = std::max(8, 2 * 152 * 4 / std::max(1, w.leg[a].n));
+      LAUNCH_T(K_LEG, hitems(c, w.leg[a]), w.leg[a].n,
+               launch_leg_contract<T>(w.leg[a].d, w.leg[a].n, gx, chimax, c->d_ptrs, c->d_ival, s));
     }
+    LAUNCH_T(K_GRAM_LEG, hitems(c, w.gram), w.gram.n,
+             launch_gram_leg<T>(w.gram.d, w.gram.n, kLegSplits, c->d_ptrs, c->d_ival, s));
+    LAUNCH_T(K_GRAM_LEG_RED, nullptr, w.gram.n,
+             launch_gram_leg_reduce(w.gram.d, w.gram.n, chimax, kLegSplits, c->d_ival, s));
+    LAUNCH_T(K_MSG, nullptr, w.rot.n, launch_rotate_back(w.rot.d, w.rot.n, chimax, c->d_ival, s));
   }
   return PEPO_OK;
 }
