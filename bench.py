@@ -116,49 +116,31 @@ def peaks():
 # --------------------------------------------------------------- CPU oracle
 def oracle_message_sample(w, seed=SEED):
     """Time one interior double-layer BP message (the dominant unit of the
-    step) with the oracle, on the workload's synthetic state at full chi."""
+    step) with the oracle, on the workload's own synthetic site tensor at full chi."""
     from oracle import bp as obp
     from oracle import gates as og
     from oracle.pepo import Network
-    from workloads.synthetic import saturated_state, site_legs
+    from workloads.synthetic import site_legs, site_tensor, spectrum
 
     Lx, Ly, chi = w["Lx"], w["Ly"], w["chi_max"]
     x, y = min(3, Lx - 2), min(4, Ly - 2)
     v = y * Lx + x
-    rng_state = saturated_state_one_site(Lx, Ly, chi, seed, v)
+    psi = site_tensor(Lx, Ly, chi, seed, v, np.float64)
+    lam = spectrum(chi)
     net = Network.__new__(Network)
     net.N = Lx * Ly
     legs = site_legs(Lx, Ly, v)
     names = ["U", "D", "L", "R"]
     net.legs = [[] for _ in range(net.N)]
     net.legs[v] = [(names[i], nb) for i, (nb, _) in enumerate(legs)]
-    psi = rng_state["psi"]
     paulis = np.stack(og.PAULI_BY_INDEX)                       # [p, s, s']
     net.O = [None] * net.N
     net.O[v] = np.tensordot(psi, paulis, axes=([psi.ndim - 1], [0]))  # Pauli -> 2x2 pair
-    M = {}
-    for (nb, b) in legs:
-        M[(nb, v)] = np.diag(rng_state["lam"]).astype(np.complex128)
+    del psi
+    M = {(nb, v): np.diag(lam).astype(np.complex128) for (nb, b) in legs}
     t0 = time.perf_counter()
     obp.double_message(net, v, 0, M)
     return time.perf_counter() - t0
-
-
-def saturated_state_one_site(Lx, Ly, chi, seed, v):
-    from workloads.synthetic import saturated_state
-    st = saturated_state(Lx, Ly, 1, seed=seed)   # cheap call only to mirror the recipe
-    del st
-    rng = np.random.default_rng(seed + 1000 + v)
-    lam = np.exp(-0.06 * np.arange(chi))
-    lam /= np.linalg.norm(lam)
-    shape = (chi,) * 4 + (4,)
-    psi = rng.standard_normal(shape)
-    sq = np.sqrt(lam)
-    for k in range(4):
-        sh = [1] * 5
-        sh[k] = chi
-        psi *= sq.reshape(sh)
-    return {"psi": psi, "lam": lam}
 
 
 def extrapolate_step(t_msg, w, sweeps):
@@ -174,22 +156,43 @@ def extrapolate_step(t_msg, w, sweeps):
 
 
 # ---------------------------------------------------------------- GPU arm
+def upload_state(eng, w, seed):
+    """Seeded synthetic saturated state, generated site by site on host threads
+    and uploaded through pepo_set_bonds / pepo_set_site (FP32)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from workloads.synthetic import bond_data, site_tensor
+    Lx, Ly, chi = w["Lx"], w["Ly"], w["chi_max"]
+    bd = bond_data(Lx, Ly, chi)
+    eng.set_bonds(0, bd["chi"], bd["lam"], bd["msgs"])
+    total = 0
+    n = Lx * Ly
+    window = 6   # sites generated ahead of the upload (bounded host memory)
+    with ThreadPoolExecutor(max_workers=window) as ex:
+        futs = {}
+        for v in range(min(window, n)):
+            futs[v] = ex.submit(site_tensor, Lx, Ly, chi, seed, v, np.float32)
+        for v in range(n):
+            t = futs.pop(v).result()
+            if v + window < n:
+                futs[v + window] = ex.submit(site_tensor, Lx, Ly, chi, seed, v + window, np.float32)
+            eng.set_site(0, v, t)
+            total += t.nbytes
+            del t
+    return total
+
+
 def run_gpu(args, rank, world, local):
     import torch
     import paper_2606_30985_gb300 as pkg
-    from workloads.synthetic import saturated_state
 
     torch.cuda.set_device(local)
     w = workload(args)
     cfg = pkg.Config(**{k: v for k, v in w.items()})
     eng = pkg.Engine(cfg, device="cuda:%d" % local)
-    st = saturated_state(w["Lx"], w["Ly"], w["chi_max"], seed=SEED + rank, dtype=np.float32)
     t_up = time.perf_counter()
-    eng.set_state(0, st["sites"], st["chi"], st["lam"], st["msgs"])
+    state_bytes = upload_state(eng, w, SEED + rank)
     torch.cuda.synchronize()
     upload_s = time.perf_counter() - t_up
-    state_bytes = sum(s.size for s in st["sites"]) * 4
-    del st
 
     def one_step():
         eng.trotter_step(1)

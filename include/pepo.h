@@ -168,6 +168,20 @@ pepo_status pepo_get_site(pepo_ctx* ctx, int inst, int site, double* out, size_t
 pepo_status pepo_set_state(pepo_ctx* ctx, int inst, const double* sites, size_t count,
                            const int* chi, const double* lam, const double* msgs);
 
+/* Set every bond's chi, lambda and both directed messages of one instance
+ * (formats as in pepo_set_state).  Call before pepo_set_site when the bond
+ * dimensions change.  Synchronises the stream. */
+pepo_status pepo_set_bonds(pepo_ctx* ctx, int inst, const int* chi, const double* lam,
+                           const double* msgs);
+
+/* Overwrite one site tensor from host data in the canonical layout; dtype 0 =
+ * float, 1 = double; count must equal 4 * prod(live chi of its legs).  The data
+ * is staged in a scratch slab and permuted into the stored layout on the device
+ * (the paper's tensor permutation, Sec. 4.1).  Resets the site's log-scale.
+ * Synchronises the stream. */
+pepo_status pepo_set_site(pepo_ctx* ctx, int inst, int site, const void* data, int dtype,
+                          size_t count);
+
 /* Copy one directed message (chi x chi, row-major) to the host. */
 pepo_status pepo_get_message(pepo_ctx* ctx, int inst, int bond, int dir, double* out,
                              int* chi_out);

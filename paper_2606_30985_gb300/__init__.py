@@ -51,7 +51,7 @@ class _Diag(ctypes.Structure):
 
 EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trotter_step",
            "pepo_bp_converge", "pepo_correlator", "pepo_get_spectrum", "pepo_get_site",
-           "pepo_set_state", "pepo_get_message", "pepo_num_bonds", "pepo_set_timing",
+           "pepo_set_state", "pepo_set_bonds", "pepo_set_site", "pepo_get_message", "pepo_num_bonds", "pepo_set_timing",
            "pepo_timing_classes", "pepo_timing_class_name", "pepo_get_timing", "pepo_reset_timing",
            "pepo_launch_count", "pepo_last_error", "pepo_destroy"]
 
@@ -87,6 +87,10 @@ def load_library(path=LIB_PATH):
     lib.pepo_set_state.argtypes = [P, I, ctypes.POINTER(D), S, ctypes.POINTER(I), ctypes.POINTER(D),
                                    ctypes.POINTER(D)]
     lib.pepo_set_state.restype = I
+    lib.pepo_set_bonds.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D)]
+    lib.pepo_set_bonds.restype = I
+    lib.pepo_set_site.argtypes = [P, I, I, P, I, S]
+    lib.pepo_set_site.restype = I
     lib.pepo_get_message.argtypes = [P, I, I, I, ctypes.POINTER(D), ctypes.POINTER(I)]
     lib.pepo_get_message.restype = I
     lib.pepo_num_bonds.argtypes = [P, I]
@@ -304,6 +308,26 @@ class Engine:
                                             chi.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                             lam.ctypes.data_as(dp), msgs.ctypes.data_as(dp)),
                     "pepo_set_state")
+
+    def set_bonds(self, inst, chi, lam, msgs):
+        chi = np.ascontiguousarray(np.asarray(chi, dtype=np.int32))
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
+        msgs = np.ascontiguousarray(np.asarray(msgs, dtype=np.float64))
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.pepo_set_bonds(self.ctx, inst, chi.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                            lam.ctypes.data_as(dp), msgs.ctypes.data_as(dp)),
+                    "pepo_set_bonds")
+
+    def set_site(self, inst, v, tensor):
+        """tensor: canonical layout [legs..., 4], float32 or float64."""
+        t = np.ascontiguousarray(tensor)
+        if t.dtype == np.float32:
+            dt = 0
+        else:
+            t = np.ascontiguousarray(t, dtype=np.float64)
+            dt = 1
+        self._check(self.lib.pepo_set_site(self.ctx, inst, v, ctypes.c_void_p(t.ctypes.data), dt, t.size),
+                    "pepo_set_site")
 
     def run(self, nsteps, measure_every=1):
         """Evolve nsteps, measuring C(t) (BP + correlator) every `measure_every` steps."""

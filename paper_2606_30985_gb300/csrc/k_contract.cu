@@ -1,28 +1,30 @@
 // Register-tiled SIMT contractions of the BP and bond-update hot loop.
 //
 //   k_leg_contract  out[o, i, q] = sum_j A[i, j] in[o, j, q] on one layout leg
-//                   (absorbing a message factor into a site tensor: Sec. 2.4
-//                   step 1, and the products of Eq. 11)
-//   k_gram_leg      out[i, i'] = sum_{o, q} X[o, i, q] Y[o, i', q]: a site tensor
-//                   contracted with itself over every index but one leg, the
-//                   Pauli leg traced (one double-layer message, Eq. 11)
+//                   (absorbing a message factor or eigenbasis into a site
+//                   tensor: Sec. 2.4 step 1 and the products of Eq. 11)
+//   k_gram_leg      out[i, i'] = sum_{o, q} w(o,q)^2 X[o, i, q] Y[o, i', q]: a site
+//                   tensor contracted with itself over every index but one leg,
+//                   the Pauli leg traced, optionally weighted (one double-layer
+//                   message, Eq. 11)
 //
-// Both are GEMMs with one short dimension (chi <= 128).  A block owns a
-// 128 x TC output tile; each of its 256 threads owns an 8 x MC register tile
-// whose rows / columns are split in two halves 64 apart, so every 16-byte
-// shared-memory load of a warp hits distinct banks.  A[i, j] is staged
-// transposed in shared memory once per block and reused for every tile of the
-// item.  FP32 storage accumulates in FP32 over the K <= 128 of a leg
-// contraction; the Gram's long K is flushed into FP64 every 256 terms.
+// Both are GEMMs with one short dimension (chi <= 128).  The tile edge TL is
+// 64 or 128 (chosen from chi_max); a block of 256 threads owns a TL x TL
+// output tile, each thread an (TL/16) x (TL/16) register tile.  With TL = 128
+// the 8 rows / columns of a thread are split in two halves 64 apart so the
+// 16-byte shared-memory loads of a warp hit distinct banks.  The leg
+// contraction stages A transposed in shared memory once per block.  FP32
+// storage accumulates the Gram's long sums in FP32 runs flushed into FP64
+// every 256 terms.
 #include "kernels.h"
 
 namespace pepo {
 
-template <typename T> struct LCfg;
-template <> struct LCfg<float> { static constexpr int TC = 128, MC = 8; };
-template <> struct LCfg<double> { static constexpr int TC = 64, MC = 4; };
-
-__device__ __forceinline__ int half_split(int t, int r) { return (r < 4) ? t * 4 + r : 64 + t * 4 + (r - 4); }
+template <int TL>
+__device__ __forceinline__ int tile_idx(int t, int r) {
+  if constexpr (TL == 128) return (r < 4) ? t * 4 + r : 64 + t * 4 + (r - 4);
+  else return t * 4 + r;
+}
 
 template <typename T>
 __device__ __forceinline__ void lds4(const T* p, T* v) {
@@ -36,16 +38,32 @@ __device__ __forceinline__ void lds4(const T* p, T* v) {
   }
 }
 
+template <int TL, typename T>
+__device__ __forceinline__ void ld_frag(const T* row, int t, T* v) {
+  lds4(row + t * 4, v);
+  if constexpr (TL == 128) lds4(row + 64 + t * 4, v + 4);
+}
+
 __device__ inline void load_dims4(const TView& v, const int* ival, int* d) {
 #pragma unroll
   for (int k = 0; k < PEPO_MAXLEG; ++k) d[k] = (k < v.nlegs) ? ival[v.dim[k]] : 1;
 }
 
 // ============================================================ leg contraction
-template <typename T>
+// Block tile: TL rows (output index i) x TC columns (o, q); TC = TL for FP32,
+// TL / 2 for FP64 (shared-memory bound).
+template <typename T, int TL>
+struct LegCfg {
+  static constexpr int TC = sizeof(T) == 4 ? TL : TL / 2;
+  static constexpr int MR = TL / 16;
+  static constexpr int MC = TC / 16;
+};
+
+template <typename T, int TL>
 __global__ void __launch_bounds__(256)
 k_leg_contract(const LegItem* __restrict__ items, void* const* ptrs, const int* __restrict__ ival) {
-  constexpr int TR = 128, TC = LCfg<T>::TC, MC = LCfg<T>::MC;
+  using C = LegCfg<T, TL>;
+  constexpr int TC = C::TC, MR = C::MR, MC = C::MC;
   const LegItem it = items[blockIdx.y];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int d[PEPO_MAXLEG];
@@ -56,10 +74,10 @@ k_leg_contract(const LegItem* __restrict__ items, void* const* ptrs, const int* 
   long long O = 1, Q = 4;
   for (int i = 0; i < k; ++i) O *= d[i];
   for (int i = k + 1; i < it.in.nlegs; ++i) Q *= d[i];
-  T* At = reinterpret_cast<T*>(smem_raw);     // [Jin][TR]
-  T* Bs = At + Jin * TR;                      // [Jin][TC]
-  for (int e = threadIdx.x; e < Jin * TR; e += blockDim.x) {
-    int j = e / TR, i = e - j * TR;
+  T* At = reinterpret_cast<T*>(smem_raw);     // [Jin][TL]
+  T* Bs = At + Jin * TL;                      // [Jin][TC]
+  for (int e = threadIdx.x; e < Jin * TL; e += blockDim.x) {
+    int j = e / TL, i = e - j * TL;
     At[e] = (i < Jout) ? (T)it.A[(long long)i * it.lda + j] : T(0);
   }
   long long G, nqb, units;
@@ -85,33 +103,31 @@ k_leg_contract(const LegItem* __restrict__ items, void* const* ptrs, const int* 
       Bs[e] = v;
     }
     __syncthreads();
-    T acc[8][MC];
+    T acc[MR][MC];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+    for (int r = 0; r < MR; ++r)
 #pragma unroll
       for (int c = 0; c < MC; ++c) acc[r][c] = T(0);
 #pragma unroll 2
     for (int j = 0; j < Jin; ++j) {
-      T a[8], b[MC];
-      lds4(At + j * TR + ty * 4, a);
-      lds4(At + j * TR + 64 + ty * 4, a + 4);
-      lds4(Bs + j * TC + tx * 4, b);
-      if constexpr (MC == 8) lds4(Bs + j * TC + 64 + tx * 4, b + 4);
+      T a[MR], b[MC];
+      ld_frag<TL>(At + j * TL, ty, a);
+      ld_frag<TC>(Bs + j * TC, tx, b);
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
+      for (int r = 0; r < MR; ++r)
 #pragma unroll
         for (int c = 0; c < MC; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
     }
 #pragma unroll
     for (int c = 0; c < MC; ++c) {
-      const int col = (MC == 8) ? half_split(tx, c) : tx * 4 + c;
+      const int col = tile_idx<TC>(tx, c);
       if (col >= width) continue;
       const long long o = (G == 1) ? o0 : o0 + col / Q;
       const long long q = (G == 1) ? q0 + col : col % Q;
       T* dst = out + o * Jout * Q + q;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int i = half_split(ty, r);
+      for (int r = 0; r < MR; ++r) {
+        const int i = tile_idx<TL>(ty, r);
         if (i < Jout) dst[(long long)i * Q] = acc[r][c];
       }
     }
@@ -119,22 +135,29 @@ k_leg_contract(const LegItem* __restrict__ items, void* const* ptrs, const int* 
   }
 }
 
+template <typename T, int TL>
+cudaError_t launch_leg_tl(const LegItem* items, int n_items, int grid_x, int chimax, void* const* ptrs,
+                          const int* ival, cudaStream_t s) {
+  size_t smem = sizeof(T) * (size_t)chimax * (TL + LegCfg<T, TL>::TC);
+  cudaError_t e = cudaFuncSetAttribute(k_leg_contract<T, TL>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_leg_contract<T, TL><<<dim3(grid_x, n_items), 256, smem, s>>>(items, ptrs, ival);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_leg_contract(const LegItem* items, int n_items, int grid_x, int chimax,
                                 void* const* ptrs, const int* ival, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  size_t smem = sizeof(T) * (size_t)chimax * (128 + LCfg<T>::TC);
-  cudaError_t e = cudaFuncSetAttribute(k_leg_contract<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  k_leg_contract<T><<<dim3(grid_x, n_items), 256, smem, s>>>(items, ptrs, ival);
-  return cudaGetLastError();
+  if (chimax <= 64) return launch_leg_tl<T, 64>(items, n_items, grid_x, chimax, ptrs, ival, s);
+  return launch_leg_tl<T, 128>(items, n_items, grid_x, chimax, ptrs, ival, s);
 }
 
 // ============================================================ Gram (free leg)
-// X, Y as [O][F][Q], F <= 128: one 128 x 128 tile.  A chunk is 16 (o, q)
-// pairs (one o and 16 consecutive q when Q >= 16, else floor(16/Q) o's).
-constexpr int GL_BK = 16;
+// X, Y as [O][F][Q], F <= TL.  A chunk is 32 (o, q) pairs: one o and 32
+// consecutive q when Q >= 32, else floor(32 / Q) consecutive o with all q.
+constexpr int GL_BK = 32;
 constexpr int GL_FLUSH = 256;
 
 // product of the square-root weights sw[u][j_u] over layout legs u in [lo, hi)
@@ -149,10 +172,11 @@ __device__ inline double leg_weight(const GramLegItem& it, const int* d, int lo,
   return w;
 }
 
-template <typename T>
+template <typename T, int TL>
 __global__ void __launch_bounds__(256)
 k_gram_leg(const GramLegItem* __restrict__ items, int splits_max, void* const* ptrs,
            const int* __restrict__ ival) {
+  constexpr int MR = TL / 16;
   const GramLegItem it = items[blockIdx.y];
   int d[PEPO_MAXLEG];
   load_dims4(it.x, ival, d);
@@ -171,106 +195,103 @@ k_gram_leg(const GramLegItem* __restrict__ items, int splits_max, void* const* p
   const bool same = it.x.ref == it.y_ref;
   bool weighted = false;
   for (int u = 0; u < it.x.nlegs; ++u) weighted |= (u != k && it.sw[u] != nullptr);
-  __shared__ __align__(16) T Xs[GL_BK][128];
-  __shared__ __align__(16) T Ys[GL_BK][128];
+  __shared__ __align__(16) T Xs[GL_BK][TL];
+  __shared__ __align__(16) T Ys[GL_BK][TL];
+  __shared__ double wk[GL_BK];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool wideQ = Q >= GL_BK;
   const long long qpc = wideQ ? (Q + GL_BK - 1) / GL_BK : 0;
+  const int Qi = wideQ ? GL_BK : (int)Q;
   const int opc = wideQ ? 1 : (int)(GL_BK / Q);
-  // FP32 storage keeps an FP64 shadow of the accumulators, flushed every
-  // GL_FLUSH terms; FP64 storage accumulates directly
-  constexpr int NS = sizeof(T) == 4 ? 8 : 1;
-  T acc[8][8];
-  double acc64[NS][NS * 8 / NS];
+  const int rows = wideQ ? GL_BK : opc * Qi;        // live rows of a chunk
+  T* Yt = same ? &Xs[0][0] : &Ys[0][0];
+  constexpr int NS = sizeof(T) == 4 ? MR : 1;
+  T acc[MR][MR];
+  double acc64[NS][MR];
 #pragma unroll
-  for (int r = 0; r < 8; ++r)
+  for (int r = 0; r < MR; ++r)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c] = T(0);
+    for (int c = 0; c < MR; ++c) acc[r][c] = T(0);
 #pragma unroll
   for (int r = 0; r < NS; ++r)
 #pragma unroll
-    for (int c = 0; c < NS * 8 / NS; ++c) acc64[r][c] = 0.0;
+    for (int c = 0; c < MR; ++c) acc64[r][c] = 0.0;
+  // rows beyond `rows` and columns beyond F stay zero for the whole block
+  for (int e = threadIdx.x; e < GL_BK * TL; e += blockDim.x) {
+    (&Xs[0][0])[e] = T(0);
+    (&Ys[0][0])[e] = T(0);
+  }
   int run = 0;
   for (long long cch = c0; cch < c1; ++cch) {
     long long o0, q0;
     if (wideQ) { o0 = cch / qpc; q0 = (cch - o0 * qpc) * GL_BK; }
     else { o0 = cch * opc; q0 = 0; }
-    // zero the tile, then fill the live part
-    for (int e = threadIdx.x; e < GL_BK * 128; e += blockDim.x) {
-      (&Xs[0][0])[e] = T(0);
-      if (!same) (&Ys[0][0])[e] = T(0);
+    __syncthreads();   // previous chunk consumed
+    if (weighted && threadIdx.x < rows) {
+      const int kk = threadIdx.x;
+      long long o, q;
+      if (wideQ) { o = o0; q = q0 + kk; }
+      else { o = o0 + kk / Qi; q = kk % Qi; }
+      double w = 0.0;
+      if (q < Q && o < O) w = leg_weight(it, d, 0, k, o) * leg_weight(it, d, k + 1, it.x.nlegs, q >> 2);
+      wk[kk] = w;
     }
-    __syncthreads();
-    if (wideQ) {
-      const double wo = weighted ? leg_weight(it, d, 0, k, o0) : 1.0;
-      for (int e = threadIdx.x; e < GL_BK * F; e += blockDim.x) {
-        int f = e / GL_BK, kk = e - f * GL_BK;
-        long long q = q0 + kk;
-        if (q < Q) {
-          long long idx = (o0 * F + f) * Q + q;
-          if (weighted) {
-            const T w = (T)(wo * leg_weight(it, d, k + 1, it.x.nlegs, q >> 2));
-            Xs[kk][f] = X[idx] * w;
-            if (!same) Ys[kk][f] = Y[idx] * w;
-          } else {
-            Xs[kk][f] = X[idx];
-            if (!same) Ys[kk][f] = Y[idx];
-          }
-        }
-      }
-    } else {
-      const int Qi = (int)Q;
-      for (int e = threadIdx.x; e < opc * F * Qi; e += blockDim.x) {
+    if (weighted) __syncthreads();
+    for (int e = threadIdx.x; e < rows * F; e += blockDim.x) {
+      int kk, f;
+      long long o, q;
+      if (wideQ) { f = e / GL_BK; kk = e - f * GL_BK; o = o0; q = q0 + kk; }
+      else {
         int qq = e % Qi, rest = e / Qi;
-        int f = rest % F, ol = rest / F;
-        long long o = o0 + ol;
-        if (o < O) {
-          long long idx = (o * F + f) * Q + qq;
-          if (weighted) {
-            const T w = (T)(leg_weight(it, d, 0, k, o) * leg_weight(it, d, k + 1, it.x.nlegs, qq >> 2));
-            Xs[ol * Qi + qq][f] = X[idx] * w;
-            if (!same) Ys[ol * Qi + qq][f] = Y[idx] * w;
-          } else {
-            Xs[ol * Qi + qq][f] = X[idx];
-            if (!same) Ys[ol * Qi + qq][f] = Y[idx];
-          }
+        f = rest % F;
+        int ol = rest / F;
+        kk = ol * Qi + qq;
+        o = o0 + ol; q = qq;
+      }
+      T xv = T(0), yv = T(0);
+      if (q < Q && o < O) {
+        long long idx = (o * F + f) * Q + q;
+        xv = X[idx];
+        if (!same) yv = Y[idx];
+        if (weighted) {
+          const T w = (T)wk[kk];
+          xv *= w;
+          yv *= w;
         }
       }
+      Xs[kk][f] = xv;
+      if (!same) Ys[kk][f] = yv;
     }
     __syncthreads();
-    const T* Yb = same ? &Xs[0][0] : &Ys[0][0];
-#pragma unroll
+#pragma unroll 4
     for (int kk = 0; kk < GL_BK; ++kk) {
-      T a[8], b[8];
-      lds4(&Xs[kk][0] + ty * 4, a);
-      lds4(&Xs[kk][0] + 64 + ty * 4, a + 4);
-      lds4(Yb + kk * 128 + tx * 4, b);
-      lds4(Yb + kk * 128 + 64 + tx * 4, b + 4);
+      T a[MR], b[MR];
+      ld_frag<TL>(&Xs[kk][0], ty, a);
+      ld_frag<TL>(Yt + kk * TL, tx, b);
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
+      for (int r = 0; r < MR; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        for (int c = 0; c < MR; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
     }
-    __syncthreads();
     if constexpr (sizeof(T) == 4) {
       run += GL_BK;
       if (run >= GL_FLUSH) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < MR; ++r)
 #pragma unroll
-          for (int c = 0; c < 8; ++c) { acc64[r % NS][c] += (double)acc[r][c]; acc[r][c] = T(0); }
+          for (int c = 0; c < MR; ++c) { acc64[r % NS][c] += (double)acc[r][c]; acc[r][c] = T(0); }
         run = 0;
       }
     }
   }
   double* P = it.partial + (long long)s * F * F;
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int fi = half_split(ty, r);
+  for (int r = 0; r < MR; ++r) {
+    const int fi = tile_idx<TL>(ty, r);
     if (fi >= F) continue;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int fj = half_split(tx, c);
+    for (int c = 0; c < MR; ++c) {
+      const int fj = tile_idx<TL>(tx, c);
       if (fj < F) {
         double v = (double)acc[r][c];
         if constexpr (sizeof(T) == 4) v += acc64[r % NS][c];
@@ -300,10 +321,13 @@ __global__ void k_gram_leg_reduce(const GramLegItem* __restrict__ items, int spl
 }
 
 template <typename T>
-cudaError_t launch_gram_leg(const GramLegItem* items, int n_items, int splits_max,
+cudaError_t launch_gram_leg(const GramLegItem* items, int n_items, int splits_max, int chimax,
                             void* const* ptrs, const int* ival, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  k_gram_leg<T><<<dim3(splits_max, n_items), 256, 0, s>>>(items, splits_max, ptrs, ival);
+  if (chimax <= 64)
+    k_gram_leg<T, 64><<<dim3(splits_max, n_items), 256, 0, s>>>(items, splits_max, ptrs, ival);
+  else
+    k_gram_leg<T, 128><<<dim3(splits_max, n_items), 256, 0, s>>>(items, splits_max, ptrs, ival);
   return cudaGetLastError();
 }
 
@@ -315,13 +339,56 @@ cudaError_t launch_gram_leg_reduce(const GramLegItem* items, int n_items, int ch
   return cudaGetLastError();
 }
 
+// ==================================================================== permute
+// Canonical site layout -> stored layout (or back): out[perm position] = in[i].
+// perm[k] = canonical leg index at layout position k; dims in canonical order.
+template <typename T>
+__global__ void k_permute(const T* __restrict__ in, T* __restrict__ out, int nlegs, int4 dims,
+                          int4 perm, int to_layout) {
+  const int dc[4] = {dims.x, dims.y, dims.z, dims.w};
+  const int pm[4] = {perm.x, perm.y, perm.z, perm.w};
+  long long n = 4;
+  for (int k = 0; k < nlegs; ++k) n *= dc[k];
+  // strides of the canonical legs inside the layout
+  long long sl[4] = {0, 0, 0, 0};
+  long long st = 4;
+  for (int k = nlegs - 1; k >= 0; --k) { sl[pm[k]] = st; st *= dc[pm[k]]; }
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long rem = e >> 2, dst = e & 3;
+    for (int k = nlegs - 1; k >= 0; --k) {
+      long long j = rem % dc[k];
+      rem /= dc[k];
+      dst += j * sl[k];
+    }
+    if (to_layout) out[dst] = in[e];
+    else out[e] = in[dst];
+  }
+}
+
+template <typename T>
+cudaError_t launch_permute(const void* in, void* out, int nlegs, const int* dims_canon, const int* perm,
+                           int to_layout, cudaStream_t s) {
+  int4 d = make_int4(nlegs > 0 ? dims_canon[0] : 1, nlegs > 1 ? dims_canon[1] : 1,
+                     nlegs > 2 ? dims_canon[2] : 1, nlegs > 3 ? dims_canon[3] : 1);
+  int4 p = make_int4(nlegs > 0 ? perm[0] : 0, nlegs > 1 ? perm[1] : 0, nlegs > 2 ? perm[2] : 0,
+                     nlegs > 3 ? perm[3] : 0);
+  k_permute<T><<<1024, 256, 0, s>>>(static_cast<const T*>(in), static_cast<T*>(out), nlegs, d, p,
+                                    to_layout);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_leg_contract<float>(const LegItem*, int, int, int, void* const*,
                                                 const int*, cudaStream_t);
 template cudaError_t launch_leg_contract<double>(const LegItem*, int, int, int, void* const*,
                                                  const int*, cudaStream_t);
-template cudaError_t launch_gram_leg<float>(const GramLegItem*, int, int, void* const*, const int*,
-                                            cudaStream_t);
-template cudaError_t launch_gram_leg<double>(const GramLegItem*, int, int, void* const*,
+template cudaError_t launch_gram_leg<float>(const GramLegItem*, int, int, int, void* const*,
+                                            const int*, cudaStream_t);
+template cudaError_t launch_gram_leg<double>(const GramLegItem*, int, int, int, void* const*,
                                              const int*, cudaStream_t);
+template cudaError_t launch_permute<float>(const void*, void*, int, const int*, const int*, int,
+                                           cudaStream_t);
+template cudaError_t launch_permute<double>(const void*, void*, int, const int*, const int*, int,
+                                            cudaStream_t);
 
 }  // namespace pepo

@@ -17,8 +17,12 @@ cudaError_t launch_gram_rows(const GramRowsItem* items, int n_items, int tiles_m
 cudaError_t launch_gram_rows_reduce(const GramRowsItem* items, int n_items, int fmax,
                                     int splits_max, int sym, const int* ival, cudaStream_t s);
 template <typename T>
-cudaError_t launch_gram_leg(const GramLegItem* items, int n_items, int splits_max,
+cudaError_t launch_gram_leg(const GramLegItem* items, int n_items, int splits_max, int chimax,
                             void* const* ptrs, const int* ival, cudaStream_t s);
+// canonical <-> stored site layout (perm[k] = canonical leg at layout position k)
+template <typename T>
+cudaError_t launch_permute(const void* in, void* out, int nlegs, const int* dims_canon, const int* perm,
+                           int to_layout, cudaStream_t s);
 cudaError_t launch_gram_leg_reduce(const GramLegItem* items, int n_items, int chimax,
                                    int splits_max, const int* ival, cudaStream_t s);
 template <typename T>

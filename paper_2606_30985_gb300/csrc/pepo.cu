@@ -137,6 +137,7 @@ struct Inst {
   int last_sweeps = 0, last_sweeps1 = 0;
   double last_delta = 0, last_delta1 = 0;
   int cap[5] = {0, 0, 0, 0, 0};   // in-flight sites per degree class
+  int scratch_ref[5] = {-1, -1, -1, -1, -1};   // one scratch slab per class (uploads)
 };
 
 }  // namespace
@@ -372,6 +373,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
       sc[d].refs.push_back(P.new_ptr(p));
     }
     maxslots += I.cap[d];
+    if (!sc[d].refs.empty()) I.scratch_ref[d] = sc[d].refs[0];
   }
   // ---- per-slot workspaces (gate update and BP)
   std::vector<SlotWS> slots(maxslots);
@@ -1096,7 +1098,7 @@ pepo_status run_bp_waves(pepo_ctx* c, Inst& I, std::vector<BpWave>& waves) {
                launch_leg_contract<T>(w.leg[a].d, w.leg[a].n, gx, chimax, c->d_ptrs, c->d_ival, s));
     }
     LAUNCH_T(K_GRAM_LEG, hitems(c, w.gram), w.gram.n,
-             launch_gram_leg<T>(w.gram.d, w.gram.n, kLegSplits, c->d_ptrs, c->d_ival, s));
+             launch_gram_leg<T>(w.gram.d, w.gram.n, kLegSplits, chimax, c->d_ptrs, c->d_ival, s));
     LAUNCH_T(K_GRAM_LEG_RED, nullptr, w.gram.n,
              launch_gram_leg_reduce(w.gram.d, w.gram.n, chimax, kLegSplits, c->d_ival, s));
     LAUNCH_T(K_MSG, nullptr, w.rot.n, launch_rotate_back(w.rot.d, w.rot.n, chimax, c->d_ival, s));
@@ -1501,55 +1503,88 @@ pepo_status pepo_get_site(pepo_ctx* c, int inst, int site, double* out, size_t c
   return PEPO_OK;
 }
 
+pepo_status pepo_set_bonds(pepo_ctx* c, int inst, const int* chi, const double* lam, const double* msgs) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
+  Inst& I = c->inst[inst];
+  if (!chi || !lam || !msgs) return fail(c, PEPO_E_INVALID, "null argument");
+  const int chimax = I.cfg.chi_max;
+  for (int b = 0; b < I.nb; ++b)
+    if (chi[b] < 1 || chi[b] > chimax) return fail(c, PEPO_E_INVALID, "chi of bond %d out of range", b);
+  std::vector<int> chiv(chi, chi + I.nb);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+      cudaMemcpy(c->d_ival + I.chi0, chiv.data(), sizeof(int) * I.nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_ival + I.pend0, chiv.data(), sizeof(int) * I.nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(I.lam, lam, sizeof(double) * I.nb * chimax, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(I.msg, msgs, sizeof(double) * 2 * I.nb * chimax * chimax, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "bond upload");
+  return PEPO_OK;
+}
+
+pepo_status pepo_set_site(pepo_ctx* c, int inst, int site, const void* data, int dtype, size_t count) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
+  Inst& I = c->inst[inst];
+  if (site < 0 || site >= I.N || !data || (dtype != 0 && dtype != 1))
+    return fail(c, PEPO_E_INVALID, "bad site upload arguments");
+  const SiteG& S = I.sites[site];
+  std::vector<int> chi(I.nb);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+      cudaMemcpy(chi.data(), c->d_ival + I.chi0, sizeof(int) * I.nb, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "chi readback");
+  int dc[4] = {1, 1, 1, 1}, perm[4] = {0, 0, 0, 0};
+  size_t n = 4;
+  for (int k = 0; k < S.deg; ++k) { dc[k] = chi[S.legs[k].bond]; n *= dc[k]; }
+  if (count != n) return fail(c, PEPO_E_INVALID, "site %d needs %zu elements, got %zu", site, n, count);
+  std::vector<int> lay = boundary_layout(S);
+  for (int k = 0; k < S.deg; ++k) perm[k] = lay[k];
+  void* ptrs[2] = {nullptr, nullptr};
+  if (cudaMemcpy(&ptrs[0], c->d_ptrs + I.site_ref0 + site, sizeof(void*), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&ptrs[1], c->d_ptrs + I.scratch_ref[S.deg], sizeof(void*), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "pointer readback");
+  const size_t ts = c->tsize;
+  cudaError_t e;
+  if ((dtype == 0 && ts == 4) || (dtype == 1 && ts == 8)) {
+    e = cudaMemcpy(ptrs[1], data, ts * n, cudaMemcpyHostToDevice);
+  } else if (ts == 4) {
+    std::vector<float> f(n);
+    const double* src = static_cast<const double*>(data);
+    for (size_t i = 0; i < n; ++i) f[i] = (float)src[i];
+    e = cudaMemcpy(ptrs[1], f.data(), 4 * n, cudaMemcpyHostToDevice);
+  } else {
+    std::vector<double> f(n);
+    const float* src = static_cast<const float*>(data);
+    for (size_t i = 0; i < n; ++i) f[i] = src[i];
+    e = cudaMemcpy(ptrs[1], f.data(), 8 * n, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return fail(c, PEPO_E_CUDA, "site upload");
+  e = ts == 4 ? launch_permute<float>(ptrs[1], ptrs[0], S.deg, dc, perm, 1, c->stream)
+              : launch_permute<double>(ptrs[1], ptrs[0], S.deg, dc, perm, 1, c->stream);
+  c->launches++;
+  if (e != cudaSuccess || cudaMemsetAsync(I.sigma + site, 0, sizeof(double), c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "site permute");
+  return PEPO_OK;
+}
+
 pepo_status pepo_set_state(pepo_ctx* c, int inst, const double* sites, size_t count, const int* chi,
                            const double* lam, const double* msgs) {
   if (!c) return PEPO_E_INVALID;
   if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
   Inst& I = c->inst[inst];
-  if (!sites || !chi || !lam || !msgs) return fail(c, PEPO_E_INVALID, "null argument");
-  const int chimax = I.cfg.chi_max;
-  for (int b = 0; b < I.nb; ++b)
-    if (chi[b] < 1 || chi[b] > chimax) return fail(c, PEPO_E_INVALID, "chi of bond %d out of range", b);
-  // site pointers (the table may have been permuted by earlier steps)
-  std::vector<void*> ptrs(I.N);
-  if (cudaMemcpy(ptrs.data(), c->d_ptrs + I.site_ref0, sizeof(void*) * I.N, cudaMemcpyDeviceToHost) !=
-      cudaSuccess)
-    return fail(c, PEPO_E_CUDA, "pointer readback");
+  if (!sites) return fail(c, PEPO_E_INVALID, "null argument");
+  pepo_status st = pepo_set_bonds(c, inst, chi, lam, msgs);
+  if (st != PEPO_OK) return st;
   size_t off = 0;
   for (int v = 0; v < I.N; ++v) {
     const SiteG& S = I.sites[v];
-    std::vector<int> lay = boundary_layout(S);
-    std::vector<int> dl(S.deg), dc(S.deg);
     size_t n = 4;
-    for (int k = 0; k < S.deg; ++k) { dl[k] = chi[S.legs[lay[k]].bond]; dc[k] = chi[S.legs[k].bond]; n *= dc[k]; }
+    for (int k = 0; k < S.deg; ++k) n *= chi[S.legs[k].bond];
     if (off + n > count) return fail(c, PEPO_E_INVALID, "site data too short");
-    std::vector<size_t> sl;
-    layout_strides(dl, sl);
-    std::vector<double> buf(n);
-    std::vector<int> idx(S.deg, 0);
-    for (size_t e = 0; e < n / 4; ++e) {
-      size_t rem = e;
-      for (int k = S.deg - 1; k >= 0; --k) { idx[k] = (int)(rem % dc[k]); rem /= dc[k]; }
-      size_t dst = 0;
-      for (int k = 0; k < S.deg; ++k) dst += (size_t)idx[lay[k]] * sl[k];
-      for (int p = 0; p < 4; ++p) buf[dst + p] = sites[off + e * 4 + p];
-    }
+    st = pepo_set_site(c, inst, v, sites + off, 1, n);
+    if (st != PEPO_OK) return st;
     off += n;
-    cudaError_t e;
-    if (c->tsize == 8) e = cudaMemcpy(ptrs[v], buf.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
-    else {
-      std::vector<float> f(buf.begin(), buf.end());
-      e = cudaMemcpy(ptrs[v], f.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
-    }
-    if (e != cudaSuccess) return fail(c, PEPO_E_CUDA, "site upload");
   }
-  std::vector<int> chiv(chi, chi + I.nb);
-  if (cudaMemcpy(c->d_ival + I.chi0, chiv.data(), sizeof(int) * I.nb, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(c->d_ival + I.pend0, chiv.data(), sizeof(int) * I.nb, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(I.lam, lam, sizeof(double) * I.nb * chimax, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(I.msg, msgs, sizeof(double) * 2 * I.nb * chimax * chimax, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(I.sigma, 0, sizeof(double) * I.N) != cudaSuccess)
-    return fail(c, PEPO_E_CUDA, "state upload");
   return PEPO_OK;
 }
 

@@ -6,8 +6,13 @@ horizontal first (y * (Lx - 1) + x) then vertical (Ly * (Lx - 1) + y * Lx + x).
 Values: Gaussian entries, each bond leg weighted by sqrt(lam) with a
 geometrically decaying lam (the shape of a saturated Schmidt spectrum), the
 identity Pauli component weighted up; messages diag(lam) on both directions.
+Every site has its own seed (seed, site), so one site can be regenerated
+without the others.
 """
 import numpy as np
+
+DECAY = 0.06
+PAULI_WEIGHT = np.array([1.0, 0.5, 0.5, 0.5])
 
 
 def bond_list(Lx, Ly):
@@ -36,30 +41,36 @@ def site_legs(Lx, Ly, v):
     return legs
 
 
-def saturated_state(Lx, Ly, chi, seed=0, decay=0.06, dtype=np.float64):
-    rng = np.random.default_rng(seed)
-    nb = len(bond_list(Lx, Ly))
+def spectrum(chi, decay=DECAY):
     lam = np.exp(-decay * np.arange(chi))
-    lam = lam / np.linalg.norm(lam)
-    lams = np.zeros((nb, chi))
-    lams[:] = lam
-    sq = np.sqrt(lam)
-    pw = np.array([1.0, 0.5, 0.5, 0.5])
-    sites = []
-    for v in range(Lx * Ly):
-        legs = site_legs(Lx, Ly, v)
-        shape = tuple([chi] * len(legs)) + (4,)
-        t = rng.standard_normal(shape).astype(dtype)
-        for k in range(len(legs)):
-            sh = [1] * (len(legs) + 1)
-            sh[k] = chi
-            t *= sq.reshape(sh).astype(dtype)
-        t *= pw.astype(dtype)
-        t /= np.sqrt(np.mean(t.astype(np.float64) ** 2)) * np.sqrt(t.size) ** (1.0 / 3.0)
-        sites.append(t)
+    return lam / np.linalg.norm(lam)
+
+
+def site_tensor(Lx, Ly, chi, seed, v, dtype=np.float64, decay=DECAY):
+    legs = site_legs(Lx, Ly, v)
+    rng = np.random.default_rng([seed, v])
+    shape = tuple([chi] * len(legs)) + (4,)
+    t = rng.standard_normal(shape, dtype=np.float32 if dtype == np.float32 else np.float64)
+    sq = np.sqrt(spectrum(chi, decay)).astype(t.dtype)
+    for k in range(len(legs)):
+        sh = [1] * (len(legs) + 1)
+        sh[k] = chi
+        t *= sq.reshape(sh)
+    t *= PAULI_WEIGHT.astype(t.dtype)
+    return t
+
+
+def bond_data(Lx, Ly, chi, decay=DECAY):
+    nb = len(bond_list(Lx, Ly))
+    lam = spectrum(chi, decay)
+    lams = np.tile(lam, (nb, 1))
     msgs = np.zeros((nb, 2, chi, chi))
-    for b in range(nb):
-        msgs[b, 0] = np.diag(lam)
-        msgs[b, 1] = np.diag(lam)
-    chis = np.full(nb, chi, dtype=np.int32)
-    return dict(sites=sites, chi=chis, lam=lams, msgs=msgs)
+    msgs[:, 0] = np.diag(lam)
+    msgs[:, 1] = np.diag(lam)
+    return dict(chi=np.full(nb, chi, dtype=np.int32), lam=lams, msgs=msgs)
+
+
+def saturated_state(Lx, Ly, chi, seed=0, dtype=np.float64, decay=DECAY):
+    st = bond_data(Lx, Ly, chi, decay)
+    st["sites"] = [site_tensor(Lx, Ly, chi, seed, v, dtype, decay) for v in range(Lx * Ly)]
+    return st
