@@ -54,9 +54,14 @@ __device__ inline void load_dims4(const TView& v, const int* ival, int* d) {
 // TL / 2 for FP64 (shared-memory bound).
 template <typename T, int TL>
 struct LegCfg {
-  static constexpr int TC = sizeof(T) == 4 ? TL : TL / 2;
+  // column tile: TL, except FP64 with TL = 128 (64, to fit shared memory)
+  static constexpr int TC = (sizeof(T) == 8 && TL == 128) ? 64 : TL;
   static constexpr int MR = TL / 16;
   static constexpr int MC = TC / 16;
+  // fragment loads read columns t*4 .. t*4+3 (and +64 when the tile is 128)
+  static_assert(TL == 64 || TL == 128, "row tile must be 64 or 128");
+  static_assert(TC == 64 || TC == 128, "column tile must be 64 or 128");
+  static_assert(MR * 16 == TL && MC * 16 == TC, "16 x 16 threads cover the tile");
 };
 
 template <typename T, int TL>

@@ -38,8 +38,10 @@ __host__ __device__ inline int gram_rows_splits(long long K, int splits_max) {
   if (s < 1) s = 1;
   return (int)(s < splits_max ? s : splits_max);
 }
+// chunks of 32 (o, q) pairs: one o and 32 consecutive q when Q >= 32, else
+// floor(32 / Q) consecutive o with all q (k_gram_leg's GL_BK)
 __host__ __device__ inline long long gram_leg_chunks(long long O, long long Q) {
-  return Q >= 16 ? O * ((Q + 15) / 16) : (O + (16 / Q) - 1) / (16 / Q);
+  return Q >= 32 ? O * ((Q + 31) / 32) : (O + (32 / Q) - 1) / (32 / Q);
 }
 __host__ __device__ inline int gram_leg_splits(long long chunks, int splits_max) {
   long long s = (chunks + 31) / 32;
