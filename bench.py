@@ -21,7 +21,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(Lx=10, Ly=10, J=1.0, h=2.0, dt=0.05, order=2, obs=(3, 4), chi_max=100,
+WORKLOAD = dict(Lx=10, Ly=10, J=1.0, h=2.0, dt=0.05, order=2, obs=(3, 4), chi_max=100, qr_ratio_thresh=16.0,
                 bp_alpha=0.5, bp_tol=1e-5, bp_max_sweeps=100, precision="fp32")
 SEED = 0
 

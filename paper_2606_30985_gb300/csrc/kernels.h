@@ -32,6 +32,12 @@ template <typename T>
 cudaError_t launch_vec_contract(const VecItem* items, int n_items, int grid_x,
                                 void* const* ptrs, const int* ival, cudaStream_t s);
 
+// ---- k_mma.cu (FP32 storage, TF32x3 tensor-core arithmetic) -------------
+cudaError_t launch_leg_contract_tc(const LegItem* items, int n_items, int grid_x, void* const* ptrs,
+                                   const int* ival, cudaStream_t s);
+cudaError_t launch_gram_leg_tc(const GramLegItem* items, int n_items, int splits_max, void* const* ptrs,
+                               const int* ival, cudaStream_t s);
+
 // Split count shared by the Gram kernels and their reductions.
 __host__ __device__ inline int gram_rows_splits(long long K, int splits_max) {
   long long s = (K + 511) / 512;

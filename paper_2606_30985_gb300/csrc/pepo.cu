@@ -124,6 +124,7 @@ struct Inst {
   int* nsv = nullptr;
   // plan
   std::vector<GateWave> gwaves[4];
+  DArr<CoreItem> gcore[4];      // all bonds of a colour in one core launch
   std::vector<BpWave> bwaves;
   std::vector<BpWave> fwaves;   // leg-0-only waves for f_v
   SlLevel sl[4];                // levels 0..3 (0: copy items for one-leg sites)
@@ -395,9 +396,10 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
     w.partial = cv.take<double>(std::max(pg, pl));
     w.W = cv.take<double>((size_t)nmax * nmax);
   }
-  const int nbslots = maxslots;   // a wave never has more bonds than sites
-  std::vector<double*> corework(nbslots);
-  for (int k = 0; k < nbslots; ++k) corework[k] = cv.take<double>((size_t)4 * rmax * rmax);
+  size_t maxcol = 0;
+  for (int col = 0; col < 4; ++col) maxcol = std::max(maxcol, I.colours[col].size());
+  std::vector<double*> corework(std::max<size_t>(1, maxcol));
+  for (size_t k = 0; k < corework.size(); ++k) corework[k] = cv.take<double>((size_t)4 * rmax * rmax);
 
   // ---- gate tables
   {
@@ -429,11 +431,26 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
     I.gates = stage(P, g);
   }
 
+  // ---- per-site factor workspaces (live from the factorisation to the reconstruct)
+  struct SiteWS { double* C; double* T; int* perm; double* W; int branch_idx, kfac_idx, rankT_idx; };
+  std::vector<SiteWS> sws(I.N);
+  for (int v = 0; v < I.N; ++v) {
+    SiteWS& q = sws[v];
+    q.C = cv.take<double>((size_t)nmax * nmax);
+    q.T = cv.take<double>((size_t)4 * nmax * rmax);
+    q.perm = cv.take<int>(rmax);
+    q.W = cv.take<double>((size_t)nmax * nmax);
+    q.branch_idx = P.new_ival(0);
+    q.kfac_idx = P.new_ival(0);
+    q.rankT_idx = P.new_ival(0);
+  }
+
   // ---- gate-update waves
   const double rel_fac = (c->prec == PEPO_FP64) ? 1e-15 : 1e-13;
   const double rel_env = I.cfg.pinv_rel;
   for (int col = 0; col < 4; ++col) {
     const auto& bl = I.colours[col];
+    std::vector<CoreItem> core_all;
     size_t pos = 0;
     while (pos < bl.size()) {
       // greedy wave
@@ -457,7 +474,6 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
       std::vector<int> cpy_out;
       std::vector<SiteFacItem> fac;
       std::vector<GramRowsItem> gram;
-      std::vector<CoreItem> core;
       std::vector<ReconItem> recon;
       std::vector<int> pairs, moves;
       int cls_used[5] = {0, 0, 0, 0, 0};
@@ -532,25 +548,25 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
           for (int j = 0; j < nenv; ++j) cvv.dim[j] = W.rank_idx[j];
           SiteFacItem f;
           f.cv = cvv;
-          f.branch_idx = W.branch_idx;
-          f.kfac_idx = W.kfac_idx;
+          f.branch_idx = sws[v].branch_idx;
+          f.kfac_idx = sws[v].kfac_idx;
           f.rg_idx = I.grank0 + b;
           f.F = (side == 0 ? I.FA : I.FB) + (size_t)b * PEPO_RG * 16;
-          f.C = W.C;
+          f.C = sws[v].C;
           f.ldc = nmax;
-          f.T = W.T;
+          f.T = sws[v].T;
           f.ldt = rmax;
-          f.perm = W.perm;
-          f.rank_idx = W.rankT_idx;
+          f.perm = sws[v].perm;
+          f.rank_idx = sws[v].rankT_idx;
           f.rel = rel_fac;
           fac_index[side] = (int)fac.size();
           fac.push_back(f);
           GramRowsItem g;
           g.x = cvv;
           g.y_ref = cv_ref;
-          g.active = W.branch_idx;
+          g.active = sws[v].branch_idx;
           g.partial = W.partial;
-          g.out = W.C;
+          g.out = sws[v].C;
           g.ldo = nmax;
           gram.push_back(g);
           // reconstruct: input = site tensor (layout lay), output layout nlay
@@ -565,7 +581,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
             int pos_in = (int)(std::find(lay.begin(), lay.end(), canon) - lay.begin());
             rc.out_perm[kk] = pos_in;
           }
-          rc.W = W.W;
+          rc.W = sws[v].W;
           rc.ldw = nmax;
           rc.scale_sq = nullptr;
           recon.push_back(rc);
@@ -586,7 +602,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
         ci.perm1 = f1.perm; ci.perm2 = f2.perm;
         ci.FA = I.FA + (size_t)b * PEPO_RG * 16;
         ci.FB = I.FB + (size_t)b * PEPO_RG * 16;
-        ci.work = corework[wbi];
+        ci.work = corework[core_all.size()];
         ci.rmax = rmax;
         ci.W1 = const_cast<double*>(recon[fac_index[0]].W);   // recon items follow fac items
         ci.W2 = const_cast<double*>(recon[fac_index[1]].W);
@@ -602,7 +618,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
         ci.nsv = I.nsv + b;
         ci.flags = nullptr;   // patched
         ci.eps_cut = I.cfg.eps_cut;
-        core.push_back(ci);
+        core_all.push_back(ci);
         moves.push_back(chi_idx(b));
         moves.push_back(I.pend0 + b);
       }
@@ -612,7 +628,6 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
       gw.copy_out = stage(P, cpy_out);
       gw.fac = stage(P, fac);
       gw.gram = stage(P, gram);
-      gw.core = stage(P, core);
       gw.recon = stage(P, recon);
       gw.pairs = stage(P, pairs);
       gw.moves = stage(P, moves);
@@ -620,6 +635,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
       gw.nmoves = (int)moves.size() / 2;
       I.gwaves[col].push_back(gw);
     }
+    I.gcore[col] = stage(P, core_all);
   }
   (void)inst_id;
 
@@ -863,17 +879,17 @@ void finalize_items(pepo_ctx* c, Planner& P) {
       g[b].rank = c->d_ival + I.grank0 + b;
       g[b].flags = c->d_flags + i;
     }
-    for (int col = 0; col < 4; ++col)
-      for (auto& w : I.gwaves[col]) {
-        CoreItem* ci = reinterpret_cast<CoreItem*>(P.st.bytes.data() + w.core.off);
-        for (int k = 0; k < w.core.n; ++k) ci[k].flags = c->d_flags + i;
-      }
+    for (int col = 0; col < 4; ++col) {
+      CoreItem* ci = reinterpret_cast<CoreItem*>(P.st.bytes.data() + I.gcore[col].off);
+      for (int k = 0; k < I.gcore[col].n; ++k) ci[k].flags = c->d_flags + i;
+    }
   }
 }
 
 void resolve_all(pepo_ctx* c) {
   char* d = c->d_items;
   for (auto& I : c->inst) {
+    for (int col = 0; col < 4; ++col) resolve(I.gcore[col], d);
     for (int col = 0; col < 4; ++col)
       for (auto& w : I.gwaves[col]) {
         resolve(w.env, d);
@@ -1037,6 +1053,20 @@ void timing_harvest(pepo_ctx* c) {
   } while (0)
 #define LAUNCH_N(n, expr) LAUNCH_T(K_OTHER, nullptr, n, expr)
 
+// tensor-core split-precision kernels for the FP32-storage mixed mode
+template <typename T>
+cudaError_t leg_dispatch(pepo_ctx* c, const LegItem* items, int n, int gx, int chimax) {
+  if (sizeof(T) == 4 && (c->prec == PEPO_TF32X3 || c->prec == PEPO_BF16X3))
+    return launch_leg_contract_tc(items, n, gx, c->d_ptrs, c->d_ival, c->stream);
+  return launch_leg_contract<T>(items, n, gx, chimax, c->d_ptrs, c->d_ival, c->stream);
+}
+template <typename T>
+cudaError_t gram_leg_dispatch(pepo_ctx* c, const GramLegItem* items, int n, int chimax) {
+  if (sizeof(T) == 4 && (c->prec == PEPO_TF32X3 || c->prec == PEPO_BF16X3))
+    return launch_gram_leg_tc(items, n, kLegSplits, c->d_ptrs, c->d_ival, c->stream);
+  return launch_gram_leg<T>(items, n, kLegSplits, chimax, c->d_ptrs, c->d_ival, c->stream);
+}
+
 template <typename T>
 pepo_status run_gate_wave(pepo_ctx* c, Inst& I, GateWave& w) {
   cudaStream_t s = c->stream;
@@ -1049,7 +1079,7 @@ pepo_status run_gate_wave(pepo_ctx* c, Inst& I, GateWave& w) {
   LAUNCH_T(K_ENV, nullptr, w.env.n, launch_env_factor(w.env.d, w.env.n, chimax, c->d_ival, I.cfg.pinv_rel, s));
   LAUNCH_N(w.copy.n, launch_copy<T>(w.copy.d, w.copy_out.d, w.copy.n, 64, c->d_ptrs, c->d_ival, s));
   for (int r = 0; r < 3; ++r)
-    LAUNCH_T(K_LEG, hitems(c, w.leg[r]), w.leg[r].n, launch_leg_contract<T>(w.leg[r].d, w.leg[r].n, gx_leg, chimax, c->d_ptrs, c->d_ival, s));
+    LAUNCH_T(K_LEG, hitems(c, w.leg[r]), w.leg[r].n, leg_dispatch<T>(c, w.leg[r].d, w.leg[r].n, gx_leg, chimax));
   LAUNCH_N(w.fac.n, launch_branch(w.fac.d, w.fac.n, c->d_ival, I.cfg.qr_n_thresh, I.cfg.qr_ratio_thresh, s));
   {
     int nt = ceil_div(nmax, 64);
@@ -1074,7 +1104,15 @@ pepo_status run_gate_wave(pepo_ctx* c, Inst& I, GateWave& w) {
   }
   LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_form(w.fac.d, w.fac.n, 16, c->d_ival, s));
   LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_factor(w.fac.d, w.fac.n, rmax, nmax, c->d_ival, s));
-  LAUNCH_T(K_CORE, nullptr, w.core.n, launch_core(w.core.d, w.core.n, c->d_ival, s));
+  return PEPO_OK;
+}
+
+// after the colour's bond core: reconstruct into the next layout, commit
+template <typename T>
+pepo_status run_gate_wave_tail(pepo_ctx* c, Inst& I, GateWave& w) {
+  cudaStream_t s = c->stream;
+  const int chimax = I.cfg.chi_max;
+  const int nmax = 4 * chimax;
   {
     long long rows = (long long)pow_sz(chimax, 3);
     int gx = (int)std::min<long long>(std::max<long long>(1, (rows + 63) / 64 * ceil_div(nmax, 64)),
@@ -1095,10 +1133,10 @@ pepo_status run_bp_waves(pepo_ctx* c, Inst& I, std::vector<BpWave>& waves) {
     for (int a = 0; a < 4; ++a) {
       int gx = std::max(8, 2 * 152 * 4 / std::max(1, w.leg[a].n));
       LAUNCH_T(K_LEG, hitems(c, w.leg[a]), w.leg[a].n,
-               launch_leg_contract<T>(w.leg[a].d, w.leg[a].n, gx, chimax, c->d_ptrs, c->d_ival, s));
+               leg_dispatch<T>(c, w.leg[a].d, w.leg[a].n, gx, chimax));
     }
     LAUNCH_T(K_GRAM_LEG, hitems(c, w.gram), w.gram.n,
-             launch_gram_leg<T>(w.gram.d, w.gram.n, kLegSplits, chimax, c->d_ptrs, c->d_ival, s));
+             gram_leg_dispatch<T>(c, w.gram.d, w.gram.n, chimax));
     LAUNCH_T(K_GRAM_LEG_RED, nullptr, w.gram.n,
              launch_gram_leg_reduce(w.gram.d, w.gram.n, chimax, kLegSplits, c->d_ival, s));
     LAUNCH_T(K_MSG, nullptr, w.rot.n, launch_rotate_back(w.rot.d, w.rot.n, chimax, c->d_ival, s));
@@ -1119,11 +1157,17 @@ template <typename T>
 pepo_status do_steps(pepo_ctx* c, int n) {
   for (int step = 0; step < n; ++step)
     for (auto& I : c->inst) {
-      for (int col = 0; col < 4; ++col)
+      for (int col = 0; col < 4; ++col) {
         for (auto& w : I.gwaves[col]) {
           pepo_status st = run_gate_wave<T>(c, I, w);
           if (st != PEPO_OK) return st;
         }
+        LAUNCH_T(K_CORE, nullptr, I.gcore[col].n, launch_core(I.gcore[col].d, I.gcore[col].n, c->d_ival, c->stream));
+        for (auto& w : I.gwaves[col]) {
+          pepo_status st = run_gate_wave_tail<T>(c, I, w);
+          if (st != PEPO_OK) return st;
+        }
+      }
       I.steps++;
     }
   c->stepped = true;

@@ -81,3 +81,21 @@ def test_qr_branch_independence(prec):
     for b in lh:
         k = min(len(lh[b]), len(lc[b]))
         assert np.max(np.abs(lh[b][:k] - lc[b][:k])) < TOL[prec][1]
+
+
+@pytest.mark.parametrize("cfgname", ["c1", "c2"])
+def test_tf32x3_mixed_precision_parity(cfgname):
+    # Mixed-precision path: Gram / absorb / BP contractions on the tensor cores
+    # with the three-product TF32 split; bound |dC| <= 1e-3 (mixed-precision
+    # target), lam error <= 1e-4.
+    if cfgname == "c1":
+        cfg = pkg.Config(Lx=3, Ly=3, J=1.0, h=1.0, dt=0.05, order=1, chi_max=8, bp_tol=1e-7,
+                         precision="tf32x3")
+        n = 20
+    else:
+        cfg = pkg.Config(Lx=4, Ly=4, J=1.0, h=2.0, dt=0.05, order=2, obs=(1, 1), chi_max=20,
+                         precision="tf32x3")
+        n = 8
+    r = compare(cfg, n)
+    assert r["dC"] < 1e-3, r["dC"]
+    assert r["lam_err"] < 1e-4, r["lam_err"]
