@@ -29,12 +29,13 @@ SEED = 0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pepo", choices=["pepo", "reference"])
     ap.add_argument("--chi", type=int, default=None, help="override chi_max (smaller test runs)")
     ap.add_argument("--grid", type=int, default=None, help="override the grid side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default=None, help="fp32 | tf32x3 | fp64 (default fp32)")
     return ap.parse_args()
 
 
@@ -49,6 +50,8 @@ def workload(args):
     w = dict(WORKLOAD)
     if args.chi:
         w["chi_max"] = args.chi
+    if args.prec:
+        w["precision"] = args.prec
     if args.grid:
         w["Lx"] = w["Ly"] = args.grid
         w["obs"] = (min(3, args.grid - 1), min(4, args.grid - 1))
@@ -103,6 +106,14 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+TF32_PER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 tensor rate of the part
+
+
+def fp32_alu_peak_tflops():
+    """FP32 FMA peak: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (maximum SM clock)."""
+    return 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 def peaks():
@@ -200,8 +211,10 @@ def run_gpu(args, rank, world, local):
         C, D = eng.correlator()
         return sw[0], D[0]
 
-    for _ in range(args.warmup):
+    for i in range(args.warmup):
+        t = time.perf_counter()
         one_step()
+        print("warmup step %d: %.1f s" % (i, time.perf_counter() - t), file=sys.stderr, flush=True)
     dist = world > 1 and torch.distributed.is_initialized()
     stream = torch.cuda.current_stream()
     if dist:
@@ -242,10 +255,25 @@ def run_gpu(args, rank, world, local):
     top = max(timing.items(), key=lambda kv: kv[1]["ms"])
     name, tk = top
     avg_ms = tk["ms"] / max(1, tk["launches"])
-    if tk["flops"] > 0 and tk["bytes"] / tk["flops"] < 1.0 / 283 and False:
-        bound = "tensor"
-    bound = "hbm"
-    achieved = (tk["bytes"] / max(1, tk["launches"])) / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    # binding limit of the dominant kernel: HBM bytes, or arithmetic (FP32 FMA
+    # pipes for the SIMT kernels, TF32 tensor pipes for the split-precision mode)
+    nl = max(1, tk["launches"])
+    gbs = (tk["bytes"] / nl) / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+    tfs = (tk["flops"] / nl) / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
+    tensor_mode = w["precision"] in ("tf32x3", "bf16x3")
+    alu_peak = fp32_alu_peak_tflops()
+    cpeak = bf16 * TF32_PER_BF16 if tensor_mode else alu_peak
+    if tfs / cpeak >= gbs / hbm:
+        roof = {"bound": "tensor" if tensor_mode else "alu", "achieved": tfs, "peak": cpeak,
+                "peak_source": ("%s bf16 x %.3f (nominal tf32/bf16)" % (src, TF32_PER_BF16)) if tensor_mode
+                else "152 SMs x 128 FP32 lanes x 2 x 2070 MHz", "unit": "TFLOP/s", "frac": tfs / cpeak}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "peak_source": src, "unit": "GB/s",
+                "frac": gbs / hbm}
+    roof.update({"kernel": name, "traffic": None, "avg_launch_ms": avg_ms,
+                 "algorithmic_bytes_per_launch": tk["bytes"] / nl,
+                 "algorithmic_flops_per_launch": tk["flops"] / nl,
+                 "achieved_gbs": gbs, "achieved_tflops": tfs})
     bond_classes = ["leg_contract", "gram_rows", "gram_rows_reduce", "reconstruct", "householder_tsqr",
                     "factor", "core_svd", "env_factor"]
     # bond-update FLOPs: algorithmic FLOPs of the bond-update kernels over their time
@@ -261,7 +289,7 @@ def run_gpu(args, rank, world, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f32" if w["precision"] == "fp32" else ("tf32x3" if w["precision"] == "tf32x3" else w["precision"]),
         "data": "synthetic (seeded saturated state, every bond at chi_max)",
         "config": {"workload": workload_name(w), "grid": "%dx%d" % (w["Lx"], w["Ly"]),
                    "chi_max": w["chi_max"], "J": w["J"], "h": w["h"], "dt": w["dt"],
@@ -269,10 +297,7 @@ def run_gpu(args, rank, world, local):
                    "bp_tol": w["bp_tol"], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.1f GB of site tensors)" % (state_bytes / 1e9),
                    "bp_sweeps": sweeps},
-        "roofline": {"bound": bound, "kernel": name, "achieved": achieved, "peak": hbm,
-                     "peak_source": src, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "avg_launch_ms": avg_ms,
-                     "algorithmic_bytes_per_launch": tk["bytes"] / max(1, tk["launches"])},
+        "roofline": roof,
         "bond_update_tflops": (sum(timing[k]["flops"] for k in bond_classes if k in timing) / 1e12
                                / (bu_ms / 1e3)) if bu_ms > 0 else None,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in timing.items() if v["launches"]},

@@ -979,7 +979,7 @@ Work work_of(const pepo_ctx* c, int cls, const void* items, int n) {
       double tot = 4;
       for (int k = 0; k < it.x.nlegs; ++k) tot *= d[k];
       double F = d[it.leg];
-      w.bytes += 2.0 * tot * ts;
+      w.bytes += (it.x.ref == it.y_ref ? 1.0 : 2.0) * tot * ts;   // a symmetric Gram reads X once
       w.flops += 2.0 * tot * F;
     } else if (cls == K_RECON) {
       const ReconItem& it = static_cast<const ReconItem*>(items)[i];
