@@ -7,16 +7,16 @@
  *   Sec. 2.1  Eq. 1       H = -J sum X_i X_j - h sum Z_i (or the ZZ/X gate set)
  *   Sec. 2.2  Eq. 4       C(t) = Tr[Z_c(t) Z_c] / 2^N
  *   Sec. 2.3              Pauli-basis network, site tensor chi^deg x 4
- *   Sec. 2.3  Eq. 5, 6    Trotter step O -> U^dagger O U, four-colour bonds
- *   Sec. 2.4  Alg. 1      bond update: absorb, QR, RR, gate, SVD, truncate,
+ *   Sec. 2.4  Eq. 5, 6    Trotter step O -> U^dagger O U, four-colour bonds
+ *   Sec. 2.5  Alg. 1      bond update: absorb, QR, RR, gate, SVD, truncate,
  *                         reconstruct, deabsorb, Vidal normalisation
- *   Sec. 4.2  Eq. 7       hybrid QR (Cholesky-QR for tall n > 150, m/n > 150)
- *   Sec. 4.2  Eq. 9, 10   truncation and lambda = s / ||s||
- *   Sec. 4.2  Eq. 11, 12  BP message update and stopping rule
- *   Sec. 6.4  Eq. 13      damped BP
- *   Sec. 2.5  Eq. 14-16   Bethe value of C(t) in log space with signs
+ *   Sec. 4.2  Eq. 10       hybrid QR (Cholesky-QR for tall n > 150, m/n > 150)
+ *   Sec. 4.2  Eq. 11, 12   truncation and lambda = s / ||s||
+ *   Sec. 4.2  Eq. 13, 14  BP message update and stopping rule
+ *   Sec. 6.3  Eq. 19      damped BP
+ *   Sec. 2.6  Eq. 7-9   Bethe value of C(t) in log space with signs
  *   Sec. 3.1              zero-malloc workspace / IsingState
- *   Sec. 5    Eq. 17-19   analytic memory model
+ *   Sec. 5    Eq. 15-17   analytic memory model
  *
  * Conventions shared by every entry point
  *   - Sites: (x, y), x = column in [0, Lx), y = row in [0, Ly), origin top
@@ -24,7 +24,7 @@
  *   - Bonds: horizontal bond (x,y)-(x+1,y) has id y*(Lx-1) + x; vertical bond
  *     (x,y)-(x,y+1) has id Ly*(Lx-1) + y*Lx + x.  The "first" site of a bond
  *     is the left / upper one.  Colour of a horizontal bond = x % 2, of a
- *     vertical bond = 2 + y % 2 (Sec. 2.3 four-colour partition).
+ *     vertical bond = 2 + y % 2 (Sec. 2.4 four-colour partition).
  *   - Site tensors in the canonical host layout: legs [U, D, L, R] (absent
  *     legs skipped), then the Pauli index p in {I, X, Y, Z} = {0,1,2,3},
  *     row-major (Pauli fastest), real coefficients.  Element type double.
@@ -80,11 +80,11 @@ typedef struct {
   int obs_x, obs_y;        /* observable site */
   int obs_pauli;           /* 1 = X, 2 = Y, 3 = Z */
   int chi_max;             /* bond-dimension cap, >= 1 */
-  double eps_cut;          /* Eq. 9 relative singular-value cut (1e-11) */
-  double bp_alpha;         /* Eq. 13 damping (1 = undamped) */
-  double bp_tol;           /* Eq. 12 tolerance on the message diagonals */
+  double eps_cut;          /* Eq. 11 relative singular-value cut (1e-11) */
+  double bp_alpha;         /* Eq. 19 damping (1 = undamped) */
+  double bp_tol;           /* Eq. 14 tolerance on the message diagonals */
   int bp_max_sweeps;       /* sweep budget (100) */
-  int qr_n_thresh;         /* Eq. 7 branch: Cholesky-QR if n > qr_n_thresh ... */
+  int qr_n_thresh;         /* Eq. 10 branch: Cholesky-QR if n > qr_n_thresh ... */
   double qr_ratio_thresh;  /* ... and m / n > qr_ratio_thresh (150, 150) */
   double pinv_rel;         /* rank threshold for message square roots (1e-12) */
   int gates;               /* pepo_gateset */
@@ -95,7 +95,7 @@ typedef struct {
 
 /* Per-instance measurement record (Table 1 diagnostics). */
 typedef struct {
-  double C;                /* Eq. 16 / Bethe ratio: C_proj / sqrt(norm) */
+  double C;                /* Eq. 9 / Bethe ratio: C_proj / sqrt(norm) */
   double C_proj;           /* single-layer Bethe value (with site scales) */
   double log_norm;         /* log of the double-layer Bethe value ("Bethe norm") */
   double gate_err;         /* Table 1: discarded weight summed over the last step */
@@ -104,7 +104,7 @@ typedef struct {
   int bp1_sweeps;          /* single-layer sweeps */
   double bp1_delta;
   double entropy_frac_max; /* Table 1: max over bonds of S_e / log chi_e */
-  int trap_type1;          /* sweeps >= 30 and delta < tol (Sec. 6.4) */
+  int trap_type1;          /* sweeps >= 30 and delta < tol (Sec. 6.3) */
   int trap_type2;          /* sweeps == max */
   int norm_exploded;       /* exp(log_norm) >= 2 */
   int flags;               /* bit 0: rank-deficient message met (env projector
@@ -119,7 +119,7 @@ void pepo_config_default(pepo_config* cfg);
 
 /* Bytes of device memory pepo_init needs for n_inst instances (array cfgs).
  * Returns 0 if a configuration is invalid.  Follows the analytic memory model
- * (Eq. 17-19) adapted to this implementation: site tensors at chi_max, two
+ * (Eq. 15-17) adapted to this implementation: site tensors at chi_max, two
  * scratch slabs per in-flight site, messages and small workspaces. */
 size_t pepo_required_bytes(const pepo_config* cfgs, int n_inst);
 
@@ -137,18 +137,18 @@ pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena,
  * instance.  Asynchronous. */
 pepo_status pepo_trotter_step(pepo_ctx* ctx, int n_steps);
 
-/* Run damped double-layer BP (Eq. 11-13) to tolerance or the sweep budget.
+/* Run damped double-layer BP (Eq. 13-19) to tolerance or the sweep budget.
  * sweeps_out / delta_out: host arrays of n_inst entries (may be NULL).
  * Synchronises the stream. */
 pepo_status pepo_bp_converge(pepo_ctx* ctx, int* sweeps_out, double* delta_out);
 
 /* Single-layer BP on the pinned network and the Bethe value of C(t)
- * (Eq. 14-16).  Uses the current double-layer messages (call
+ * (Eq. 7-9).  Uses the current double-layer messages (call
  * pepo_bp_converge first).  C_out: n_inst doubles; diag_out: n_inst records
  * (either may be NULL).  Synchronises the stream. */
 pepo_status pepo_correlator(pepo_ctx* ctx, double* C_out, pepo_diag* diag_out);
 
-/* Vidal-normalised singular values of a bond (Eq. 10) from its last update.
+/* Vidal-normalised singular values of a bond (Eq. 12) from its last update.
  * lam_out: at least chi_max doubles; *chi_out receives the live chi. */
 pepo_status pepo_get_spectrum(pepo_ctx* ctx, int inst, int bond, double* lam_out,
                               int* chi_out);

@@ -14,16 +14,16 @@ Representation (deliberately different from the GPU path):
     unitaries (the GPU uses real Pauli transfer matrices);
   * every step follows the paper's order: absorb the square-rooted environment,
     permute, Householder QR, RR = R1 R2, gate, SVD + truncation, Q M,
-    inverse permute, deabsorb (Sec. 2.4 "Gate Update", Algorithm 1).
+    inverse permute, deabsorb (Sec. 2.5 "Gate Update", Algorithm 1).
 
 Modules
   lattice   geometry and the four-colour bond partition (Sec. 2.3)
   gates     unitaries and the Trotter schedule (Eq. 6 / Sec. 2.3)
   dense     brute-force 2^N x 2^N operator evolution (Eq. 3-5)
-  pepo      the operator network and the bond update (Sec. 2.4, Alg. 1)
+  pepo      the operator network and the bond update (Sec. 2.5, Alg. 1)
   bp        double- and single-layer belief propagation, Bethe value
-            (Eq. 11, 12, 14, 15, 16, 17)
-  contract  exact contraction of small networks (Sec. 2.5 step 1)
+            (Eq. 13, 14, 7, 8, 9, 15)
+  contract  exact contraction of small networks (Sec. 2.6 step 1)
   run       the time loop (Fig. 1 pipeline)
 
 Parity status of each function is stated in its module header.

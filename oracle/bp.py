@@ -1,7 +1,7 @@
 """Belief propagation and the Bethe value of C(t) (oracle, complex128).
 
-Double layer (Sec. 2.3; Eq. 11 read as matrix messages, Eq. 13 damping,
-Eq. 12 stopping rule):
+Double layer (Sec. 2.3; Eq. 13 read as matrix messages, Eq. 19 damping,
+Eq. 14 stopping rule):
   M_{v->w}[i,i'] = sum conj(O_v[..i..j..]) O_v[..i'..j'..] prod_{u != w} M_{u->v}[j_u, j'_u]
   (the physical pair is traced, i.e. the Hilbert-Schmidt norm network);
   Hermitian-symmetrise, normalise to unit trace, damp
@@ -9,13 +9,13 @@ Eq. 12 stopping rule):
   Jacobi schedule (every new message from the previous sweep), stop when
   delta < tol or after max_sweeps.
 
-Single layer (Sec. 2.5 step 1: pin Z at c and I elsewhere; vector messages,
+Single layer (Sec. 2.6 step 1: pin Z at c and I elsewhere; vector messages,
 "observable-specific messages can be negative"):
   t_v = Tr(O_v P_v) / 2,  m_{v->w}[i] = sum t_v[..i..j..] prod_{u != w} m_{u->v}[j_u];
   unit 2-norm, phase aligned with the previous iterate before damping, same
   alpha / tol / max_sweeps.  Initial m_{v->w} = sqrt(diag M_{v->w}), normalised.
 
-Bethe value with sign (phase) tracking (Eq. 14-16):
+Bethe value with sign (phase) tracking (Eq. 7-9):
   log|C_proj| = sum_v log|vs_v| - sum_e log|Z_e|,  Z_e = sum_i m_ab[i] m_ba[i]
   log N       = sum_v log f_v - sum_e log Z2_e,  Z2_e = sum_ij M_ab[i,j] M_ba[i,j]
   C(t)        = phase * exp(log|C_proj| - log N / 2)
@@ -23,7 +23,7 @@ where vs_v (f_v) is the full contraction of the single (double) layer site
 with all of its incoming messages, each carrying the per-site factor 1/2 of
 the normalised trace.  Dividing by sqrt(N) (the paper's "Bethe norm",
 Table 1) makes the estimate independent of the network's overall scale; when
-N = 1 it is the paper's Eq. 16.
+N = 1 it is the paper's Eq. 9.
 
 Pinned by: tests/test_oracle_pepo.py -- on trees (1 x N chains and the star
 around an edge site) BP is exact, so the Bethe value must equal the dense

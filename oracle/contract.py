@@ -1,6 +1,6 @@
 """Exact contraction of small operator networks (oracle).
 
-Sec. 2.5 step 1: by Pauli orthogonality the trace Tr[O P]/2^N is the full
+Sec. 2.6 step 1: by Pauli orthogonality the trace Tr[O P]/2^N is the full
 contraction of the network with every physical pair pinned (P_c at the
 observable site, I elsewhere).  ``pinned_value`` does that contraction
 exactly (no Bethe factorisation) and ``to_dense`` contracts the network with

@@ -10,7 +10,7 @@ gate sets share one code path:
                   exp(-i theta P / 2), R_xx(2 J dt) = exp(-i J dt XX) and the two
                   R_z(h dt) factors of Eq. 6 are exp(-i (h dt / 2) Z) each.
 
-Schedule of one step (Sec. 2.3, Eq. 6; reading: the paper calls Eq. 6 first
+Schedule of one step (Sec. 2.4, Eq. 6; reading: the paper calls Eq. 6 first
 order although it is the symmetric split):
   order 1: all site gates with angle h dt, then bond colours 0, 1, 2, 3 with
            angle J dt;

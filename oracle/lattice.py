@@ -7,7 +7,7 @@ index is v = y * Lx + x.  Each site lists its legs in the canonical order
 (Sec. 2.1, open boundary conditions).
 
 The bonds are split into four colour classes such that no two bonds of one
-class share a site (Sec. 2.3, four-colour decomposition):
+class share a site (Sec. 2.4, four-colour decomposition):
   colour 0: horizontal bonds (x, y)-(x+1, y) with x even
   colour 1: horizontal bonds with x odd
   colour 2: vertical bonds (x, y)-(x, y+1) with y even

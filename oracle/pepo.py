@@ -8,23 +8,23 @@ State (Sec. 2.3 "Pauli Basis Tensor Network", Sec. 3.1 IsingState):
   M[(u,v)]  double-layer message from u into v: the environment of v's leg
             toward u.  Convention: M[j, j'] pairs conj(O_v) at index j with
             O_v at index j'.
-  lam[b]    Vidal-normalised singular values of bond b (Eq. 10).
+  lam[b]    Vidal-normalised singular values of bond b (Eq. 12).
 
 Initial state (Sec. 2.3, Fig. 1): the observable Pauli at site c, the identity
 elsewhere, every bond dimension 1 and every message [[1]].
 
-Bond update (Sec. 2.4 steps 1-8, Algorithm 1), applied literally:
+Bond update (Sec. 2.5 steps 1-8, Algorithm 1), applied literally:
   1. pseudo square roots of the environment messages by eigh of (M + M^H)/2,
      eigenvalues below pinv_rel * max treated as zero (Sec. 4 Fig. 1 step 1);
   2. absorb sqrt(M) on every leg except the cut;
   3. permute the cut leg next to the physical pair;
   4. Householder QR (numpy.linalg.qr) of the (env) x (cut, s, s') matrix;
   5. RR4 = R1 . R2 contracted over the cut (Fig. 1 step 5);
-  6. the gate acts by g^dagger (.) g on the two physical pairs (Sec. 2.4 step 4);
-  7. SVD, truncation chi_new = min(#{s_i >= eps_cut s_0}, chi_max) (Eq. 9);
+  6. the gate acts by g^dagger (.) g on the two physical pairs (Sec. 2.5 step 4);
+  7. SVD, truncation chi_new = min(#{s_i >= eps_cut s_0}, chi_max) (Eq. 11);
   8. M1 = U sqrt(S), M2 = sqrt(S) V^H with the raw singular values; Q M;
      inverse permute; deabsorb with M^{-1/2}; messages <- diag(lam) with
-     lam = s / ||s_kept|| (Eq. 10).
+     lam = s / ||s_kept|| (Eq. 12).
 
 Pinned by: tests/test_oracle_pepo.py -- without truncation the network
 contracts to the dense operator exactly on a 3 x 3 grid (loops) and on chains;

@@ -1,7 +1,7 @@
 // Internal definitions shared by the libpepo kernels and the host driver.
 //
 // Device-resident sizes.  Live bond dimensions grow from 1 to chi_max during a
-// run (Sec. 2.3) and are decided on the device (Eq. 9), so no kernel takes a
+// run (Sec. 2.3) and are decided on the device (Eq. 11), so no kernel takes a
 // live size as a launch argument: every kernel reads the sizes it needs from
 // the int table `ival` through index records prepared at init.  Grids are
 // sized for chi_max and surplus blocks return early, so one recorded launch
@@ -34,7 +34,7 @@ __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; 
 __host__ __device__ inline long long ceil_divl(long long a, long long b) { return (a + b - 1) / b; }
 
 // Leg contraction: out[o, i, q] = sum_j A[i, j] in[o, j, q] on layout leg `leg`
-// (absorb of Sec. 2.4 step 1 and the BP products of Eq. 11).
+// (absorb of Sec. 2.5 step 1 and the BP products of Eq. 13).
 struct LegItem {
   TView in;
   int out_ref;
@@ -46,7 +46,7 @@ struct LegItem {
 };
 
 // Gram over rows: C[f, f'] = sum_k X[k, f] Y[k, f'], X, Y row-major K x F with
-// F = 4 * (size of the innermost leg): the cv^T cv of Eq. 7 (Cholesky-QR).
+// F = 4 * (size of the innermost leg): the cv^T cv of Eq. 10 (Cholesky-QR).
 struct GramRowsItem {
   TView x;
   int y_ref;
@@ -57,7 +57,7 @@ struct GramRowsItem {
 };
 
 // Free-leg contraction: out[i, i'] = sum_{o,q} X[o, i, q] Y[o, i', q], free leg
-// at layout position `leg` (one BP message, Eq. 11 with the Pauli leg traced).
+// at layout position `leg` (one BP message, Eq. 13 with the Pauli leg traced).
 struct GramLegItem {
   TView x;
   int y_ref;
@@ -72,7 +72,7 @@ struct GramLegItem {
 
 // Eigen-decomposition of a (symmetrised) message M = V diag(D) V^T by one-sided
 // Jacobi (FP64); writes Vt (row i = eigenvector i, leading dimension ld) and
-// sqrt(D).  Used to rotate a site tensor into the message eigenbasis (Eq. 11).
+// sqrt(D).  Used to rotate a site tensor into the message eigenbasis (Eq. 13).
 struct EnvEigItem {
   const double* M;
   int ld;
@@ -91,7 +91,7 @@ struct RotItem {
   int chi_idx;
 };
 
-// Reconstruct (Sec. 2.4 step 6, Q-less): out = in * W where `in` is viewed as
+// Reconstruct (Sec. 2.5 step 6, Q-less): out = in * W where `in` is viewed as
 // rows x (cut, Pauli) with the cut innermost; the output leg order is out_perm
 // (output leg k is input leg out_perm[k]); the cut leg gets size new_dim.
 struct ReconItem {
@@ -118,7 +118,7 @@ struct VecItem {
 
 // ------------------------------------------------------------ linear algebra
 // Pivoted Cholesky factor of a (symmetrised) message: L^T L = M with L k x chi
-// in the original column order (a square root of the environment, Sec. 2.4
+// in the original column order (a square root of the environment, Sec. 2.5
 // step 1 / Fig. 1 "pseudo_sqrt"; eigen-directions below rel * max dropped).
 struct EnvFactorItem {
   const double* M;         // chi x chi, leading dimension ld
@@ -126,10 +126,11 @@ struct EnvFactorItem {
   int ld;
   int chi_idx;             // ival index of chi
   int rank_idx;            // ival index receiving k
+  double rel;              // relative pivot threshold of the instance
 };
 
 // Per-site factor of the bond update: either Cholesky-QR (Gram) or
-// Householder (TSQR) produces an R-factor of cv (Eq. 7); the gate's
+// Householder (TSQR) produces an R-factor of cv (Eq. 10); the gate's
 // operator-Schmidt factors turn it into the factor T of X = (gate half) cv.
 struct SiteFacItem {
   TView cv;                // absorbed tensor, cut leg innermost (env dims = factor ranks)
@@ -144,9 +145,11 @@ struct SiteFacItem {
   int* perm;               // pivot order (r entries)
   int rank_idx;            // ival: rank of the factor
   double rel;              // rank threshold
+  int n_thr;               // Eq. 10 branch thresholds of the instance
+  double ratio_thr;
 };
 
-// Per-bond core: SVD of R1 R2^T, truncation (Eq. 9), lambda (Eq. 10), the
+// Per-bond core: SVD of R1 R2^T, truncation (Eq. 11), lambda (Eq. 12), the
 // reconstruct matrices W1, W2, messages diag(lambda) (Alg. 1 line 13).
 struct CoreItem {
   int bond;                // bond id (instance-local)
@@ -169,12 +172,12 @@ struct CoreItem {
   double* disc;            // discarded weight of this bond (Table 1 gate_err)
   double* svals;           // all singular values (rmax entries, for diagnostics)
   int* nsv;                // number of singular values
-  int* flags;              // instance flag word
+  int inst;                // instance (its flag word is flags_base[inst])
   double eps_cut;
 };
 
 // ------------------------------------------------------------------- BP
-// One directed message (Eq. 11-13): unnormalised estimate `hat` (double layer)
+// One directed message (Eq. 13-19): unnormalised estimate `hat` (double layer)
 // or `vhat` (single layer) is turned into the damped, normalised message.
 struct MsgItem {
   int inst;
@@ -183,16 +186,18 @@ struct MsgItem {
   double* msg;             // chi x chi (ld chimax) current message (updated)
   const double* vhat;      // chi single-layer estimate
   double* vec;             // chi single-layer message (updated)
-  double* vinit_from;      // unused (kept for layout)
+  int ld;                  // leading dimension of hat / msg (the instance's chi_max)
+  double alpha;            // damping of the instance (Eq. 19)
 };
 
-// Per-site Bethe factors (Eq. 14-16): vs_v = <vhat_{v->w}, m_{w->v}>,
+// Per-site Bethe factors (Eq. 7-9): vs_v = <vhat_{v->w}, m_{w->v}>,
 // f_v = <hat_{v->w}, M_{w->v}>, with w the site's first layout leg.
 struct SiteScalarItem {
   int chi_idx;
   const double* hat; const double* msg_in;
   const double* vhat; const double* vec_in;
   double* vs; double* fv;
+  int ld;
 };
 
 // Per-bond edge factors: Z_e = m_ab . m_ba, Z2_e = sum M_ab * M_ba.
@@ -201,9 +206,10 @@ struct EdgeItem {
   const double* m12; const double* m21;     // double-layer messages
   const double* v12; const double* v21;     // single-layer messages
   double* ze; double* z2e;
+  int ld;
 };
 
-// Per-instance sums of Eq. 16 and the Bethe norm.
+// Per-instance sums of Eq. 9 and the Bethe norm.
 struct BetheItem {
   int nsites, nbonds;
   const double* vs; const double* fv; const double* sigma;

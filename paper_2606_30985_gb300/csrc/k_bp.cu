@@ -1,13 +1,13 @@
 // Belief propagation bookkeeping, the Bethe value, gate tables and init.
 //
-//   k_bp_finish    double-layer message (Eq. 11): symmetrise, unit trace,
-//                  damping (Eq. 13), delta = max |diag change| (Eq. 12)
+//   k_bp_finish    double-layer message (Eq. 13): symmetrise, unit trace,
+//                  damping (Eq. 19), delta = max |diag change| (Eq. 14)
 //   k_sl_init      single-layer start m = sqrt(diag M), unit norm
 //   k_sl_finish    single-layer message: unit 2-norm, sign aligned with the
 //                  previous iterate, damping, delta = max |change|
-//   k_site_scalars vs_v and f_v of Eq. 14 / Table 1 (Bethe norm)
-//   k_edge_scalars Z_e (Eq. 15) and its double-layer analogue
-//   k_bethe        log-space sum with explicit signs (Eq. 16)
+//   k_site_scalars vs_v and f_v of Eq. 7 / Table 1 (Bethe norm)
+//   k_edge_scalars Z_e (Eq. 8) and its double-layer analogue
+//   k_bethe        log-space sum with explicit signs (Eq. 9)
 //   k_gates        Pauli transfer matrices of the gates (Sec. 2.3, real
 //                  orthogonal), site gates folded into bond gates, and the
 //                  operator-Schmidt factors used by the bond core
@@ -55,10 +55,13 @@ __device__ inline void atomic_max_nonneg(unsigned long long* a, double v) {
 }
 
 // ================================================================ BP finish
-__global__ void k_bp_finish(const MsgItem* __restrict__ items, const int* ival, int chimax,
-                            double alpha, unsigned long long* delta, int* flags) {
+__global__ void k_bp_finish(const MsgItem* __restrict__ items, const int* ival, const int* active,
+                            unsigned long long* delta, int* flags) {
   const MsgItem it = items[blockIdx.x];
+  if (active && !active[it.inst]) return;   // converged instance of a batch: keep its messages
   const int n = ival[it.chi_idx];
+  const int chimax = it.ld;
+  const double alpha = it.alpha;
   __shared__ double red[8];
   double tr = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) tr += it.hat[i * chimax + i];
@@ -81,17 +84,18 @@ __global__ void k_bp_finish(const MsgItem* __restrict__ items, const int* ival, 
   if (threadIdx.x == 0) atomic_max_nonneg(&delta[it.inst], dmax);
 }
 
-cudaError_t launch_bp_finish(const MsgItem* items, int n, const int* ival, int chimax, double alpha,
+cudaError_t launch_bp_finish(const MsgItem* items, int n, const int* ival, const int* active,
                              unsigned long long* delta, int* flags, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_bp_finish<<<n, 256, 0, s>>>(items, ival, chimax, alpha, delta, flags);
+  k_bp_finish<<<n, 256, 0, s>>>(items, ival, active, delta, flags);
   return cudaGetLastError();
 }
 
 // ============================================================ single layer
-__global__ void k_sl_init(const MsgItem* __restrict__ items, const int* ival, int chimax) {
+__global__ void k_sl_init(const MsgItem* __restrict__ items, const int* ival) {
   const MsgItem it = items[blockIdx.x];
   const int n = ival[it.chi_idx];
+  const int chimax = it.ld;
   __shared__ double red[8];
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -104,10 +108,12 @@ __global__ void k_sl_init(const MsgItem* __restrict__ items, const int* ival, in
     it.vec[i] = (i < n) ? sqrt(fmax(it.msg[i * chimax + i], 0.0)) * inv : 0.0;
 }
 
-__global__ void k_sl_finish(const MsgItem* __restrict__ items, const int* ival, double alpha,
+__global__ void k_sl_finish(const MsgItem* __restrict__ items, const int* ival, const int* active,
                             unsigned long long* delta) {
   const MsgItem it = items[blockIdx.x];
+  if (active && !active[it.inst]) return;
   const int n = ival[it.chi_idx];
+  const double alpha = it.alpha;
   __shared__ double red[8];
   double nn = 0.0, dot = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -130,22 +136,23 @@ __global__ void k_sl_finish(const MsgItem* __restrict__ items, const int* ival, 
   if (threadIdx.x == 0) atomic_max_nonneg(&delta[it.inst], dmax);
 }
 
-cudaError_t launch_sl_init(const MsgItem* items, int n, const int* ival, int chimax, cudaStream_t s) {
+cudaError_t launch_sl_init(const MsgItem* items, int n, const int* ival, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_sl_init<<<n, 256, 0, s>>>(items, ival, chimax);
+  k_sl_init<<<n, 256, 0, s>>>(items, ival);
   return cudaGetLastError();
 }
-cudaError_t launch_sl_finish(const MsgItem* items, int n, const int* ival, double alpha,
+cudaError_t launch_sl_finish(const MsgItem* items, int n, const int* ival, const int* active,
                              unsigned long long* delta, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_sl_finish<<<n, 256, 0, s>>>(items, ival, alpha, delta);
+  k_sl_finish<<<n, 256, 0, s>>>(items, ival, active, delta);
   return cudaGetLastError();
 }
 
 // ================================================================ scalars
-__global__ void k_site_scalars(const SiteScalarItem* __restrict__ items, const int* ival, int chimax) {
+__global__ void k_site_scalars(const SiteScalarItem* __restrict__ items, const int* ival) {
   const SiteScalarItem it = items[blockIdx.x];
   const int n = ival[it.chi_idx];
+  const int chimax = it.ld;
   __shared__ double red[8];
   double f = 0.0, v = 0.0;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -158,9 +165,10 @@ __global__ void k_site_scalars(const SiteScalarItem* __restrict__ items, const i
   if (threadIdx.x == 0) { *it.fv = f; *it.vs = v; }
 }
 
-__global__ void k_edge_scalars(const EdgeItem* __restrict__ items, const int* ival, int chimax) {
+__global__ void k_edge_scalars(const EdgeItem* __restrict__ items, const int* ival) {
   const EdgeItem it = items[blockIdx.x];
   const int n = ival[it.chi_idx];
+  const int chimax = it.ld;
   __shared__ double red[8];
   double z2 = 0.0, z = 0.0;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -173,21 +181,19 @@ __global__ void k_edge_scalars(const EdgeItem* __restrict__ items, const int* iv
   if (threadIdx.x == 0) { *it.ze = z; *it.z2e = z2; }
 }
 
-cudaError_t launch_site_scalars(const SiteScalarItem* items, int n, const int* ival, int chimax,
-                                cudaStream_t s) {
+cudaError_t launch_site_scalars(const SiteScalarItem* items, int n, const int* ival, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_site_scalars<<<n, 256, 0, s>>>(items, ival, chimax);
+  k_site_scalars<<<n, 256, 0, s>>>(items, ival);
   return cudaGetLastError();
 }
-cudaError_t launch_edge_scalars(const EdgeItem* items, int n, const int* ival, int chimax,
-                                cudaStream_t s) {
+cudaError_t launch_edge_scalars(const EdgeItem* items, int n, const int* ival, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_edge_scalars<<<n, 256, 0, s>>>(items, ival, chimax);
+  k_edge_scalars<<<n, 256, 0, s>>>(items, ival);
   return cudaGetLastError();
 }
 
 // ================================================================== Bethe
-// FP64 log-space sum with sign parity (Eq. 16); one block per instance.
+// FP64 log-space sum with sign parity (Eq. 9); one block per instance.
 __global__ void k_bethe(const BetheItem* __restrict__ items) {
   const BetheItem it = items[blockIdx.x];
   __shared__ double red[8];

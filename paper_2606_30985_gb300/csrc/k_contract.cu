@@ -2,11 +2,11 @@
 //
 //   k_leg_contract  out[o, i, q] = sum_j A[i, j] in[o, j, q] on one layout leg
 //                   (absorbing a message factor or eigenbasis into a site
-//                   tensor: Sec. 2.4 step 1 and the products of Eq. 11)
+//                   tensor: Sec. 2.5 step 1 and the products of Eq. 13)
 //   k_gram_leg      out[i, i'] = sum_{o, q} w(o,q)^2 X[o, i, q] Y[o, i', q]: a site
 //                   tensor contracted with itself over every index but one leg,
 //                   the Pauli leg traced, optionally weighted (one double-layer
-//                   message, Eq. 11)
+//                   message, Eq. 13)
 //
 // Both are GEMMs with one short dimension (chi <= 128).  The tile edge TL is
 // 64 or 128 (chosen from chi_max); a block of 256 threads owns a TL x TL
@@ -191,7 +191,7 @@ k_gram_leg(const GramLegItem* __restrict__ items, int splits_max, void* const* p
   for (int i = 0; i < k; ++i) O *= d[i];
   for (int i = k + 1; i < it.x.nlegs; ++i) Q *= d[i];
   const long long NC = gram_leg_chunks(O, Q);
-  const int S = gram_leg_splits(NC, splits_max);
+  const int S = gram_leg_splits_k(O * Q, splits_max);
   const int s = blockIdx.x;
   if (s >= S) return;
   const long long c0 = NC * s / S, c1 = NC * (s + 1) / S;
@@ -316,7 +316,7 @@ __global__ void k_gram_leg_reduce(const GramLegItem* __restrict__ items, int spl
   long long O = 1, Q = 4;
   for (int i = 0; i < k; ++i) O *= d[i];
   for (int i = k + 1; i < it.x.nlegs; ++i) Q *= d[i];
-  const int S = gram_leg_splits(gram_leg_chunks(O, Q), splits_max);
+  const int S = gram_leg_splits_k(O * Q, splits_max);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < F * F; e += gridDim.x * blockDim.x) {
     double sum = 0.0;
     for (int s = 0; s < S; ++s) sum += it.partial[(long long)s * F * F + e];

@@ -1,10 +1,10 @@
 // Small dense linear algebra of the bond update, FP64 unless noted.
 //
 //   k_env_factor   pivoted Cholesky square root L of a message M (L^T L = M):
-//                  the environment square root of Sec. 2.4 step 1 (Fig. 1
+//                  the environment square root of Sec. 2.5 step 1 (Fig. 1
 //                  "pseudo_sqrt"); any factor with L^T L = M gives the same cv
 //                  Gram, so no eigensolver is needed.
-//   k_branch       Eq. 7 branch rule: Cholesky-QR when n > n_thr and
+//   k_branch       Eq. 10 branch rule: Cholesky-QR when n > n_thr and
 //                  m / n > ratio_thr, Householder otherwise (Sec. 4.2).
 //   k_hh_level     Householder QR (TSQR tree, R only) of cv in its storage
 //                  precision with FP64 reductions (Sec. 4.2 Householder-QR).
@@ -13,8 +13,8 @@
 //   k_factor       rank-revealing factor T of X: pivoted Cholesky of G
 //                  (Cholesky-QR branch) or column-pivoted Householder of B.
 //   k_core         per bond: R1 R2^T, one-sided Jacobi SVD, truncation
-//                  (Eq. 9), lambda (Eq. 10), reconstruct matrices W1, W2
-//                  (Sec. 2.4 steps 5-8 in Q-less form), messages diag(lambda).
+//                  (Eq. 11), lambda (Eq. 12), reconstruct matrices W1, W2
+//                  (Sec. 2.5 steps 5-8 in Q-less form), messages diag(lambda).
 #include "kernels.h"
 #include "linalg.h"
 
@@ -70,8 +70,9 @@ __device__ inline int block_argmax(const double* values, int lo, int hi, double*
 // =============================================================== env factor
 // Pivoted (outer-product) Cholesky of the symmetrised message in shared memory.
 __global__ void __launch_bounds__(256)
-k_env_factor(const EnvFactorItem* __restrict__ items, int* ival, double rel) {
+k_env_factor(const EnvFactorItem* __restrict__ items, int* ival) {
   const EnvFactorItem it = items[blockIdx.x];
+  const double rel = it.rel;
   const int n = ival[it.chi_idx];
   extern __shared__ __align__(16) double sm[];
   double* A = sm;                 // n x n
@@ -127,13 +128,13 @@ k_env_factor(const EnvFactorItem* __restrict__ items, int* ival, double rel) {
 }
 
 cudaError_t launch_env_factor(const EnvFactorItem* items, int n_items, int chimax, int* ival,
-                              double rel, cudaStream_t s) {
+                              cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   size_t smem = sizeof(double) * ((size_t)chimax * chimax + chimax) + sizeof(int) * chimax;
   cudaError_t e = cudaFuncSetAttribute(k_env_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_env_factor<<<n_items, 256, smem, s>>>(items, ival, rel);
+  k_env_factor<<<n_items, 256, smem, s>>>(items, ival);
   return cudaGetLastError();
 }
 
@@ -144,21 +145,19 @@ __device__ inline void cv_shape(const TView& v, const int* ival, long long& m, i
   n = 4 * (v.nlegs > 0 ? ival[v.dim[v.nlegs - 1]] : 1);
 }
 
-__global__ void k_branch(const SiteFacItem* __restrict__ items, int n_items, int* ival,
-                         int n_thr, double ratio_thr) {
+__global__ void k_branch(const SiteFacItem* __restrict__ items, int n_items, int* ival) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_items) return;
   const SiteFacItem it = items[i];
   long long m;
   int n;
   cv_shape(it.cv, ival, m, n);
-  ival[it.branch_idx] = (n > n_thr && (double)m / (double)n > ratio_thr) ? 1 : 0;
+  ival[it.branch_idx] = (n > it.n_thr && (double)m / (double)n > it.ratio_thr) ? 1 : 0;
 }
 
-cudaError_t launch_branch(const SiteFacItem* items, int n_items, int* ival, int n_thr,
-                          double ratio_thr, cudaStream_t s) {
+cudaError_t launch_branch(const SiteFacItem* items, int n_items, int* ival, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  k_branch<<<ceil_div(n_items, 128), 128, 0, s>>>(items, n_items, ival, n_thr, ratio_thr);
+  k_branch<<<ceil_div(n_items, 128), 128, 0, s>>>(items, n_items, ival);
   return cudaGetLastError();
 }
 
@@ -611,8 +610,9 @@ __device__ int jacobi_svd(double* A, int m, int n, double* V, int max_sweeps, in
 }
 
 __global__ void __launch_bounds__(1024)
-k_core(const CoreItem* __restrict__ items, int* ival) {
+k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
   const CoreItem it = items[blockIdx.x];
+  int* flags = flags_base + it.inst;
   const int chic = ival[it.chi_idx];
   const int rg = ival[it.rg_idx];
   const int r = rg * chic;
@@ -667,7 +667,7 @@ k_core(const CoreItem* __restrict__ items, int* ival) {
   }
   __syncthreads();
   const double s0 = sv[order[0]];
-  // truncation, Eq. 9
+  // truncation, Eq. 11
   __shared__ int sh_chi;
   __shared__ double sh_sum, sh_tot;
   if (threadIdx.x == 0) {
@@ -688,8 +688,8 @@ k_core(const CoreItem* __restrict__ items, int* ival) {
     *it.disc = tot > 0.0 ? (tot - kept) / tot : 0.0;
     ival[it.new_idx] = chi;
     *it.nsv = N;
-    if (!(s0 > 0.0) || !isfinite(s0)) atomicOr(it.flags, 2);
-    if (sh_capped) atomicOr(it.flags, 4);
+    if (!(s0 > 0.0) || !isfinite(s0)) atomicOr(flags, 2);
+    if (sh_capped) atomicOr(flags, 4);
     const double nrm = sqrt(kept);
     for (int i = 0; i < it.chimax; ++i) it.lam[i] = (i < chi) ? sv[order[i]] / nrm : 0.0;
     for (int i = 0; i < N; ++i) it.svals[i] = sv[order[i]];
@@ -773,9 +773,9 @@ k_core(const CoreItem* __restrict__ items, int* ival) {
   }
 }
 
-cudaError_t launch_core(const CoreItem* items, int n_items, int* ival, cudaStream_t s) {
+cudaError_t launch_core(const CoreItem* items, int n_items, int* ival, int* flags_base, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  k_core<<<n_items, 1024, 0, s>>>(items, ival);
+  k_core<<<n_items, 1024, 0, s>>>(items, ival, flags_base);
   return cudaGetLastError();
 }
 

@@ -1,9 +1,9 @@
 // HBM-bound tensor kernels of the bond update and of BP.
 //
-//   k_gram_rows      cv^T cv with FP64 accumulation (Eq. 7, Cholesky-QR Gram)
+//   k_gram_rows      cv^T cv with FP64 accumulation (Eq. 10, Cholesky-QR Gram)
 //   k_reconstruct    psi_new = psi W written in the next update's layout
-//                    (Sec. 2.4 steps 6-7 in Q-less form, Alg. 1 lines 9-12)
-//   k_vec_contract   one-leg vector contraction (single-layer BP, Sec. 2.5)
+//                    (Sec. 2.5 steps 6-7 in Q-less form, Alg. 1 lines 9-12)
+//   k_vec_contract   one-leg vector contraction (single-layer BP, Sec. 2.6)
 //
 // All sizes are read on the device (see common.cuh).  Accumulation: FP32
 // storage accumulates with FP32 FMAs over short runs that are flushed into

@@ -49,6 +49,13 @@ __host__ __device__ inline int gram_rows_splits(long long K, int splits_max) {
 __host__ __device__ inline long long gram_leg_chunks(long long O, long long Q) {
   return Q >= 32 ? O * ((Q + 31) / 32) : (O + (32 / Q) - 1) / (32 / Q);
 }
+// split count of a free-leg Gram from its summed extent K = O * Q (shared by
+// every Gram variant and the reduction, independent of their chunk sizes)
+__host__ __device__ inline int gram_leg_splits_k(long long K, int splits_max) {
+  long long s = K / 2048;
+  if (s < 1) s = 1;
+  return (int)(s < splits_max ? s : splits_max);
+}
 __host__ __device__ inline int gram_leg_splits(long long chunks, int splits_max) {
   long long s = (chunks + 31) / 32;
   if (s < 1) s = 1;

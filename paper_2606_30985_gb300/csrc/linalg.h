@@ -4,9 +4,8 @@
 
 namespace pepo {
 cudaError_t launch_env_factor(const EnvFactorItem* items, int n_items, int chimax, int* ival,
-                              double rel, cudaStream_t s);
-cudaError_t launch_branch(const SiteFacItem* items, int n_items, int* ival, int n_thr,
-                          double ratio_thr, cudaStream_t s);
+                              cudaStream_t s);
+cudaError_t launch_branch(const SiteFacItem* items, int n_items, int* ival, cudaStream_t s);
 template <typename T>
 cudaError_t launch_hh_level(const SiteFacItem* items, int n_items, int level, int grid_x, int nmax,
                             void* const* ptrs, const int* ival, cudaStream_t s);
@@ -17,7 +16,7 @@ cudaError_t launch_form(const SiteFacItem* items, int n_items, int grid_x, const
                         cudaStream_t s);
 cudaError_t launch_factor(const SiteFacItem* items, int n_items, int rmax, int nmax, int* ival,
                           cudaStream_t s);
-cudaError_t launch_core(const CoreItem* items, int n_items, int* ival, cudaStream_t s);
+cudaError_t launch_core(const CoreItem* items, int n_items, int* ival, int* flags_base, cudaStream_t s);
 }  // namespace pepo
 
 namespace pepo {

@@ -2,10 +2,10 @@
 // Trotter step / BP sweep, and the C ABI of include/pepo.h.
 //
 // Plan.  Everything a step launches is decided at init from the geometry
-// alone (Sec. 2.3 four-colour schedule), because live sizes are read on the
+// alone (Sec. 2.4 four-colour schedule), because live sizes are read on the
 // device.  Per colour the bonds are cut into waves that fit the scratch slabs;
 // per wave the launch sequence is (Alg. 1 / Fig. 1, Q-less form):
-//   env factors -> absorb (leg contractions) -> Eq. 7 branch ->
+//   env factors -> absorb (leg contractions) -> Eq. 10 branch ->
 //   [Cholesky-QR: Gram -> reduce] | [Householder: TSQR levels -> extract] ->
 //   gate fold (formG / formB) -> rank-revealing factor -> bond core (SVD,
 //   truncation, lambda, W, messages) -> reconstruct into the next layout ->
@@ -511,6 +511,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
             e.ld = chimax;
             e.chi_idx = chi_idx(bj);
             e.rank_idx = W.rank_idx[j];
+            e.rel = I.cfg.pinv_rel;
             env.push_back(e);
           }
           // absorb chain
@@ -559,6 +560,8 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
           f.perm = sws[v].perm;
           f.rank_idx = sws[v].rankT_idx;
           f.rel = rel_fac;
+          f.n_thr = I.cfg.qr_n_thresh;
+          f.ratio_thr = I.cfg.qr_ratio_thresh;
           fac_index[side] = (int)fac.size();
           fac.push_back(f);
           GramRowsItem g;
@@ -616,7 +619,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
         ci.disc = I.disc + b;
         ci.svals = I.svals + (size_t)b * rmax;
         ci.nsv = I.nsv + b;
-        ci.flags = nullptr;   // patched
+        ci.inst = inst_id;
         ci.eps_cut = I.cfg.eps_cut;
         core_all.push_back(ci);
         moves.push_back(chi_idx(b));
@@ -640,7 +643,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
   (void)inst_id;
 
   // ---- BP waves (double layer): sites grouped by class caps
-  // Double-layer BP plan (Eq. 11).  Every incoming message is eigen-decomposed,
+  // Double-layer BP plan (Eq. 13).  Every incoming message is eigen-decomposed,
   // M_{u->v} = V_u diag(D_u) V_u^T; the site tensor is rotated into the
   // eigenbases of all its legs, psi' = psi x_u V_u^T (deg leg contractions);
   // then each outgoing message is the Gram of psi' over every index but one
@@ -820,7 +823,8 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
       m.msg = mptr(I.msg, id);
       m.vhat = I.vhat + (size_t)id * chimax;
       m.vec = I.vec + (size_t)id * chimax;
-      m.vinit_from = nullptr;
+      m.ld = chimax;
+      m.alpha = I.cfg.bp_alpha;
     }
     I.msgs = stage(P, mi);
     std::vector<SiteScalarItem> ss(I.N);
@@ -836,6 +840,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
       s.vec_in = I.vec + (size_t)msg_in(v, b0) * chimax;
       s.vs = I.vs + v;
       s.fv = I.fv + v;
+      s.ld = chimax;
     }
     I.sscal = stage(P, ss);
     std::vector<EdgeItem> es(I.nb);
@@ -848,6 +853,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
       e.v21 = I.vec + (size_t)(2 * b + 1) * chimax;
       e.ze = I.ze + b;
       e.z2e = I.z2e + b;
+      e.ld = chimax;
     }
     I.escal = stage(P, es);
     std::vector<BetheItem> bi(1);
@@ -879,10 +885,7 @@ void finalize_items(pepo_ctx* c, Planner& P) {
       g[b].rank = c->d_ival + I.grank0 + b;
       g[b].flags = c->d_flags + i;
     }
-    for (int col = 0; col < 4; ++col) {
-      CoreItem* ci = reinterpret_cast<CoreItem*>(P.st.bytes.data() + I.gcore[col].off);
-      for (int k = 0; k < I.gcore[col].n; ++k) ci[k].flags = c->d_flags + i;
-    }
+
   }
 }
 
@@ -1076,11 +1079,11 @@ pepo_status run_gate_wave(pepo_ctx* c, Inst& I, GateWave& w) {
   int gx_leg = (int)std::min<long long>(std::max<long long>(1, big / (long long)(chimax * 64) + 1),
                                         (long long)(2 * 152 * 4 / std::max(1, w.leg[0].n) + 1));
   gx_leg = std::max(gx_leg, 8);
-  LAUNCH_T(K_ENV, nullptr, w.env.n, launch_env_factor(w.env.d, w.env.n, chimax, c->d_ival, I.cfg.pinv_rel, s));
+  LAUNCH_T(K_ENV, nullptr, w.env.n, launch_env_factor(w.env.d, w.env.n, chimax, c->d_ival, s));
   LAUNCH_N(w.copy.n, launch_copy<T>(w.copy.d, w.copy_out.d, w.copy.n, 64, c->d_ptrs, c->d_ival, s));
   for (int r = 0; r < 3; ++r)
     LAUNCH_T(K_LEG, hitems(c, w.leg[r]), w.leg[r].n, leg_dispatch<T>(c, w.leg[r].d, w.leg[r].n, gx_leg, chimax));
-  LAUNCH_N(w.fac.n, launch_branch(w.fac.d, w.fac.n, c->d_ival, I.cfg.qr_n_thresh, I.cfg.qr_ratio_thresh, s));
+  LAUNCH_N(w.fac.n, launch_branch(w.fac.d, w.fac.n, c->d_ival, s));
   {
     int nt = ceil_div(nmax, 64);
     LAUNCH_T(K_GRAM_ROWS, hitems(c, w.gram), w.gram.n, launch_gram_rows<T>(w.gram.d, w.gram.n, nt * (nt + 1) / 2, kGramSplits, 1, c->d_ptrs,
@@ -1162,7 +1165,7 @@ pepo_status do_steps(pepo_ctx* c, int n) {
           pepo_status st = run_gate_wave<T>(c, I, w);
           if (st != PEPO_OK) return st;
         }
-        LAUNCH_T(K_CORE, nullptr, I.gcore[col].n, launch_core(I.gcore[col].d, I.gcore[col].n, c->d_ival, c->stream));
+        LAUNCH_T(K_CORE, nullptr, I.gcore[col].n, launch_core(I.gcore[col].d, I.gcore[col].n, c->d_ival, c->d_flags, c->stream));
         for (auto& w : I.gwaves[col]) {
           pepo_status st = run_gate_wave_tail<T>(c, I, w);
           if (st != PEPO_OK) return st;
@@ -1198,8 +1201,7 @@ pepo_status do_bp(pepo_ctx* c, int* sweeps_out, double* delta_out) {
       any = true;
       pepo_status st = run_bp_waves<T>(c, I, I.bwaves);
       if (st != PEPO_OK) return st;
-      LAUNCH_T(K_MSG, nullptr, I.msgs.n, launch_bp_finish(I.msgs.d, I.msgs.n, c->d_ival, I.cfg.chi_max, I.cfg.bp_alpha,
-                              c->d_delta2, c->d_flags, s));
+      LAUNCH_T(K_MSG, nullptr, I.msgs.n, launch_bp_finish(I.msgs.d, I.msgs.n, c->d_ival, nullptr, c->d_delta2, c->d_flags, s));
     }
     if (!any) break;
     if (cudaMemcpyAsync(hd.data(), c->d_delta2, sizeof(unsigned long long) * c->n_inst,
@@ -1226,7 +1228,7 @@ pepo_status do_bp(pepo_ctx* c, int* sweeps_out, double* delta_out) {
 template <typename T>
 pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
   cudaStream_t s = c->stream;
-  for (auto& I : c->inst) LAUNCH_N(I.msgs.n, launch_sl_init(I.msgs.d, I.msgs.n, c->d_ival, I.cfg.chi_max, s));
+  for (auto& I : c->inst) LAUNCH_N(I.msgs.n, launch_sl_init(I.msgs.d, I.msgs.n, c->d_ival, s));
   std::vector<int> done(c->n_inst, 0), sweeps(c->n_inst, 0);
   std::vector<double> delta(c->n_inst, INFINITY);
   std::vector<unsigned long long> hd(c->n_inst);
@@ -1242,7 +1244,7 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
       any = true;
       pepo_status st = run_sl_pass<T>(c, I);
       if (st != PEPO_OK) return st;
-      LAUNCH_T(K_MSG, nullptr, I.msgs.n, launch_sl_finish(I.msgs.d, I.msgs.n, c->d_ival, I.cfg.bp_alpha, c->d_delta1, s));
+      LAUNCH_T(K_MSG, nullptr, I.msgs.n, launch_sl_finish(I.msgs.d, I.msgs.n, c->d_ival, nullptr, c->d_delta1, s));
     }
     if (!any) break;
     if (cudaMemcpyAsync(hd.data(), c->d_delta1, sizeof(unsigned long long) * c->n_inst,
@@ -1263,8 +1265,8 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
     if (st != PEPO_OK) return st;
     st = run_bp_waves<T>(c, I, I.fwaves);
     if (st != PEPO_OK) return st;
-    LAUNCH_N(I.sscal.n, launch_site_scalars(I.sscal.d, I.sscal.n, c->d_ival, I.cfg.chi_max, s));
-    LAUNCH_N(I.escal.n, launch_edge_scalars(I.escal.d, I.escal.n, c->d_ival, I.cfg.chi_max, s));
+    LAUNCH_N(I.sscal.n, launch_site_scalars(I.sscal.d, I.sscal.n, c->d_ival, s));
+    LAUNCH_N(I.escal.n, launch_edge_scalars(I.escal.d, I.escal.n, c->d_ival, s));
     LAUNCH_N(1, launch_bethe(I.bethe.d, 1, s));
   }
   std::vector<int> flags(c->n_inst);

@@ -58,7 +58,7 @@ def test_required_bytes_valid_and_invalid(lib):
 
 
 def test_required_bytes_follow_the_memory_model(lib):
-    # Eq. 17: the site tensors alone are (4 chi^2 + 2 (k+l-4) chi^3 + (k-2)(l-2) chi^4) * 4 * 4 B
+    # Eq. 15: the site tensors alone are (4 chi^2 + 2 (k+l-4) chi^3 + (k-2)(l-2) chi^4) * 4 * 4 B
     k = l = 10
     chi = 100
     m_psi = (4 * chi ** 2 + 2 * (k + l - 4) * chi ** 3 + (k - 2) * (l - 2) * chi ** 4) * 4 * 4

@@ -113,7 +113,7 @@ def test_zzx_h0_pipeline_is_one():
 
 
 def test_truncation_rule_and_lambda_normalisation():
-    # Eq. 9 / Eq. 10: chi_new <= chi_max and sum lam^2 = 1 on every bond.
+    # Eq. 11 / Eq. 12: chi_new <= chi_max and sum lam^2 = 1 on every bond.
     cfg = dict(Lx=3, Ly=3, J=1.0, h=1.0, dt=0.05, order=1, chi_max=3, bp_tol=1e-8)
     out, net = run.simulate(cfg, nsteps=5)
     for r in out[1:]:
