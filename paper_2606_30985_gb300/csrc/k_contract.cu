@@ -306,7 +306,7 @@ k_gram_leg(const GramLegItem* __restrict__ items, int splits_max, void* const* p
   }
 }
 
-__global__ void k_gram_leg_reduce(const GramLegItem* __restrict__ items, int splits_max,
+__global__ void k_gram_leg_reduce(const GramLegItem* __restrict__ items, int splits_max, int sym,
                                   const int* __restrict__ ival) {
   const GramLegItem it = items[blockIdx.y];
   int d[PEPO_MAXLEG];
@@ -318,9 +318,14 @@ __global__ void k_gram_leg_reduce(const GramLegItem* __restrict__ items, int spl
   for (int i = k + 1; i < it.x.nlegs; ++i) Q *= d[i];
   const int S = gram_leg_splits_k(O * Q, splits_max);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < F * F; e += gridDim.x * blockDim.x) {
+    int fi = e / F, fj = e - fi * F;
     double sum = 0.0;
     for (int s = 0; s < S; ++s) sum += it.partial[(long long)s * F * F + e];
-    int fi = e / F, fj = e - fi * F;
+    if (sym) {
+      double st = 0.0;
+      for (int s = 0; s < S; ++s) st += it.partial[(long long)s * F * F + (long long)fj * F + fi];
+      sum = 0.5 * (sum + st);
+    }
     it.out[(long long)fi * it.ldo + fj] = sum;
   }
 }
@@ -337,10 +342,10 @@ cudaError_t launch_gram_leg(const GramLegItem* items, int n_items, int splits_ma
 }
 
 cudaError_t launch_gram_leg_reduce(const GramLegItem* items, int n_items, int chimax,
-                                   int splits_max, const int* ival, cudaStream_t s) {
+                                   int splits_max, int sym, const int* ival, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   int gx = ceil_div(chimax * chimax, 256);
-  k_gram_leg_reduce<<<dim3(gx, n_items), 256, 0, s>>>(items, splits_max, ival);
+  k_gram_leg_reduce<<<dim3(gx, n_items), 256, 0, s>>>(items, splits_max, sym, ival);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,842 @@
+// Fifth-generation tensor-core (tcgen05) contractions for the FP32-storage
+// mixed-precision mode: the leg contraction and the free-leg Gram of the BP
+// message products (Eq. 13) and of the absorb step (Sec. 2.5 step 1).
+//
+//   k_leg_umma   out[o, i, q] = sum_j A[i, j] in[o, j, q]
+//   k_gram_umma  S[i, i'] = sum_k w_k^2 (Xh[i,k] Xh[i',k] + 2 Xh[i,k] Xl[i',k])
+//                over one K-range (split) of k = (o, q); the reduction sums the
+//                splits and symmetrises: G = (S + S^T) / 2 = sum w^2 X X^T up
+//                to the dropped lo*lo term.
+//
+// Split precision (three-product TF32): every FP32 operand x is split as
+// x = hi + lo with hi = tf32(x) (round to nearest) and lo = x - hi (exact in
+// FP32; the tensor core keeps its leading 11 bits).  A product a*b is taken as
+// ah*bh + ah*bl + al*bh; the dropped al*bl and the truncation of lo are
+// ~2^-21 relative.  For the leg contraction the hi and lo rows of the small
+// matrix A are stacked along N, so one MMA of width 2N gives [ah*bh | ah*bl]
+// and a second of width N adds al*bh to the first half.  For the Gram both
+// operands are the same tile X, stacked as [Xh; Xl] along N: one MMA gives
+// [Xh Xh^T | Xh Xl^T] and the symmetrisation supplies Xl Xh^T.
+//
+// Pipeline (one persistent CTA per SM, 512 threads):
+//   warp 0        allocates tensor memory; lane 0 issues every MMA and the
+//                 commits that release shared-memory stages and hand finished
+//                 accumulators to the epilogue
+//   warps 4-7     epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//                 lanes 32 (w % 4) .. +31), store to global memory (leg) or
+//                 add into compensated FP32 sums in shared memory (Gram)
+//   warps 8-15    converters: coalesced 16-byte global loads, weight, split,
+//                 and 16-byte / conflict-free stores into the K-major
+//                 no-swizzle core-matrix layout the MMA descriptors describe
+// Stages and accumulators are handed over with mbarriers.  Every wait is
+// bounded (a few seconds of %globaltimer); on expiry the kernel records bit 0
+// in *err, every role leaves its loop, the MMA issuer drains its outstanding
+// MMAs (bounded), tensor memory is freed and the kernel returns.
+//
+// Shared-memory operand layout (K-major, no swizzle): a core matrix is 8 rows
+// x 16 bytes (4 TF32 along K) stored contiguously, row r at byte 16 r.  Core
+// matrices adjacent along M/N are SBO = 128 bytes apart, adjacent along K are
+// LBO bytes apart (LBO = 128 x number of M/N core rows), so element (n, k) of
+// an operand sits at (k / 4) LBO + (n / 8) 128 + (n % 8) 16 + (k % 4) 4.
+#include "kernels.h"
+
+namespace pepo {
+namespace um {
+
+constexpr int kThreads = 512;
+constexpr int kConv = 256;              // converter threads (warps 8..15)
+constexpr int kM = 128;                 // accumulator rows = TMEM lanes
+constexpr int kKC = 32;                 // K values per staged chunk
+constexpr int kTmemCols = 512;          // two accumulators of 256 columns
+constexpr int kRun = 8;                 // Gram chunks per FP32 accumulator run
+constexpr unsigned long long kTimeoutNs = 4000000000ull;
+constexpr int kMaxItems = 512;
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase of parity `parity`; false once the CTA aborts.
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err) {
+  if (mbar_try(b, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (true) {
+    if (mbar_try(b, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > kTimeoutNs) {
+      *abort_flag = 1;
+      atomicOr(err, 1);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)),
+               "r"(kTmemCols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version of the sm_100 family
+  return d;
+}
+// instruction descriptor: kind::tf32, FP32 accumulator, A and B TF32 K-major
+__device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+               : "memory");
+}
+// 32 TMEM lanes x 16 consecutive 32-bit columns; thread t receives lane
+// (lane base + t).  The registers are valid after tmem_wait16.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+// completes outstanding tcgen05.ld; the registers are threaded through so no
+// use of them is scheduled before the wait
+__device__ __forceinline__ void tmem_wait16(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15])
+               :
+               : "memory");
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ float pick(const float4& v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ============================================================ leg contraction
+struct LegDims {
+  long long O, Q, R, tiles;
+  int J, Jout, K8, N16;
+  const float* in;
+  float* out;
+  const double* A;
+  int lda;
+};
+
+__device__ inline void leg_dims(const LegItem& it, void* const* ptrs, const int* ival, LegDims& L) {
+  int d[PEPO_MAXLEG];
+  for (int k = 0; k < PEPO_MAXLEG; ++k) d[k] = (k < it.in.nlegs) ? ival[it.in.dim[k]] : 1;
+  const int k = it.leg;
+  L.J = d[k];
+  L.Jout = ival[it.out_dim];
+  L.O = 1;
+  L.Q = 4;
+  for (int i = 0; i < k; ++i) L.O *= d[i];
+  for (int i = k + 1; i < it.in.nlegs; ++i) L.Q *= d[i];
+  L.R = L.O * L.Q;
+  L.tiles = (L.R + kM - 1) / kM;
+  L.K8 = round_up(L.J, 8);
+  L.N16 = round_up(L.Jout, 16);
+  L.in = static_cast<const float*>(ptrs[it.in.ref]);
+  L.out = static_cast<float*>(ptrs[it.out_ref]);
+  L.A = it.A;
+  L.lda = it.lda;
+}
+
+// Shared-memory plan of k_leg_umma for a given chi bound.
+struct LegSmem {
+  int k8max, n16max, stages;
+  size_t b_bytes, stage_bytes, bar_off, total;
+};
+__host__ __device__ inline LegSmem leg_smem(int chimax) {
+  LegSmem p;
+  p.k8max = round_up(chimax, 8);
+  p.n16max = round_up(chimax, 16);
+  p.b_bytes = (size_t)(p.k8max / 4) * (2 * p.n16max / 8) * 128;   // [Ah; Al] of the small matrix
+  p.stage_bytes = 2 * (size_t)(kKC / 4) * (kM / 8) * 128;          // hi + lo tile, 2 x 16 KB
+  const size_t budget = 227 * 1024 - 1024 - 8 * kMaxItems - 512;
+  p.stages = (int)((budget - p.b_bytes) / p.stage_bytes);
+  if (p.stages > 4) p.stages = 4;
+  p.bar_off = p.b_bytes + p.stages * p.stage_bytes;
+  p.total = p.bar_off + 512 + 8 * (size_t)(kMaxItems + 1) + 1024;   // + alignment slack
+  return p;
+}
+
+struct LegCursor {   // position in the CTA's tile range
+  int item;
+  long long tile;    // tile within the item
+  long long left;    // tiles left for this CTA
+  LegDims L;
+};
+
+__device__ inline bool cursor_start(LegCursor& c, const long long* toff, int n, long long t0, long long t1,
+                                    const LegItem* items, void* const* ptrs, const int* ival) {
+  c.left = t1 - t0;
+  if (c.left <= 0) return false;
+  int i = 0;
+  while (i + 1 < n && toff[i + 1] <= t0) ++i;
+  c.item = i;
+  c.tile = t0 - toff[i];
+  leg_dims(items[i], ptrs, ival, c.L);
+  return true;
+}
+// advance to the next tile; returns true when the item changed
+__device__ inline bool cursor_next(LegCursor& c, const long long* toff, int n, const LegItem* items,
+                                   void* const* ptrs, const int* ival) {
+  --c.left;
+  ++c.tile;
+  bool changed = false;
+  while (c.left > 0 && c.tile >= c.L.tiles && c.item + 1 < n) {
+    ++c.item;
+    c.tile = 0;
+    leg_dims(items[c.item], ptrs, ival, c.L);
+    changed = true;
+  }
+  return changed;
+}
+
+struct LegBars {
+  uint64_t full[4], empty[4], accfull[2], accempty[2], bfull, bfree, drain;
+  uint32_t tmem;
+  int abort_flag;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* const* ptrs,
+           const int* __restrict__ ival, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const LegSmem P = leg_smem(chimax);
+  unsigned char* Bs = smem;                          // [Ah; Al] small matrix
+  unsigned char* As = smem + P.b_bytes;              // stages: hi tile, lo tile
+  LegBars* bars = reinterpret_cast<LegBars*>(smem + P.bar_off);
+  long long* toff = reinterpret_cast<long long*>(smem + P.bar_off + 512);
+  volatile int* abort_flag = &bars->abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int NS = P.stages;
+
+  if (tid == 0) {
+    long long acc = 0;
+    for (int i = 0; i < n_items; ++i) {
+      toff[i] = acc;
+      LegDims L;
+      leg_dims(items[i], ptrs, ival, L);
+      acc += L.tiles;
+    }
+    toff[n_items] = acc;
+    for (int s = 0; s < NS; ++s) { mbar_init(&bars->full[s], kConv); mbar_init(&bars->empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&bars->accfull[b], 1); mbar_init(&bars->accempty[b], 128); }
+    mbar_init(&bars->bfull, kConv);
+    mbar_init(&bars->bfree, 1);
+    mbar_init(&bars->drain, 1);
+    bars->abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(&bars->tmem);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = bars->tmem;
+  const long long T = toff[n_items];
+  const long long t0 = T * blockIdx.x / gridDim.x, t1 = T * (blockIdx.x + 1) / gridDim.x;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      LegCursor c;
+      bool live = cursor_start(c, toff, n_items, t0, t1, items, ptrs, ival);
+      long long cc = 0, tc = 0;
+      int item_n = 0;
+      bool ok = true;
+      if (live) ok = mbar_wait(&bars->bfull, 0, abort_flag, err);
+      while (live && ok) {
+        const int b = (int)(tc & 1);
+        if (!mbar_wait(&bars->accempty[b], (uint32_t)(((tc >> 1) & 1) ^ 1), abort_flag, err)) break;
+        tc_after();
+        const uint32_t d_tmem = tmem + (uint32_t)(b * 256);
+        const int N16 = c.L.N16, K8 = c.L.K8;
+        const uint32_t lbo_b = (uint32_t)(2 * N16 / 8) * 128;
+        const uint32_t id_wide = idesc_tf32(kM, 2 * N16), id_half = idesc_tf32(kM, N16);
+        const int nkc = (K8 + kKC - 1) / kKC;
+        for (int kc = 0; kc < nkc && ok; ++kc, ++cc) {
+          const int s = (int)(cc % NS);
+          if (!mbar_wait(&bars->full[s], (uint32_t)((cc / NS) & 1), abort_flag, err)) { ok = false; break; }
+          tc_after();
+          const uint32_t a_hi = su32(As + (size_t)s * P.stage_bytes);
+          const uint32_t a_lo = a_hi + (uint32_t)(P.stage_bytes / 2);
+          const uint32_t b0 = su32(Bs);
+          const int ksteps = min(kKC, K8 - kc * kKC) / 8;
+          for (int st = 0; st < ksteps; ++st) {
+            const uint32_t koff_a = (uint32_t)(st * 2) * 2048u;
+            const uint32_t koff_b = (uint32_t)(kc * 8 + st * 2) * lbo_b;
+            const uint64_t dah = sdesc(a_hi + koff_a, 2048u, 128u);
+            const uint64_t dal = sdesc(a_lo + koff_a, 2048u, 128u);
+            const uint64_t db = sdesc(b0 + koff_b, lbo_b, 128u);
+            mma_tf32(d_tmem, dah, db, id_wide, (kc > 0 || st > 0) ? 1u : 0u);
+            mma_tf32(d_tmem, dal, db, id_half, 1u);
+          }
+          mma_commit(&bars->empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&bars->accfull[b]);
+        ++tc;
+        const bool last = (c.left == 1);
+        const bool changed = cursor_next(c, toff, n_items, items, ptrs, ival);
+        if (changed || last) mma_commit(&bars->bfree);
+        if (last) break;
+        if (changed) {
+          ++item_n;
+          if (!mbar_wait(&bars->bfull, (uint32_t)(item_n & 1), abort_flag, err)) break;
+          tc_after();
+        }
+      }
+      // every issued MMA completes before tensor memory is released
+      mma_commit(&bars->drain);
+      mbar_wait(&bars->drain, 0, abort_flag, err);
+    }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 8) {
+    // -------------------------------------------------------------- epilogue
+    LegCursor c;
+    bool live = cursor_start(c, toff, n_items, t0, t1, items, ptrs, ival);
+    const int row = 32 * (warp & 3) + lane;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    long long tc = 0;
+    while (live) {
+      const int b = (int)(tc & 1);
+      if (!mbar_wait(&bars->accfull[b], (uint32_t)((tc >> 1) & 1), abort_flag, err)) break;
+      tc_after();
+      const LegDims& L = c.L;
+      const long long rg = c.tile * kM + row;
+      const bool valid = rg < L.R;
+      long long o = 0, q = 0;
+      if (valid) { o = rg / L.Q; q = rg - o * L.Q; }
+      float* dst = L.out + (o * L.Jout) * L.Q + q;
+      const uint32_t tbase = tmem + lane_base + (uint32_t)(b * 256);
+      for (int c0 = 0; c0 < L.N16; c0 += 16) {
+        uint32_t v1[16], v2[16];
+        tmem_ld16(tbase + (uint32_t)c0, v1);
+        tmem_wait16(v1);
+        tmem_ld16(tbase + (uint32_t)(L.N16 + c0), v2);
+        tmem_wait16(v2);
+        if (valid) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int col = c0 + i;
+            if (col < L.Jout) dst[(long long)col * L.Q] = __uint_as_float(v1[i]) + __uint_as_float(v2[i]);
+          }
+        }
+      }
+      tc_before();
+      mbar_arrive(&bars->accempty[b]);
+      ++tc;
+      if (c.left == 1) break;
+      cursor_next(c, toff, n_items, items, ptrs, ival);
+    }
+  } else if (warp >= 8) {
+    // ------------------------------------------------------------ converters
+    const int ct = tid - 256, cw = ct >> 5;
+    const int jj = lane & 3, rq = (lane >> 2) & 1, a = lane >> 3;
+    const int r = 32 * (cw & 3) + 8 * a + 4 * rq;   // this thread's 4-row group
+    const int jq0 = cw >> 2;                        // j quads jq0, jq0 + 2, +4, +6
+    LegCursor c;
+    bool live = cursor_start(c, toff, n_items, t0, t1, items, ptrs, ival);
+    long long cc = 0;
+    int item_n = 0;
+    bool need_b = true;
+    while (live) {
+      const LegDims& L = c.L;
+      if (need_b) {
+        if (item_n > 0 && !mbar_wait(&bars->bfree, (uint32_t)((item_n - 1) & 1), abort_flag, err)) break;
+        // [Ah; Al]: rows n < N16 hold hi(A[n, :]), rows N16 + n hold lo(A[n, :])
+        const uint32_t lbo_b = (uint32_t)(2 * L.N16 / 8) * 128;
+        for (int e = ct; e < L.N16 * L.K8; e += kConv) {
+          const int n = e / L.K8, j = e - n * L.K8;
+          float x = 0.f;
+          if (n < L.Jout && j < L.J) x = (float)L.A[(long long)n * L.lda + j];
+          const float h = tf32_hi(x);
+          const float l = x - h;
+          const size_t kb = (size_t)(j >> 2) * lbo_b + (size_t)(j & 3) * 4;
+          *reinterpret_cast<float*>(Bs + kb + (size_t)(n >> 3) * 128 + (size_t)(n & 7) * 16) = h;
+          const int n2 = n + L.N16;
+          *reinterpret_cast<float*>(Bs + kb + (size_t)(n2 >> 3) * 128 + (size_t)(n2 & 7) * 16) = l;
+        }
+        fence_async_smem();
+        mbar_arrive(&bars->bfull);
+        need_b = false;
+      }
+      const long long rg = c.tile * kM + r;
+      const bool valid = rg < L.R;
+      const float* src = L.in;
+      if (valid) {
+        const long long o = rg / L.Q, q = rg - o * L.Q;
+        src = L.in + o * L.J * L.Q + q;
+      }
+      const int nkc = (L.K8 + kKC - 1) / kKC;
+      bool ok = true;
+      for (int kc = 0; kc < nkc; ++kc, ++cc) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = kc * kKC + 4 * (jq0 + 2 * u) + jj;
+          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (valid && j < L.J) v[u] = __ldg(reinterpret_cast<const float4*>(src + (long long)j * L.Q));
+        }
+        const int s = (int)(cc % NS);
+        if (!mbar_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
+        unsigned char* hi = As + (size_t)s * P.stage_bytes;
+        unsigned char* lo = hi + P.stage_bytes / 2;
+        const size_t rbase = (size_t)(r >> 3) * 128 + (size_t)jj * 4;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const size_t kb = (size_t)(jq0 + 2 * u) * 2048 + rbase;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int e = (i + a) & 3;        // rotation keeps the 32 lanes on 32 banks
+            const float x = pick(v[u], e);
+            const float h = tf32_hi(x);
+            const size_t off = kb + (size_t)(4 * rq + e) * 16;
+            *reinterpret_cast<float*>(hi + off) = h;
+            *reinterpret_cast<float*>(lo + off) = x - h;
+          }
+        }
+        fence_async_smem();
+        mbar_arrive(&bars->full[s]);
+      }
+      if (!ok) break;
+      if (c.left == 1) break;
+      if (cursor_next(c, toff, n_items, items, ptrs, ival)) { ++item_n; need_b = true; }
+    }
+  }
+  tc_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_after();
+    tmem_free(tmem);
+  }
+}
+
+// ============================================================ Gram (free leg)
+struct GramDims {
+  long long O, Q, NC;
+  int F, F8, S, k, nlegs, d[PEPO_MAXLEG];
+  bool wide;
+  long long qpc;
+  int opc;
+  const float* X;
+  double* partial;
+};
+
+__device__ inline void gram_dims(const GramLegItem& it, void* const* ptrs, const int* ival, int splits_max,
+                                 GramDims& G) {
+  G.nlegs = it.x.nlegs;
+  for (int k = 0; k < PEPO_MAXLEG; ++k) G.d[k] = (k < it.x.nlegs) ? ival[it.x.dim[k]] : 1;
+  G.k = it.leg;
+  G.F = G.d[G.k];
+  G.F8 = round_up(G.F, 8);
+  G.O = 1;
+  G.Q = 4;
+  for (int i = 0; i < G.k; ++i) G.O *= G.d[i];
+  for (int i = G.k + 1; i < G.nlegs; ++i) G.Q *= G.d[i];
+  G.NC = gram_leg_chunks(G.O, G.Q);
+  G.S = gram_leg_splits_k(G.O * G.Q, splits_max);
+  G.wide = G.Q >= kKC;
+  G.qpc = G.wide ? (G.Q + kKC - 1) / kKC : 0;
+  G.opc = G.wide ? 1 : (int)(kKC / G.Q);
+  G.X = static_cast<const float*>(ptrs[it.x.ref]);
+  G.partial = it.partial;
+}
+
+struct GramSmem {
+  int f8max, stages, ld;
+  size_t stage_bytes, acc_off, bar_off, total;
+};
+__host__ __device__ inline GramSmem gram_smem(int chimax) {
+  GramSmem p;
+  p.f8max = round_up(chimax, 8);
+  p.stage_bytes = (size_t)(kKC / 4) * (2 * p.f8max / 8) * 128;   // [Xh; Xl]
+  p.ld = p.f8max + 1;                                               // odd row stride (words)
+  const size_t acc_bytes = 2 * (size_t)p.f8max * p.ld * 4;          // sum + compensation
+  const size_t pad = 2048;                                          // A-operand rows past 2 F8
+  const size_t budget = 227 * 1024 - 1024 - 8 * (kMaxItems + 1) - 512 - 1024;
+  p.stages = (int)((budget - acc_bytes - pad) / p.stage_bytes);
+  if (p.stages > 4) p.stages = 4;
+  p.acc_off = p.stages * p.stage_bytes + pad;
+  p.bar_off = p.acc_off + acc_bytes;
+  p.total = p.bar_off + 512 + 8 * (size_t)(kMaxItems + 1) + 1024 + 1024;
+  return p;
+}
+
+struct GramCursor {
+  int item, s;
+  long long c, c1;    // current chunk, end of the unit's range
+  GramDims G;
+};
+
+// unit u -> (item, split) through the prefix table of split counts
+__device__ inline void gram_unit(GramCursor& g, long long u, const long long* uoff, int n,
+                                 const GramLegItem* items, void* const* ptrs, const int* ival, int splits_max) {
+  int i = 0;
+  while (i + 1 < n && uoff[i + 1] <= u) ++i;
+  if (i != g.item) {
+    g.item = i;
+    gram_dims(items[i], ptrs, ival, splits_max, g.G);
+  }
+  g.s = (int)(u - uoff[i]);
+  g.c = g.G.NC * g.s / g.G.S;
+  g.c1 = g.G.NC * (g.s + 1) / g.G.S;
+}
+
+struct GramBars {
+  uint64_t full[4], empty[4], accfull[2], accempty[2], drain;
+  uint32_t tmem;
+  int abort_flag;
+};
+
+// odometer over the legs other than the free leg, used to form the weight
+// prod_{u != k} sw[u][j_u] of one 4-wide (Pauli) column group
+struct Odo {
+  int dig[PEPO_MAXLEG];
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, int chimax, void* const* ptrs,
+            const int* __restrict__ ival, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const GramSmem P = gram_smem(chimax);
+  unsigned char* Xs = smem;
+  float* acc = reinterpret_cast<float*>(smem + P.acc_off);
+  float* cmp = acc + (size_t)P.f8max * P.ld;
+  GramBars* bars = reinterpret_cast<GramBars*>(smem + P.bar_off);
+  long long* uoff = reinterpret_cast<long long*>(smem + P.bar_off + 512);
+  volatile int* abort_flag = &bars->abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int NS = P.stages;
+
+  if (tid == 0) {
+    long long a = 0;
+    for (int i = 0; i < n_items; ++i) {
+      uoff[i] = a;
+      GramDims G;
+      gram_dims(items[i], ptrs, ival, splits_max, G);
+      a += G.S;
+    }
+    uoff[n_items] = a;
+    for (int s = 0; s < NS; ++s) { mbar_init(&bars->full[s], kConv); mbar_init(&bars->empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&bars->accfull[b], 1); mbar_init(&bars->accempty[b], 128); }
+    mbar_init(&bars->drain, 1);
+    bars->abort_flag = 0;
+    fence_mbar_init();
+  }
+  // zero the operand stages once: rows [F, F8) stay zero-filled by the
+  // converters, everything else is rewritten before use
+  for (size_t e = tid; e < (size_t)NS * P.stage_bytes / 16; e += kThreads)
+    reinterpret_cast<float4*>(Xs)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (warp == 0) tmem_alloc(&bars->tmem);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = bars->tmem;
+  const long long U = uoff[n_items];
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      GramCursor g;
+      g.item = -1;
+      long long cc = 0, rc = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < U && ok; u += gridDim.x) {
+        gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max);
+        const int F8 = g.G.F8;
+        const uint32_t lbo = (uint32_t)(2 * F8 / 8) * 128;
+        const uint32_t id = idesc_tf32(kM, 2 * F8);
+        for (long long c = g.c; c < g.c1 && ok;) {
+          const int b = (int)(rc & 1);
+          if (!mbar_wait(&bars->accempty[b], (uint32_t)(((rc >> 1) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
+          tc_after();
+          const uint32_t d_tmem = tmem + (uint32_t)(b * 256);
+          const long long cend = min(g.c1, c + kRun);
+          for (long long cr = c; cr < cend; ++cr, ++cc) {
+            const int s = (int)(cc % NS);
+            if (!mbar_wait(&bars->full[s], (uint32_t)((cc / NS) & 1), abort_flag, err)) { ok = false; break; }
+            tc_after();
+            const uint32_t x0 = su32(Xs + (size_t)s * P.stage_bytes);
+#pragma unroll
+            for (int st = 0; st < kKC / 8; ++st) {
+              const uint64_t d = sdesc(x0 + (uint32_t)(2 * st) * lbo, lbo, 128u);
+              mma_tf32(d_tmem, d, d, id, (cr > c || st > 0) ? 1u : 0u);
+            }
+            mma_commit(&bars->empty[s]);
+          }
+          if (!ok) break;
+          mma_commit(&bars->accfull[b]);
+          ++rc;
+          c = cend;
+        }
+      }
+      mma_commit(&bars->drain);
+      mbar_wait(&bars->drain, 0, abort_flag, err);
+    }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 8) {
+    // -------------------------------------------------------------- epilogue
+    const int row = 32 * (warp & 3) + lane;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    GramCursor g;
+    g.item = -1;
+    long long rc = 0;
+    bool ok = true;
+    for (long long u = blockIdx.x; u < U && ok; u += gridDim.x) {
+      gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max);
+      const int F = g.G.F, F8 = g.G.F8;
+      const bool live_row = row < F;
+      if (live_row)
+        for (int c0 = 0; c0 < F8; ++c0) { acc[(size_t)row * P.ld + c0] = 0.f; cmp[(size_t)row * P.ld + c0] = 0.f; }
+      for (long long c = g.c; c < g.c1; c += kRun) {
+        const int b = (int)(rc & 1);
+        if (!mbar_wait(&bars->accfull[b], (uint32_t)((rc >> 1) & 1), abort_flag, err)) { ok = false; break; }
+        tc_after();
+        const uint32_t tbase = tmem + lane_base + (uint32_t)(b * 256);
+        for (int c0 = 0; c0 < F8; c0 += 16) {
+          uint32_t v1[16], v2[16];
+          tmem_ld16(tbase + (uint32_t)c0, v1);
+          tmem_wait16(v1);
+          tmem_ld16(tbase + (uint32_t)(F8 + c0), v2);
+          tmem_wait16(v2);
+          if (live_row) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int col = c0 + i;
+              if (col < F) {
+                // compensated (Kahan) FP32 sum of S += Xh Xh^T + 2 Xh Xl^T
+                float* pa = acc + (size_t)row * P.ld + col;
+                float* pc = cmp + (size_t)row * P.ld + col;
+                const float y = (__uint_as_float(v1[i]) + 2.f * __uint_as_float(v2[i])) - *pc;
+                const float t = *pa + y;
+                *pc = (t - *pa) - y;
+                *pa = t;
+              }
+            }
+          }
+        }
+        tc_before();
+        mbar_arrive(&bars->accempty[b]);
+        ++rc;
+      }
+      if (!ok) break;
+      if (live_row) {
+        double* P0 = g.G.partial + (size_t)g.s * F * F + (size_t)row * F;
+        for (int col = 0; col < F; ++col)
+          P0[col] = (double)acc[(size_t)row * P.ld + col] - (double)cmp[(size_t)row * P.ld + col];
+      }
+    }
+  } else if (warp >= 8) {
+    // ------------------------------------------------------------ converters
+    const int ct = tid - 256, cw = ct >> 5;
+    const int kq = 4 * (cw & 1) + (lane >> 3);     // this thread's 4-wide K group of a chunk
+    const int i8_0 = cw >> 1;                      // row groups i8_0 + 4 u, u = 0..3
+    const int il = lane & 7;
+    GramCursor g;
+    g.item = -1;
+    long long cc = 0;
+    int wt_item = -1;
+    const double* sw[PEPO_MAXLEG];
+    unsigned dd[PEPO_MAXLEG];
+    for (long long u = blockIdx.x; u < U; u += gridDim.x) {
+      gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max);
+      const GramDims& G = g.G;
+      if (g.item != wt_item) {
+        const GramLegItem& it = items[g.item];
+#pragma unroll
+        for (int uu = 0; uu < PEPO_MAXLEG; ++uu) {
+          sw[uu] = (uu < G.nlegs && uu != G.k) ? it.sw[uu] : nullptr;
+          dd[uu] = (unsigned)G.d[uu];
+        }
+        wt_item = g.item;
+      }
+      const int F = G.F, F8 = G.F8;
+      const size_t lbo = (size_t)(2 * F8 / 8) * 128;
+      bool ok = true;
+      long long o_w = -1;     // o of the cached outer weight
+      float w_out = 0.f;
+      for (long long c = g.c; c < g.c1; ++c, ++cc) {
+        // k group of this thread: legs before the free leg give o, legs after give q
+        long long o, q;
+        bool kvalid;
+        if (G.wide) {
+          o = c / G.qpc;
+          q = (c - o * G.qpc) * kKC + 4 * kq;
+          kvalid = q < G.Q;
+        } else {
+          o = c * G.opc + (4 * kq) / G.Q;
+          q = (4 * kq) % G.Q;
+          kvalid = (4 * kq) / G.Q < G.opc && o < G.O;
+        }
+        // weight prod_{u != k} sw[u][j_u]: outer legs from o (cached per o),
+        // inner legs from q / 4 (the Pauli index shares one weight)
+        float w = 0.f;
+        if (kvalid) {
+          if (o != o_w) {
+            float wo = 1.f;
+            unsigned t = (unsigned)o;
+#pragma unroll
+            for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
+              if (uu < G.k) {
+                const unsigned j = t % dd[uu];
+                t /= dd[uu];
+                if (sw[uu]) wo *= (float)sw[uu][j];
+              }
+            }
+            w_out = wo;
+            o_w = o;
+          }
+          float wi = 1.f;
+          unsigned t = (unsigned)(q >> 2);
+#pragma unroll
+          for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
+            if (uu > G.k && uu < G.nlegs) {
+              const unsigned j = t % dd[uu];
+              t /= dd[uu];
+              if (sw[uu]) wi *= (float)sw[uu][j];
+            }
+          }
+          w = w_out * wi;
+        }
+        float4 v[4];
+#pragma unroll
+        for (int u4 = 0; u4 < 4; ++u4) {
+          const int i = 8 * (i8_0 + 4 * u4) + il;
+          v[u4] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (kvalid && i < F) v[u4] = __ldg(reinterpret_cast<const float4*>(G.X + (o * F + i) * G.Q + q));
+        }
+        const int s = (int)(cc % NS);
+        if (!mbar_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
+        unsigned char* st = Xs + (size_t)s * P.stage_bytes + (size_t)kq * lbo;
+#pragma unroll
+        for (int u4 = 0; u4 < 4; ++u4) {
+          const int i = 8 * (i8_0 + 4 * u4) + il;
+          if (i < F8) {
+            const float4 x = make_float4(v[u4].x * w, v[u4].y * w, v[u4].z * w, v[u4].w * w);
+            const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+            const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+            const int i2 = i + F8;
+            *reinterpret_cast<float4*>(st + (size_t)(i >> 3) * 128 + (size_t)(i & 7) * 16) = h;
+            *reinterpret_cast<float4*>(st + (size_t)(i2 >> 3) * 128 + (size_t)(i2 & 7) * 16) = l;
+          }
+        }
+        fence_async_smem();
+        mbar_arrive(&bars->full[s]);
+      }
+      if (!ok) break;
+    }
+  }
+  tc_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_after();
+    tmem_free(tmem);
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace um
+
+bool umma_supported(int chimax) { return chimax >= 1 && chimax <= 128; }
+
+cudaError_t launch_leg_umma(const LegItem* items, int n_items, int chimax, void* const* ptrs, const int* ival,
+                            int* err, cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  if (!umma_supported(chimax)) return cudaErrorInvalidValue;
+  const um::LegSmem P = um::leg_smem(chimax);
+  if (P.stages < 2) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(um::k_leg_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.total);
+  if (e != cudaSuccess) return e;
+  for (int i0 = 0; i0 < n_items; i0 += um::kMaxItems) {
+    const int n = std::min(um::kMaxItems, n_items - i0);
+    um::k_leg_umma<<<um::sm_count(), um::kThreads, P.total, s>>>(items + i0, n, chimax, ptrs, ival, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_gram_umma(const GramLegItem* items, int n_items, int splits_max, int chimax,
+                             void* const* ptrs, const int* ival, int* err, cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  if (!umma_supported(chimax)) return cudaErrorInvalidValue;
+  const um::GramSmem P = um::gram_smem(chimax);
+  if (P.stages < 2) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(um::k_gram_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.total);
+  if (e != cudaSuccess) return e;
+  for (int i0 = 0; i0 < n_items; i0 += um::kMaxItems) {
+    const int n = std::min(um::kMaxItems, n_items - i0);
+    um::k_gram_umma<<<um::sm_count(), um::kThreads, P.total, s>>>(items + i0, n, splits_max, chimax, ptrs, ival,
+                                                                   err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace pepo

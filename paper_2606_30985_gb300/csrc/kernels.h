@@ -23,8 +23,9 @@ cudaError_t launch_gram_leg(const GramLegItem* items, int n_items, int splits_ma
 template <typename T>
 cudaError_t launch_permute(const void* in, void* out, int nlegs, const int* dims_canon, const int* perm,
                            int to_layout, cudaStream_t s);
+// sum of the per-split partials; sym = 1 symmetrises the sum as (S + S^T) / 2
 cudaError_t launch_gram_leg_reduce(const GramLegItem* items, int n_items, int chimax,
-                                   int splits_max, const int* ival, cudaStream_t s);
+                                   int splits_max, int sym, const int* ival, cudaStream_t s);
 template <typename T>
 cudaError_t launch_reconstruct(const ReconItem* items, int n_items, int grid_x, int ntile_max,
                                void* const* ptrs, const int* ival, cudaStream_t s);
@@ -37,6 +38,15 @@ cudaError_t launch_leg_contract_tc(const LegItem* items, int n_items, int grid_x
                                    const int* ival, cudaStream_t s);
 cudaError_t launch_gram_leg_tc(const GramLegItem* items, int n_items, int splits_max, void* const* ptrs,
                                const int* ival, cudaStream_t s);
+
+// ---- k_umma.cu (FP32 storage, TF32x3 on tcgen05 tensor cores, chi <= 128)
+bool umma_supported(int chimax);
+// err: device int; bit 0 is set when a pipeline wait of the kernel expired
+cudaError_t launch_leg_umma(const LegItem* items, int n_items, int chimax, void* const* ptrs, const int* ival,
+                            int* err, cudaStream_t s);
+// writes per-split partial sums S; the reduction with sym = 1 returns (S + S^T) / 2
+cudaError_t launch_gram_umma(const GramLegItem* items, int n_items, int splits_max, int chimax,
+                             void* const* ptrs, const int* ival, int* err, cudaStream_t s);
 
 // Split count shared by the Gram kernels and their reductions.
 __host__ __device__ inline int gram_rows_splits(long long K, int splits_max) {

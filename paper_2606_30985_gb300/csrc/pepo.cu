@@ -158,6 +158,7 @@ struct pepo_ctx {
   unsigned long long* d_delta2 = nullptr;
   unsigned long long* d_delta1 = nullptr;
   int* d_flags = nullptr;
+  int* d_kerr = nullptr;   // bit 0: a tensor-core pipeline wait expired
   char* d_items = nullptr;
   long long launches = 0;
   std::string err;
@@ -930,6 +931,7 @@ size_t layout_arena(pepo_ctx* c, char* base, Planner* keep) {
   c->d_delta2 = cv.take<unsigned long long>(c->n_inst);
   c->d_delta1 = cv.take<unsigned long long>(c->n_inst);
   c->d_flags = cv.take<int>(c->n_inst);
+  c->d_kerr = cv.take<int>(1);
   c->d_items = cv.take<char>(P.st.bytes.size() + 256);
   size_t total = cv.off + kAlign;
   if (keep) *keep = std::move(P);
@@ -1056,17 +1058,22 @@ void timing_harvest(pepo_ctx* c) {
   } while (0)
 #define LAUNCH_N(n, expr) LAUNCH_T(K_OTHER, nullptr, n, expr)
 
-// tensor-core split-precision kernels for the FP32-storage mixed mode
+// tensor-core split-precision kernels for the FP32-storage mixed mode:
+// tcgen05 (TMEM accumulators) for chi_max <= 128, else the FP32 SIMT kernels
+template <typename T>
+bool use_umma(const pepo_ctx* c, int chimax) {
+  return sizeof(T) == 4 && (c->prec == PEPO_TF32X3 || c->prec == PEPO_BF16X3) && umma_supported(chimax);
+}
 template <typename T>
 cudaError_t leg_dispatch(pepo_ctx* c, const LegItem* items, int n, int gx, int chimax) {
-  if (sizeof(T) == 4 && (c->prec == PEPO_TF32X3 || c->prec == PEPO_BF16X3))
-    return launch_leg_contract_tc(items, n, gx, c->d_ptrs, c->d_ival, c->stream);
+  if (use_umma<T>(c, chimax))
+    return launch_leg_umma(items, n, chimax, c->d_ptrs, c->d_ival, c->d_kerr, c->stream);
   return launch_leg_contract<T>(items, n, gx, chimax, c->d_ptrs, c->d_ival, c->stream);
 }
 template <typename T>
 cudaError_t gram_leg_dispatch(pepo_ctx* c, const GramLegItem* items, int n, int chimax) {
-  if (sizeof(T) == 4 && (c->prec == PEPO_TF32X3 || c->prec == PEPO_BF16X3))
-    return launch_gram_leg_tc(items, n, kLegSplits, c->d_ptrs, c->d_ival, c->stream);
+  if (use_umma<T>(c, chimax))
+    return launch_gram_umma(items, n, kLegSplits, chimax, c->d_ptrs, c->d_ival, c->d_kerr, c->stream);
   return launch_gram_leg<T>(items, n, kLegSplits, chimax, c->d_ptrs, c->d_ival, c->stream);
 }
 
@@ -1141,7 +1148,8 @@ pepo_status run_bp_waves(pepo_ctx* c, Inst& I, std::vector<BpWave>& waves) {
     LAUNCH_T(K_GRAM_LEG, hitems(c, w.gram), w.gram.n,
              gram_leg_dispatch<T>(c, w.gram.d, w.gram.n, chimax));
     LAUNCH_T(K_GRAM_LEG_RED, nullptr, w.gram.n,
-             launch_gram_leg_reduce(w.gram.d, w.gram.n, chimax, kLegSplits, c->d_ival, s));
+             launch_gram_leg_reduce(w.gram.d, w.gram.n, chimax, kLegSplits, use_umma<T>(c, chimax) ? 1 : 0,
+                                    c->d_ival, s));
     LAUNCH_T(K_MSG, nullptr, w.rot.n, launch_rotate_back(w.rot.d, w.rot.n, chimax, c->d_ival, s));
   }
   return PEPO_OK;
@@ -1204,10 +1212,13 @@ pepo_status do_bp(pepo_ctx* c, int* sweeps_out, double* delta_out) {
       LAUNCH_T(K_MSG, nullptr, I.msgs.n, launch_bp_finish(I.msgs.d, I.msgs.n, c->d_ival, nullptr, c->d_delta2, c->d_flags, s));
     }
     if (!any) break;
+    int kerr = 0;
     if (cudaMemcpyAsync(hd.data(), c->d_delta2, sizeof(unsigned long long) * c->n_inst,
                         cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&kerr, c->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return fail(c, PEPO_E_CUDA, "BP delta readback: %s", cudaGetErrorString(cudaGetLastError()));
+    if (kerr) return fail(c, PEPO_E_CUDA, "a tensor-core pipeline wait expired (kernel error word %d)", kerr);
     for (int i = 0; i < c->n_inst; ++i) {
       Inst& I = c->inst[i];
       if (done[i] || sw > I.cfg.bp_max_sweeps) continue;
@@ -1247,10 +1258,13 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
       LAUNCH_T(K_MSG, nullptr, I.msgs.n, launch_sl_finish(I.msgs.d, I.msgs.n, c->d_ival, nullptr, c->d_delta1, s));
     }
     if (!any) break;
+    int kerr = 0;
     if (cudaMemcpyAsync(hd.data(), c->d_delta1, sizeof(unsigned long long) * c->n_inst,
                         cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&kerr, c->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return fail(c, PEPO_E_CUDA, "single-layer delta readback");
+    if (kerr) return fail(c, PEPO_E_CUDA, "a tensor-core pipeline wait expired (kernel error word %d)", kerr);
     for (int i = 0; i < c->n_inst; ++i) {
       Inst& I = c->inst[i];
       if (done[i] || sw > I.cfg.bp_max_sweeps) continue;
@@ -1270,9 +1284,13 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
     LAUNCH_N(1, launch_bethe(I.bethe.d, 1, s));
   }
   std::vector<int> flags(c->n_inst);
+  int kerr = 0;
   if (cudaMemcpyAsync(flags.data(), c->d_flags, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, s) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaMemcpyAsync(&kerr, c->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
     return fail(c, PEPO_E_CUDA, "flags readback");
+  if (kerr) return fail(c, PEPO_E_CUDA, "a tensor-core pipeline wait expired (kernel error word %d)", kerr);
   for (int i = 0; i < c->n_inst; ++i) {
     Inst& I = c->inst[i];
     double out[8];
@@ -1415,6 +1433,7 @@ pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena, size
   ok = ok && cudaMemcpyAsync(c->d_items, P.st.bytes.data(), P.st.bytes.size(), cudaMemcpyHostToDevice,
                              s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->d_flags, 0, sizeof(int) * n_inst, s) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->d_kerr, 0, sizeof(int), s) == cudaSuccess;
   resolve_all(c);
   // initial state (Sec. 2.3): chi = 1 everywhere, observable Pauli at c, I elsewhere
   for (auto& I : c->inst) {
