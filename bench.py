@@ -22,7 +22,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(Lx=10, Ly=10, J=1.0, h=2.0, dt=0.05, order=2, obs=(3, 4), chi_max=100, qr_ratio_thresh=16.0,
-                bp_alpha=0.5, bp_tol=1e-5, bp_max_sweeps=100, precision="fp32")
+                bp_alpha=0.5, bp_tol=1e-5, bp_max_sweeps=100, precision="tf32x3")
 SEED = 0
 
 
@@ -35,7 +35,7 @@ def parse():
     ap.add_argument("--chi", type=int, default=None, help="override chi_max (smaller test runs)")
     ap.add_argument("--grid", type=int, default=None, help="override the grid side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--prec", default=None, help="fp32 | tf32x3 | fp64 (default fp32)")
+    ap.add_argument("--prec", default=None, help="tf32x3 | fp32 | fp64 (default tf32x3)")
     return ap.parse_args()
 
 
