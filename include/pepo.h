@@ -182,6 +182,23 @@ pepo_status pepo_set_bonds(pepo_ctx* ctx, int inst, const int* chi, const double
 pepo_status pepo_set_site(pepo_ctx* ctx, int inst, int site, const void* data, int dtype,
                           size_t count);
 
+/* pepo_set_site without any memory allocation (the paper has no counterpart:
+ * it is an interface variant, not a step of the method).  Same arguments and
+ * result as pepo_set_site, but the host data is staged in a fixed 16 MiB
+ * device buffer compiled into the library instead of the arena's scratch
+ * slab, and dtype must be the storage type (0 = float for FP32 / TF32X3
+ * contexts, 1 = double for FP64).  For callers that may not allocate or touch
+ * the arena's scratch (device memory fully committed to the arena, or a
+ * latency-bound loop where an allocation would synchronise the device).
+ * Limit: 4 * prod(chi) * sizeof(storage) <= 16 MiB, else PEPO_E_INVALID with
+ * the sizes in pepo_last_error.  The first call on each device looks up the
+ * buffer's device address (call it with that device current, once, before
+ * any stream capture).  Nothing in the buffer needs to start at zero.  Calls
+ * that overlap in time share the buffer and race: serialise them.
+ * Synchronises the stream. */
+pepo_status pepo_set_site_static(pepo_ctx* ctx, int inst, int site, const void* data, int dtype,
+                                 size_t count);
+
 /* Copy one directed message (chi x chi, row-major) to the host. */
 pepo_status pepo_get_message(pepo_ctx* ctx, int inst, int bond, int dir, double* out,
                              int* chi_out);

@@ -51,7 +51,7 @@ class _Diag(ctypes.Structure):
 
 EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trotter_step",
            "pepo_bp_converge", "pepo_correlator", "pepo_get_spectrum", "pepo_get_site",
-           "pepo_set_state", "pepo_set_bonds", "pepo_set_site", "pepo_get_message", "pepo_num_bonds", "pepo_set_timing",
+           "pepo_set_state", "pepo_set_bonds", "pepo_set_site", "pepo_set_site_static", "pepo_get_message", "pepo_num_bonds", "pepo_set_timing",
            "pepo_timing_classes", "pepo_timing_class_name", "pepo_get_timing", "pepo_reset_timing",
            "pepo_launch_count", "pepo_last_error", "pepo_destroy"]
 
@@ -91,6 +91,8 @@ def load_library(path=LIB_PATH):
     lib.pepo_set_bonds.restype = I
     lib.pepo_set_site.argtypes = [P, I, I, P, I, S]
     lib.pepo_set_site.restype = I
+    lib.pepo_set_site_static.argtypes = [P, I, I, P, I, S]
+    lib.pepo_set_site_static.restype = I
     lib.pepo_get_message.argtypes = [P, I, I, I, ctypes.POINTER(D), ctypes.POINTER(I)]
     lib.pepo_get_message.restype = I
     lib.pepo_num_bonds.argtypes = [P, I]
@@ -328,6 +330,14 @@ class Engine:
             dt = 1
         self._check(self.lib.pepo_set_site(self.ctx, inst, v, ctypes.c_void_p(t.ctypes.data), dt, t.size),
                     "pepo_set_site")
+
+    def set_site_static(self, inst, v, tensor):
+        """As set_site, through the library's fixed device staging buffer (no
+        allocation); tensor must already have the storage dtype."""
+        t = np.ascontiguousarray(tensor)
+        dt = 0 if t.dtype == np.float32 else 1
+        self._check(self.lib.pepo_set_site_static(self.ctx, inst, v, ctypes.c_void_p(t.ctypes.data), dt,
+                                                  t.size), "pepo_set_site_static")
 
     def run(self, nsteps, measure_every=1):
         """Evolve nsteps, measuring C(t) (BP + correlator) every `measure_every` steps."""

@@ -1632,6 +1632,79 @@ pepo_status pepo_set_site(pepo_ctx* c, int inst, int site, const void* data, int
   return PEPO_OK;
 }
 
+// ----------------------------------------------- allocation-free site upload
+// pepo_set_site staged through a file-scope device buffer instead of the
+// arena's scratch slab.  The buffer's device address is looked up once per
+// device (cudaGetSymbolAddress, with that device current) on the first call;
+// nothing here allocates host or device memory.  No byte of the buffer needs
+// to start at zero: each call writes the first count elements before the
+// permutation reads them.  Calls that overlap in time (any contexts on the
+// same device) share the buffer and race.
+constexpr size_t kStaticStageBytes = (size_t)16 << 20;
+constexpr int kStaticMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_static_stage[kStaticStageBytes];
+static void* g_static_stage_ptr[kStaticMaxDevices];
+
+static pepo_status static_stage(pepo_ctx* c, void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices)
+    return fail(c, PEPO_E_CUDA, "no current CUDA device for the static staging buffer");
+  if (g_static_stage_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_stage);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(c, PEPO_E_CUDA, "static staging buffer lookup: %s", cudaGetErrorString(e));
+    g_static_stage_ptr[dev] = p;
+  }
+  *out = g_static_stage_ptr[dev];
+  return PEPO_OK;
+}
+
+pepo_status pepo_set_site_static(pepo_ctx* c, int inst, int site, const void* data, int dtype, size_t count) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
+  Inst& I = c->inst[inst];
+  if (site < 0 || site >= I.N || !data || (dtype != 0 && dtype != 1))
+    return fail(c, PEPO_E_INVALID, "bad site upload arguments");
+  const size_t ts = c->tsize;
+  if ((dtype == 0) != (ts == 4))
+    return fail(c, PEPO_E_INVALID, "static upload needs the storage type (%s)", ts == 4 ? "float" : "double");
+  const SiteG& S = I.sites[site];
+  void* stage = nullptr;
+  pepo_status st = static_stage(c, &stage);
+  if (st != PEPO_OK) return st;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, PEPO_E_CUDA, "stream sync");
+  int dc[4] = {1, 1, 1, 1}, perm[4] = {0, 0, 0, 0};
+  size_t n = 4;
+  for (int k = 0; k < S.deg; ++k) {
+    if (cudaMemcpy(&dc[k], c->d_ival + I.chi0 + S.legs[k].bond, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(c, PEPO_E_CUDA, "chi readback");
+    n *= (size_t)dc[k];
+  }
+  if (count != n) return fail(c, PEPO_E_INVALID, "site %d needs %zu elements, got %zu", site, n, count);
+  if (n * ts > kStaticStageBytes)
+    return fail(c, PEPO_E_INVALID, "site %d needs %zu bytes; the static staging buffer holds %zu", site,
+                n * ts, kStaticStageBytes);
+  // stored layout at step boundaries: the legs other than the first update's
+  // cut in canonical order, then the cut
+  const int cut = S.upd[0];
+  int p = 0;
+  for (int k = 0; k < S.deg; ++k) if (k != cut) perm[p++] = k;
+  perm[p] = cut;
+  void* dst = nullptr;
+  if (cudaMemcpy(&dst, c->d_ptrs + I.site_ref0 + site, sizeof(void*), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "pointer readback");
+  cudaError_t e = cudaMemcpyAsync(stage, data, ts * n, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return fail(c, PEPO_E_CUDA, "site upload: %s", cudaGetErrorString(e));
+  e = ts == 4 ? launch_permute<float>(stage, dst, S.deg, dc, perm, 1, c->stream)
+              : launch_permute<double>(stage, dst, S.deg, dc, perm, 1, c->stream);
+  c->launches++;
+  if (e != cudaSuccess || cudaMemsetAsync(I.sigma + site, 0, sizeof(double), c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "site permute");
+  return PEPO_OK;
+}
+
 pepo_status pepo_set_state(pepo_ctx* c, int inst, const double* sites, size_t count, const int* chi,
                            const double* lam, const double* msgs) {
   if (!c) return PEPO_E_INVALID;
