@@ -385,17 +385,55 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
     }
   } else if (warp >= 8) {
     // ------------------------------------------------------------ converters
+    // Loads run two chunks ahead of the shared-memory stores (register ring
+    // v0, v1, v2), so three chunks of global reads are in flight per thread.
     const int ct = tid - 256, cw = ct >> 5;
     const int jj = lane & 3, rq = (lane >> 2) & 1, a = lane >> 3;
     const int r = 32 * (cw & 3) + 8 * a + 4 * rq;   // this thread's 4-row group
     const int jq0 = cw >> 2;                        // j quads jq0, jq0 + 2, +4, +6
+    // load cursor
+    LegCursor lc;
+    bool lc_live = cursor_start(lc, toff, n_items, t0, t1, items, ptrs, ival);
+    int lkc = 0;
+    bool lvalid = false;
+    const float* lsrc = nullptr;
+    auto enter_tile = [&]() {
+      const long long rg = lc.tile * kM + r;
+      lvalid = rg < lc.L.R;
+      lsrc = lc.L.in;
+      if (lvalid) {
+        const long long o = rg / lc.L.Q, q = rg - o * lc.L.Q;
+        lsrc = lc.L.in + o * lc.L.J * lc.L.Q + q;
+      }
+      lkc = 0;
+    };
+    if (lc_live) enter_tile();
+    auto load_next = [&](float4* v) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!lc_live) return;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = lkc * kKC + 4 * (jq0 + 2 * u) + jj;
+        if (lvalid && j < lc.L.J) v[u] = __ldg(reinterpret_cast<const float4*>(lsrc + (long long)j * lc.L.Q));
+      }
+      if (++lkc < (lc.L.K8 + kKC - 1) / kKC) return;
+      if (lc.left == 1) { lc_live = false; return; }
+      cursor_next(lc, toff, n_items, items, ptrs, ival);
+      enter_tile();
+    };
+    float4 v0[4], v1[4], v2[4];
+    load_next(v0);
+    load_next(v1);
+    // store cursor
     LegCursor c;
     bool live = cursor_start(c, toff, n_items, t0, t1, items, ptrs, ival);
     long long cc = 0;
-    int item_n = 0;
+    int item_n = 0, kc = 0;
     bool need_b = true;
     while (live) {
       const LegDims& L = c.L;
+      load_next(v2);
       if (need_b) {
         if (item_n > 0 && !mbar_wait(&bars->bfree, (uint32_t)((item_n - 1) & 1), abort_flag, err)) break;
         // [Ah; Al]: rows n < N16 hold hi(A[n, :]), rows N16 + n hold lo(A[n, :])
@@ -415,45 +453,31 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
         mbar_arrive(&bars->bfull);
         need_b = false;
       }
-      const long long rg = c.tile * kM + r;
-      const bool valid = rg < L.R;
-      const float* src = L.in;
-      if (valid) {
-        const long long o = rg / L.Q, q = rg - o * L.Q;
-        src = L.in + o * L.J * L.Q + q;
-      }
-      const int nkc = (L.K8 + kKC - 1) / kKC;
-      bool ok = true;
-      for (int kc = 0; kc < nkc; ++kc, ++cc) {
-        float4 v[4];
+      const int s = (int)(cc % NS);
+      if (!mbar_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) break;
+      unsigned char* hi = As + (size_t)s * P.stage_bytes;
+      unsigned char* lo = hi + P.stage_bytes / 2;
+      const size_t rbase = (size_t)(r >> 3) * 128 + (size_t)jj * 4;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int j = kc * kKC + 4 * (jq0 + 2 * u) + jj;
-          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (valid && j < L.J) v[u] = __ldg(reinterpret_cast<const float4*>(src + (long long)j * L.Q));
+      for (int u = 0; u < 4; ++u) {
+        const size_t kb = (size_t)(jq0 + 2 * u) * 2048 + rbase;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int e = (i + a) & 3;        // rotation keeps the 32 lanes on 32 banks
+          const float x = pick(v0[u], e);
+          const float h = tf32_hi(x);
+          const size_t off = kb + (size_t)(4 * rq + e) * 16;
+          *reinterpret_cast<float*>(hi + off) = h;
+          *reinterpret_cast<float*>(lo + off) = x - h;
         }
-        const int s = (int)(cc % NS);
-        if (!mbar_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
-        unsigned char* hi = As + (size_t)s * P.stage_bytes;
-        unsigned char* lo = hi + P.stage_bytes / 2;
-        const size_t rbase = (size_t)(r >> 3) * 128 + (size_t)jj * 4;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const size_t kb = (size_t)(jq0 + 2 * u) * 2048 + rbase;
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int e = (i + a) & 3;        // rotation keeps the 32 lanes on 32 banks
-            const float x = pick(v[u], e);
-            const float h = tf32_hi(x);
-            const size_t off = kb + (size_t)(4 * rq + e) * 16;
-            *reinterpret_cast<float*>(hi + off) = h;
-            *reinterpret_cast<float*>(lo + off) = x - h;
-          }
-        }
-        fence_async_smem();
-        mbar_arrive(&bars->full[s]);
       }
-      if (!ok) break;
+      fence_async_smem();
+      mbar_arrive(&bars->full[s]);
+      ++cc;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { v0[u] = v1[u]; v1[u] = v2[u]; }
+      if (++kc < (L.K8 + kKC - 1) / kKC) continue;
+      kc = 0;
       if (c.left == 1) break;
       if (cursor_next(c, toff, n_items, items, ptrs, ival)) { ++item_n; need_b = true; }
     }
@@ -684,83 +708,111 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
     }
   } else if (warp >= 8) {
     // ------------------------------------------------------------ converters
-    const int ct = tid - 256, cw = ct >> 5;
+    // Loads (and the weight of the thread's column group) run two chunks
+    // ahead of the shared-memory stores (register ring v0, v1, v2).
+    const int cw = (tid - 256) >> 5;
     const int kq = 4 * (cw & 1) + (lane >> 3);     // this thread's 4-wide K group of a chunk
     const int i8_0 = cw >> 1;                      // row groups i8_0 + 4 u, u = 0..3
     const int il = lane & 7;
-    GramCursor g;
-    g.item = -1;
-    long long cc = 0;
+    // load cursor
+    GramCursor lg;
+    lg.item = -1;
+    long long lu = blockIdx.x, lcur = 0;
+    bool l_live = false;
     int wt_item = -1;
     const double* sw[PEPO_MAXLEG];
     unsigned dd[PEPO_MAXLEG];
-    for (long long u = blockIdx.x; u < U; u += gridDim.x) {
-      gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max);
-      const GramDims& G = g.G;
-      if (g.item != wt_item) {
-        const GramLegItem& it = items[g.item];
+    long long o_w = -1;     // o of the cached outer weight
+    float w_out = 0.f;
+    auto enter_unit = [&]() {
+      l_live = lu < U;
+      if (!l_live) return;
+      gram_unit(lg, lu, uoff, n_items, items, ptrs, ival, splits_max);
+      lcur = lg.c;
+      if (lg.item != wt_item) {
+        const GramLegItem& it = items[lg.item];
 #pragma unroll
         for (int uu = 0; uu < PEPO_MAXLEG; ++uu) {
-          sw[uu] = (uu < G.nlegs && uu != G.k) ? it.sw[uu] : nullptr;
-          dd[uu] = (unsigned)G.d[uu];
+          sw[uu] = (uu < lg.G.nlegs && uu != lg.G.k) ? it.sw[uu] : nullptr;
+          dd[uu] = (unsigned)lg.G.d[uu];
         }
-        wt_item = g.item;
+        wt_item = lg.item;
+        o_w = -1;
       }
-      const int F = G.F, F8 = G.F8;
-      const size_t lbo = (size_t)(2 * F8 / 8) * 128;
-      bool ok = true;
-      long long o_w = -1;     // o of the cached outer weight
-      float w_out = 0.f;
-      for (long long c = g.c; c < g.c1; ++c, ++cc) {
-        // k group of this thread: legs before the free leg give o, legs after give q
-        long long o, q;
-        bool kvalid;
-        if (G.wide) {
-          o = c / G.qpc;
-          q = (c - o * G.qpc) * kKC + 4 * kq;
-          kvalid = q < G.Q;
-        } else {
-          o = c * G.opc + (4 * kq) / G.Q;
-          q = (4 * kq) % G.Q;
-          kvalid = (4 * kq) / G.Q < G.opc && o < G.O;
-        }
-        // weight prod_{u != k} sw[u][j_u]: outer legs from o (cached per o),
-        // inner legs from q / 4 (the Pauli index shares one weight)
-        float w = 0.f;
-        if (kvalid) {
-          if (o != o_w) {
-            float wo = 1.f;
-            unsigned t = (unsigned)o;
+    };
+    enter_unit();
+    auto load_next = [&](float4* v, float& w) {
 #pragma unroll
-            for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
-              if (uu < G.k) {
-                const unsigned j = t % dd[uu];
-                t /= dd[uu];
-                if (sw[uu]) wo *= (float)sw[uu][j];
-              }
-            }
-            w_out = wo;
-            o_w = o;
-          }
-          float wi = 1.f;
-          unsigned t = (unsigned)(q >> 2);
+      for (int u4 = 0; u4 < 4; ++u4) v[u4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      w = 0.f;
+      if (!l_live) return;
+      const GramDims& G = lg.G;
+      const long long c = lcur;
+      // k group of this thread: legs before the free leg give o, legs after give q
+      long long o, q;
+      bool kvalid;
+      if (G.wide) {
+        o = c / G.qpc;
+        q = (c - o * G.qpc) * kKC + 4 * kq;
+        kvalid = q < G.Q;
+      } else {
+        o = c * G.opc + (4 * kq) / G.Q;
+        q = (4 * kq) % G.Q;
+        kvalid = (4 * kq) / G.Q < G.opc && o < G.O;
+      }
+      // weight prod_{u != k} sw[u][j_u]: outer legs from o (cached per o),
+      // inner legs from q / 4 (the Pauli index shares one weight)
+      if (kvalid) {
+        if (o != o_w) {
+          float wo = 1.f;
+          unsigned t = (unsigned)o;
 #pragma unroll
           for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
-            if (uu > G.k && uu < G.nlegs) {
+            if (uu < G.k) {
               const unsigned j = t % dd[uu];
               t /= dd[uu];
-              if (sw[uu]) wi *= (float)sw[uu][j];
+              if (sw[uu]) wo *= (float)sw[uu][j];
             }
           }
-          w = w_out * wi;
+          w_out = wo;
+          o_w = o;
         }
-        float4 v[4];
+        float wi = 1.f;
+        unsigned t = (unsigned)(q >> 2);
+#pragma unroll
+        for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
+          if (uu > G.k && uu < G.nlegs) {
+            const unsigned j = t % dd[uu];
+            t /= dd[uu];
+            if (sw[uu]) wi *= (float)sw[uu][j];
+          }
+        }
+        w = w_out * wi;
 #pragma unroll
         for (int u4 = 0; u4 < 4; ++u4) {
           const int i = 8 * (i8_0 + 4 * u4) + il;
-          v[u4] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (kvalid && i < F) v[u4] = __ldg(reinterpret_cast<const float4*>(G.X + (o * F + i) * G.Q + q));
+          if (i < G.F) v[u4] = __ldg(reinterpret_cast<const float4*>(G.X + (o * G.F + i) * G.Q + q));
         }
+      }
+      if (++lcur < lg.c1) return;
+      lu += gridDim.x;
+      enter_unit();
+    };
+    float4 v0[4], v1[4], v2[4];
+    float w0, w1, w2;
+    load_next(v0, w0);
+    load_next(v1, w1);
+    // store cursor
+    GramCursor g;
+    g.item = -1;
+    long long cc = 0;
+    bool ok = true;
+    for (long long u = blockIdx.x; u < U && ok; u += gridDim.x) {
+      gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max);
+      const int F8 = g.G.F8;
+      const size_t lbo = (size_t)(2 * F8 / 8) * 128;
+      for (long long c = g.c; c < g.c1; ++c, ++cc) {
+        load_next(v2, w2);
         const int s = (int)(cc % NS);
         if (!mbar_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
         unsigned char* st = Xs + (size_t)s * P.stage_bytes + (size_t)kq * lbo;
@@ -768,7 +820,7 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
         for (int u4 = 0; u4 < 4; ++u4) {
           const int i = 8 * (i8_0 + 4 * u4) + il;
           if (i < F8) {
-            const float4 x = make_float4(v[u4].x * w, v[u4].y * w, v[u4].z * w, v[u4].w * w);
+            const float4 x = make_float4(v0[u4].x * w0, v0[u4].y * w0, v0[u4].z * w0, v0[u4].w * w0);
             const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
             const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
             const int i2 = i + F8;
@@ -778,8 +830,11 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
         }
         fence_async_smem();
         mbar_arrive(&bars->full[s]);
+#pragma unroll
+        for (int u4 = 0; u4 < 4; ++u4) { v0[u4] = v1[u4]; v1[u4] = v2[u4]; }
+        w0 = w1;
+        w1 = w2;
       }
-      if (!ok) break;
     }
   }
   tc_before();

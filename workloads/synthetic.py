@@ -6,6 +6,12 @@ horizontal first (y * (Lx - 1) + x) then vertical (Ly * (Lx - 1) + y * Lx + x).
 Values: Gaussian entries, each bond leg weighted by sqrt(lam) with a
 geometrically decaying lam (the shape of a saturated Schmidt spectrum), the
 identity Pauli component weighted up; messages diag(lam) on both directions.
+The identity component also carries a positive rank-1 backbone (the outer
+product of sqrt(lam) over the legs, times sqrt(chi)), as the identity slices
+of an evolved operator do away from the observable: without it the
+single-layer network pinned at the identity is a random sign network on
+which vector BP does not converge (residual ~0.4 after 100 sweeps); with it
+both BP layers converge in a few tens of sweeps, like physical states.
 Every site has its own seed (seed, site), so one site can be regenerated
 without the others.
 """
@@ -46,7 +52,7 @@ def spectrum(chi, decay=DECAY):
     return lam / np.linalg.norm(lam)
 
 
-def site_tensor(Lx, Ly, chi, seed, v, dtype=np.float64, decay=DECAY):
+def site_tensor(Lx, Ly, chi, seed, v, dtype=np.float64, decay=DECAY, backbone=True):
     legs = site_legs(Lx, Ly, v)
     rng = np.random.default_rng([seed, v])
     shape = tuple([chi] * len(legs)) + (4,)
@@ -57,6 +63,11 @@ def site_tensor(Lx, Ly, chi, seed, v, dtype=np.float64, decay=DECAY):
         sh[k] = chi
         t *= sq.reshape(sh)
     t *= PAULI_WEIGHT.astype(t.dtype)
+    if backbone:
+        bb = np.ones((), dtype=t.dtype)
+        for _ in legs:
+            bb = np.multiply.outer(bb, sq)
+        t[..., 0] += np.asarray(np.sqrt(chi), dtype=t.dtype) * bb
     return t
 
 
