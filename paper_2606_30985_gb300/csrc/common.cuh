@@ -174,6 +174,7 @@ struct CoreItem {
   int* nsv;                // number of singular values
   int inst;                // instance (its flag word is flags_base[inst])
   double eps_cut;
+  int mixed_svd;           // 1: FP32 Jacobi + FP64 Rayleigh step (FP32-storage modes)
 };
 
 // ------------------------------------------------------------------- BP

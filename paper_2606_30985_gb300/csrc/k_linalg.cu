@@ -530,21 +530,22 @@ cudaError_t launch_factor(const SiteFacItem* items, int n_items, int rmax, int n
 // One-sided Jacobi (Hestenes) on the columns of A (m x n, column-major, m >= n),
 // accumulating V (n x n, column-major).  Returns the sweep count; sets
 // *capped when the sweep budget ran out.
-__device__ int jacobi_svd(double* A, int m, int n, double* V, int max_sweeps, int* capped,
-                          double* red) {
+template <typename R>
+__device__ int jacobi_svd(R* A, int m, int n, R* V, int max_sweeps, int* capped, double* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   // V == nullptr: rotations are not accumulated (the caller recovers the other
   // side's vectors from a copy of the input)
   if (V)
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = (e % (n + 1) == 0) ? 1.0 : 0.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = (e % (n + 1) == 0) ? R(1) : R(0);
   __syncthreads();
   if (n < 2) return 0;
   const int np = (n % 2) ? n + 1 : n;   // players incl. a dummy
-  const double tol = 1e-15 * sqrt((double)m);
+  // orthogonality target: a few units of the working precision times sqrt(m)
+  const double tol = (sizeof(R) == 4 ? 2e-7 : 1e-15) * sqrt((double)m);
   // columns below 1e-30 of the total squared norm are numerically zero: rotating
   // them only stirs rounding noise and never converges
   double fro = 0.0;
-  for (long long e = threadIdx.x; e < (long long)m * n; e += blockDim.x) fro = fma(A[e], A[e], fro);
+  for (long long e = threadIdx.x; e < (long long)m * n; e += blockDim.x) fro = fma((double)A[e], (double)A[e], fro);
   {
     fro = warp_sum(fro);
     __shared__ double fr[32];
@@ -568,29 +569,29 @@ __device__ int jacobi_svd(double* A, int m, int n, double* V, int max_sweeps, in
         else { a = (round + pi) % (np - 1); b = (round - pi + np - 1) % (np - 1); }
         if (a >= n || b >= n) continue;
         int p = a < b ? a : b, q = a < b ? b : a;
-        double* Ap = A + (long long)p * m;
-        double* Aq = A + (long long)q * m;
-        double al = 0.0, be = 0.0, ga = 0.0;
+        R* Ap = A + (long long)p * m;
+        R* Aq = A + (long long)q * m;
+        R al = 0, be = 0, ga = 0;
         for (int i = lane; i < m; i += 32) {
-          double x = Ap[i], y = Aq[i];
+          R x = Ap[i], y = Aq[i];
           al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
         }
-        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-        if (ga != 0.0 && al > negligible && be > negligible && fabs(ga) > tol * sqrt(al * be)) {
+        al = (R)warp_sum((double)al); be = (R)warp_sum((double)be); ga = (R)warp_sum((double)ga);
+        if (ga != R(0) && al > negligible && be > negligible && fabs((double)ga) > tol * sqrt((double)al * be)) {
           rotated = 1;
-          const double zeta = (be - al) / (2.0 * ga);
+          const double zeta = ((double)be - al) / (2.0 * ga);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          const R c = (R)(1.0 / sqrt(1.0 + t * t)), s = (R)((1.0 / sqrt(1.0 + t * t)) * t);
           for (int i = lane; i < m; i += 32) {
-            double x = Ap[i], y = Aq[i];
+            R x = Ap[i], y = Aq[i];
             Ap[i] = c * x - s * y;
             Aq[i] = s * x + c * y;
           }
           if (V) {
-            double* Vp = V + (long long)p * n;
-            double* Vq = V + (long long)q * n;
+            R* Vp = V + (long long)p * n;
+            R* Vq = V + (long long)q * n;
             for (int i = lane; i < n; i += 32) {
-              double x = Vp[i], y = Vq[i];
+              R x = Vp[i], y = Vq[i];
               Vp[i] = c * x - s * y;
               Vq[i] = s * x + c * y;
             }
@@ -650,22 +651,99 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
   __syncthreads();
   for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) V[e] = Tc[e];   // copy of Tcore
   __syncthreads();
-  jacobi_svd(Tc, M, N, nullptr, 60, &sh_capped, red);
+  __shared__ int sh_resolved;
+  __shared__ double sh_fro2;
+  if (threadIdx.x == 0) { sh_resolved = 0; sh_fro2 = -1.0; }
   __syncthreads();
-  // singular values (column norms) and descending order
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    double s = 0.0;
-    const double* col = Tc + (long long)j * M;
-    for (int i = 0; i < M; ++i) s = fma(col[i], col[i], s);
-    sv[j] = sqrt(s);
+  if (it.mixed_svd) {
+    // FP32 one-sided Jacobi with accumulated right vectors V32 (in the R2
+    // block, free until the reconstruct step), then an FP64 Rayleigh step on
+    // the kept set: column j of Tc becomes T v32_j in FP64 and its norm the
+    // singular value (second-order accurate in the FP32 vector error).  Valid
+    // when every kept FP32 singular value stands well above FP32 noise
+    // (>= 1e-5 s_0): the truncation count then cannot change; else the full
+    // FP64 Jacobi below runs.
+    float* T32 = reinterpret_cast<float*>(R2o);
+    float* V32 = T32 + (long long)M * N;
+    for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) T32[e] = (float)Tc[e];
+    __syncthreads();
+    __shared__ int sh_capped32;   // a capped FP32 pass only means the FP64 path runs
+    if (threadIdx.x == 0) sh_capped32 = 0;
+    __syncthreads();
+    jacobi_svd<float>(T32, M, N, V32, 60, &sh_capped32, red);
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      double s = 0.0;
+      const float* col = T32 + (long long)j * M;
+      for (int i = 0; i < M; ++i) s = fma((double)col[i], (double)col[i], s);
+      sv[j] = sqrt(s);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      int rk = 0;
+      for (int i = 0; i < N; ++i) if (sv[i] > sv[j] || (sv[i] == sv[j] && i < j)) ++rk;
+      order[rk] = j;
+    }
+    __syncthreads();
+    const int nk = N < it.chimax ? N : it.chimax;
+    if (threadIdx.x == 0)
+      sh_resolved = (!sh_capped32 && sv[order[0]] > 0.0 && sv[order[nk - 1]] >= 1e-5 * sv[order[0]]) ? 1 : 0;
+    __syncthreads();
+    if (sh_resolved) {
+      // exact ||T||_F^2 (FP64) for the discarded weight
+      double f = 0.0;
+      for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) f = fma(V[e], V[e], f);
+      f = block_sum(f, red);
+      if (threadIdx.x == 0) sh_fro2 = f;
+      // kept columns: Tc[:, j] = T v32_j (FP64)
+      for (long long e = threadIdx.x; e < (long long)nk * M; e += blockDim.x) {
+        const int c = (int)(e / M), i = (int)(e % M);
+        const int j = order[c];
+        const float* vj = V32 + (long long)j * N;
+        double acc = 0.0;
+        for (int k = 0; k < N; ++k) acc = fma(V[(long long)k * M + i], (double)vj[k], acc);
+        Tc[(long long)j * M + i] = acc;
+      }
+      __syncthreads();
+      for (int c = threadIdx.x; c < nk; c += blockDim.x) {
+        const int j = order[c];
+        double s = 0.0;
+        const double* col = Tc + (long long)j * M;
+        for (int i = 0; i < M; ++i) s = fma(col[i], col[i], s);
+        sv[j] = sqrt(s);
+      }
+      __syncthreads();
+      // re-rank the kept set by its FP64 values (the rest keep FP32 values
+      // and their FP32 ranks, used for diagnostics only)
+      if (threadIdx.x == 0) {
+        for (int a = 1; a < nk; ++a) {
+          const int j = order[a];
+          int b = a - 1;
+          while (b >= 0 && sv[order[b]] < sv[j]) { order[b + 1] = order[b]; --b; }
+          order[b + 1] = j;
+        }
+      }
+      __syncthreads();
+    }
   }
-  __syncthreads();
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    int rk = 0;
-    for (int i = 0; i < N; ++i) if (sv[i] > sv[j] || (sv[i] == sv[j] && i < j)) ++rk;
-    order[rk] = j;
+  if (!sh_resolved) {   // Tc still holds Tcore (the FP32 pass worked on a copy)
+    jacobi_svd<double>(Tc, M, N, nullptr, 60, &sh_capped, red);
+    __syncthreads();
+    // singular values (column norms) and descending order
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      double s = 0.0;
+      const double* col = Tc + (long long)j * M;
+      for (int i = 0; i < M; ++i) s = fma(col[i], col[i], s);
+      sv[j] = sqrt(s);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      int rk = 0;
+      for (int i = 0; i < N; ++i) if (sv[i] > sv[j] || (sv[i] == sv[j] && i < j)) ++rk;
+      order[rk] = j;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const double s0 = sv[order[0]];
   // truncation, Eq. 11
   __shared__ int sh_chi;
@@ -678,6 +756,7 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
       tot += s * s;
       if (s >= it.eps_cut * s0 && s > 0.0) ++cnt;
     }
+    if (sh_fro2 >= 0.0) tot = sh_fro2;   // mixed path: exact Frobenius norm
     int chi = cnt < it.chimax ? cnt : it.chimax;
     if (chi < 1) chi = 1;
     double kept = 0.0, ksum = 0.0;
@@ -796,20 +875,44 @@ namespace pepo {
 // S = |eigenvalues| and V the eigenvectors (U = V up to signs of numerically
 // zero eigenvalues).  Outputs Vt (row i = column i of V) and sqrt(S).
 __global__ void __launch_bounds__(1024)
-k_env_eig(const EnvEigItem* __restrict__ items, const int* ival) {
+k_env_eig(const EnvEigItem* __restrict__ items, const int* ival, int fp32) {
   const EnvEigItem it = items[blockIdx.x];
   const int n = ival[it.chi_idx];
-  double* A = it.work;                      // n x n column-major
-  double* V = it.work + (long long)n * n;   // n x n column-major
   __shared__ double red[32];
   __shared__ int capped;
   if (threadIdx.x == 0) capped = 0;
+  if (fp32) {
+    // FP32-storage modes: the eigenbasis only rotates FP32 tensors, so the
+    // Jacobi runs in FP32 entirely in shared memory
+    extern __shared__ __align__(16) float sm32[];
+    float* A = sm32;                       // n x n column-major
+    float* V = sm32 + (long long)n * n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      int i = e / n, j = e - i * n;
+      A[(long long)j * n + i] = (float)(0.5 * (it.M[i * it.ld + j] + it.M[j * it.ld + i]));
+    }
+    __syncthreads();
+    jacobi_svd<float>(A, n, n, V, 60, &capped, red);
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double s = 0.0;
+      for (int i = 0; i < n; ++i) s = fma((double)A[(long long)j * n + i], (double)A[(long long)j * n + i], s);
+      it.sqrtD[j] = sqrt(sqrt(s));
+    }
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      int i = e / n, j = e - i * n;
+      it.Vt[i * it.ld + j] = (double)V[(long long)i * n + j];
+    }
+    return;
+  }
+  double* A = it.work;                      // n x n column-major
+  double* V = it.work + (long long)n * n;   // n x n column-major
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     int i = e / n, j = e - i * n;   // A column j, row i
     A[(long long)j * n + i] = 0.5 * (it.M[i * it.ld + j] + it.M[j * it.ld + i]);
   }
   __syncthreads();
-  jacobi_svd(A, n, n, V, 60, &capped, red);
+  jacobi_svd<double>(A, n, n, V, 60, &capped, red);
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     double s = 0.0;
@@ -822,9 +925,15 @@ k_env_eig(const EnvEigItem* __restrict__ items, const int* ival) {
   }
 }
 
-cudaError_t launch_env_eig(const EnvEigItem* items, int n_items, const int* ival, cudaStream_t s) {
+cudaError_t launch_env_eig(const EnvEigItem* items, int n_items, int chimax, int fp32, const int* ival,
+                           cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  k_env_eig<<<n_items, 1024, 0, s>>>(items, ival);
+  size_t smem = fp32 ? 2 * sizeof(float) * (size_t)chimax * chimax : 0;
+  if (smem > 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_env_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_env_eig<<<n_items, 1024, smem, s>>>(items, ival, fp32);
   return cudaGetLastError();
 }
 

@@ -845,6 +845,294 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
   }
 }
 
+// ================================================================ reconstruct
+// out[perm(r), c] = sum_k in[r, k] W[k, c]: rows r = environment index of the
+// site tensor (cut leg last), k = (cut, Pauli), c = (new cut, Pauli) written
+// into the next update's layout.  Tiles are (128 rows, one N block of at most
+// 128 columns); both operands stream in 32-wide K chunks: A through the
+// converters (row-contiguous, 16-byte loads), B = [hi(W^T); lo(W^T)] for the
+// tile's N block converted from the FP64 W (L2-resident) by the same warps.
+struct RecDims {
+  long long R, tiles, nrb;
+  int n, np, K8, nnb, NB, cut, nl;
+  int d[PEPO_MAXLEG];
+  long long rstride[PEPO_MAXLEG], ostride[PEPO_MAXLEG];
+  const float* in;
+  float* out;
+  const double* W;
+  int ldw;
+};
+
+__device__ inline void rec_dims(const ReconItem& it, void* const* ptrs, const int* ival, RecDims& D) {
+  D.nl = it.in.nlegs;
+  for (int k = 0; k < PEPO_MAXLEG; ++k) D.d[k] = (k < D.nl) ? ival[it.in.dim[k]] : 1;
+  D.cut = D.nl - 1;
+  D.n = 4 * D.d[D.cut];
+  const int chin = ival[it.new_dim];
+  D.np = 4 * chin;
+  D.R = 1;
+  for (int i = 0; i < D.cut; ++i) D.R *= D.d[i];
+  int od[PEPO_MAXLEG];
+  for (int i = 0; i < D.nl; ++i) od[i] = (i == D.cut) ? chin : D.d[i];
+  long long st = 4;
+  for (int kk = D.nl - 1; kk >= 0; --kk) {
+    const int li = it.out_perm[kk];
+    D.ostride[li] = st;
+    st *= od[li];
+  }
+  st = 1;
+  for (int i = D.cut - 1; i >= 0; --i) { D.rstride[i] = st; st *= D.d[i]; }
+  D.K8 = round_up(D.n, 8);
+  D.nnb = (D.np + 127) / 128;
+  D.NB = round_up((D.np + D.nnb - 1) / D.nnb, 8);
+  D.nrb = (D.R + kM - 1) / kM;
+  D.tiles = D.nrb * D.nnb;
+  D.in = static_cast<const float*>(ptrs[it.in.ref]);
+  D.out = static_cast<float*>(ptrs[it.out_ref]);
+  D.W = it.W;
+  D.ldw = it.ldw;
+}
+
+struct RecSmem {
+  int stages;
+  size_t a_bytes, stage_bytes, bar_off, total;
+};
+__host__ __device__ inline RecSmem rec_smem() {
+  RecSmem p;
+  p.a_bytes = (size_t)(kKC / 4) * (kM / 8) * 128;                 // 16 KB per hi / lo
+  p.stage_bytes = 2 * p.a_bytes + (size_t)(kKC / 4) * (256 / 8) * 128;   // + [Bh; Bl], NB <= 128
+  p.stages = 3;
+  p.bar_off = p.stages * p.stage_bytes;
+  p.total = p.bar_off + 512 + 8 * (size_t)(kMaxItems + 1) + 1024;
+  return p;
+}
+
+struct RecCursor {
+  int item;
+  long long tile, left;
+  RecDims D;
+};
+__device__ inline bool rec_start(RecCursor& c, const long long* toff, int n, long long t0, long long t1,
+                                 const ReconItem* items, void* const* ptrs, const int* ival) {
+  c.left = t1 - t0;
+  if (c.left <= 0) return false;
+  int i = 0;
+  while (i + 1 < n && toff[i + 1] <= t0) ++i;
+  c.item = i;
+  c.tile = t0 - toff[i];
+  rec_dims(items[i], ptrs, ival, c.D);
+  return true;
+}
+__device__ inline void rec_next(RecCursor& c, const long long* toff, int n, const ReconItem* items,
+                                void* const* ptrs, const int* ival) {
+  --c.left;
+  ++c.tile;
+  while (c.left > 0 && c.tile >= c.D.tiles && c.item + 1 < n) {
+    ++c.item;
+    c.tile = 0;
+    rec_dims(items[c.item], ptrs, ival, c.D);
+  }
+}
+
+struct RecBars {
+  uint64_t full[4], empty[4], accfull[2], accempty[2], drain;
+  uint32_t tmem;
+  int abort_flag;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs, const int* __restrict__ ival,
+             int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const RecSmem P = rec_smem();
+  RecBars* bars = reinterpret_cast<RecBars*>(smem + P.bar_off);
+  long long* toff = reinterpret_cast<long long*>(smem + P.bar_off + 512);
+  volatile int* abort_flag = &bars->abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int NS = P.stages;
+  if (tid == 0) {
+    long long acc = 0;
+    for (int i = 0; i < n_items; ++i) {
+      toff[i] = acc;
+      RecDims D;
+      rec_dims(items[i], ptrs, ival, D);
+      acc += D.tiles;
+    }
+    toff[n_items] = acc;
+    for (int s = 0; s < NS; ++s) { mbar_init(&bars->full[s], kConv); mbar_init(&bars->empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&bars->accfull[b], 1); mbar_init(&bars->accempty[b], 128); }
+    mbar_init(&bars->drain, 1);
+    bars->abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(&bars->tmem);
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = bars->tmem;
+  const long long T = toff[n_items];
+  const long long t0 = T * blockIdx.x / gridDim.x, t1 = T * (blockIdx.x + 1) / gridDim.x;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      RecCursor c;
+      bool live = rec_start(c, toff, n_items, t0, t1, items, ptrs, ival);
+      long long cc = 0, tc = 0;
+      bool ok = true;
+      while (live && ok) {
+        const int b = (int)(tc & 1);
+        if (!mbar_wait(&bars->accempty[b], (uint32_t)(((tc >> 1) & 1) ^ 1), abort_flag, err)) break;
+        tc_after();
+        const uint32_t d_tmem = tmem + (uint32_t)(b * 256);
+        const int NB = c.D.NB, K8 = c.D.K8;
+        const uint32_t lbo_b = (uint32_t)(2 * NB / 8) * 128;
+        const uint32_t id_wide = idesc_tf32(kM, 2 * NB), id_half = idesc_tf32(kM, NB);
+        const int nkc = (K8 + kKC - 1) / kKC;
+        for (int kc = 0; kc < nkc; ++kc, ++cc) {
+          const int s = (int)(cc % NS);
+          if (!mbar_wait(&bars->full[s], (uint32_t)((cc / NS) & 1), abort_flag, err)) { ok = false; break; }
+          tc_after();
+          const uint32_t a_hi = su32(smem + (size_t)s * P.stage_bytes);
+          const uint32_t a_lo = a_hi + (uint32_t)P.a_bytes;
+          const uint32_t bb = a_hi + (uint32_t)(2 * P.a_bytes);
+          const int ksteps = min(kKC, K8 - kc * kKC) / 8;
+          for (int st = 0; st < ksteps; ++st) {
+            const uint64_t dah = sdesc(a_hi + (uint32_t)(st * 2) * 2048u, 2048u, 128u);
+            const uint64_t dal = sdesc(a_lo + (uint32_t)(st * 2) * 2048u, 2048u, 128u);
+            const uint64_t db = sdesc(bb + (uint32_t)(st * 2) * lbo_b, lbo_b, 128u);
+            mma_tf32(d_tmem, dah, db, id_wide, (kc > 0 || st > 0) ? 1u : 0u);
+            mma_tf32(d_tmem, dal, db, id_half, 1u);
+          }
+          mma_commit(&bars->empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&bars->accfull[b]);
+        ++tc;
+        if (c.left == 1) break;
+        rec_next(c, toff, n_items, items, ptrs, ival);
+      }
+      mma_commit(&bars->drain);
+      mbar_wait(&bars->drain, 0, abort_flag, err);
+    }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 8) {
+    // -------------------------------------------------------------- epilogue
+    RecCursor c;
+    bool live = rec_start(c, toff, n_items, t0, t1, items, ptrs, ival);
+    const int row = 32 * (warp & 3) + lane;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    long long tc = 0;
+    while (live) {
+      const int b = (int)(tc & 1);
+      if (!mbar_wait(&bars->accfull[b], (uint32_t)((tc >> 1) & 1), abort_flag, err)) break;
+      tc_after();
+      const RecDims& D = c.D;
+      const long long rb = c.tile / D.nnb;
+      const int nb = (int)(c.tile - rb * D.nnb);
+      const long long rg = rb * kM + row;
+      const bool valid = rg < D.R;
+      long long base = 0;
+      if (valid) {
+        long long rem = rg;
+        for (int i = 0; i < D.cut; ++i) {
+          const long long idx = rem / D.rstride[i];
+          rem -= idx * D.rstride[i];
+          base += idx * D.ostride[i];
+        }
+      }
+      const long long ocut = D.ostride[D.cut];
+      const uint32_t tbase = tmem + lane_base + (uint32_t)(b * 256);
+      for (int c0 = 0; c0 < D.NB; c0 += 16) {
+        uint32_t v1[16], v2[16];
+        tmem_ld16(tbase + (uint32_t)c0, v1);
+        tmem_wait16(v1);
+        tmem_ld16(tbase + (uint32_t)(D.NB + c0), v2);
+        tmem_wait16(v2);
+        if (valid) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int cg = nb * D.NB + c0 + i;
+            if (c0 + i < D.NB && cg < D.np)
+              D.out[base + (long long)(cg >> 2) * ocut + (cg & 3)] = __uint_as_float(v1[i]) + __uint_as_float(v2[i]);
+          }
+        }
+      }
+      tc_before();
+      mbar_arrive(&bars->accempty[b]);
+      ++tc;
+      if (c.left == 1) break;
+      rec_next(c, toff, n_items, items, ptrs, ival);
+    }
+  } else if (warp >= 8) {
+    // ------------------------------------------------------------ converters
+    const int ct = tid - 256, cw = ct >> 5;
+    const int kq = 4 * (cw & 1) + (lane >> 3);     // 4-wide K group of A handled by this thread
+    const int i8_0 = cw >> 1;                      // A row groups i8_0 + 4 u
+    const int il = lane & 7;
+    RecCursor c;
+    bool live = rec_start(c, toff, n_items, t0, t1, items, ptrs, ival);
+    long long cc = 0;
+    while (live) {
+      const RecDims& D = c.D;
+      const long long rb = c.tile / D.nnb;
+      const int nb = (int)(c.tile - rb * D.nnb);
+      const int nkc = (D.K8 + kKC - 1) / kKC;
+      const uint32_t lbo_b = (uint32_t)(2 * D.NB / 8) * 128;
+      bool ok = true;
+      for (int kc = 0; kc < nkc; ++kc, ++cc) {
+        float4 v[4];
+        const int k = kc * kKC + 4 * kq;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long long r = rb * kM + 8 * (i8_0 + 4 * u) + il;
+          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (r < D.R && k < D.n) v[u] = __ldg(reinterpret_cast<const float4*>(D.in + r * D.n + k));
+        }
+        const int s = (int)(cc % NS);
+        if (!mbar_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
+        unsigned char* hi = smem + (size_t)s * P.stage_bytes;
+        unsigned char* lo = hi + P.a_bytes;
+        unsigned char* bs = hi + 2 * P.a_bytes;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = 8 * (i8_0 + 4 * u) + il;
+          const float4 x = v[u];
+          const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+          const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+          const size_t off = (size_t)kq * 2048 + (size_t)(i >> 3) * 128 + (size_t)(i & 7) * 16;
+          *reinterpret_cast<float4*>(hi + off) = h;
+          *reinterpret_cast<float4*>(lo + off) = l;
+        }
+        // B chunk: rows c < NB hold hi(W[k, nb NB + c]), rows NB + c the lo part
+        for (int e = ct; e < D.NB * kKC; e += kConv) {
+          const int kk = e / D.NB, cl = e - kk * D.NB;
+          const int kg = kc * kKC + kk, cg = nb * D.NB + cl;
+          float x = 0.f;
+          if (kg < D.n && cg < D.np) x = (float)D.W[(long long)kg * D.ldw + cg];
+          const float h = tf32_hi(x);
+          const size_t kb = (size_t)(kk >> 2) * lbo_b + (size_t)(kk & 3) * 4;
+          *reinterpret_cast<float*>(bs + kb + (size_t)(cl >> 3) * 128 + (size_t)(cl & 7) * 16) = h;
+          const int c2 = cl + D.NB;
+          *reinterpret_cast<float*>(bs + kb + (size_t)(c2 >> 3) * 128 + (size_t)(c2 & 7) * 16) = x - h;
+        }
+        fence_async_smem();
+        mbar_arrive(&bars->full[s]);
+      }
+      if (!ok) break;
+      if (c.left == 1) break;
+      rec_next(c, toff, n_items, items, ptrs, ival);
+    }
+  }
+  tc_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_after();
+    tmem_free(tmem);
+  }
+}
+
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -870,6 +1158,22 @@ cudaError_t launch_leg_umma(const LegItem* items, int n_items, int chimax, void*
   for (int i0 = 0; i0 < n_items; i0 += um::kMaxItems) {
     const int n = std::min(um::kMaxItems, n_items - i0);
     um::k_leg_umma<<<um::sm_count(), um::kThreads, P.total, s>>>(items + i0, n, chimax, ptrs, ival, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_recon_umma(const ReconItem* items, int n_items, int chimax, void* const* ptrs,
+                              const int* ival, int* err, cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  if (!umma_supported(chimax)) return cudaErrorInvalidValue;
+  const um::RecSmem P = um::rec_smem();
+  cudaError_t e = cudaFuncSetAttribute(um::k_recon_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.total);
+  if (e != cudaSuccess) return e;
+  for (int i0 = 0; i0 < n_items; i0 += um::kMaxItems) {
+    const int n = std::min(um::kMaxItems, n_items - i0);
+    um::k_recon_umma<<<um::sm_count(), um::kThreads, P.total, s>>>(items + i0, n, ptrs, ival, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

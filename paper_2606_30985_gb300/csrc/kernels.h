@@ -44,6 +44,9 @@ bool umma_supported(int chimax);
 // err: device int; bit 0 is set when a pipeline wait of the kernel expired
 cudaError_t launch_leg_umma(const LegItem* items, int n_items, int chimax, void* const* ptrs, const int* ival,
                             int* err, cudaStream_t s);
+// psi_new = psi W into the next layout (Q-less reconstruct), W from the bond core
+cudaError_t launch_recon_umma(const ReconItem* items, int n_items, int chimax, void* const* ptrs,
+                              const int* ival, int* err, cudaStream_t s);
 // writes per-split partial sums S; the reduction with sym = 1 returns (S + S^T) / 2
 cudaError_t launch_gram_umma(const GramLegItem* items, int n_items, int splits_max, int chimax,
                              void* const* ptrs, const int* ival, int* err, cudaStream_t s);

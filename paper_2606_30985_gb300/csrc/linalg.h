@@ -20,7 +20,9 @@ cudaError_t launch_core(const CoreItem* items, int n_items, int* ival, int* flag
 }  // namespace pepo
 
 namespace pepo {
-cudaError_t launch_env_eig(const EnvEigItem* items, int n_items, const int* ival, cudaStream_t s);
+// fp32 = 1: FP32 Jacobi in shared memory (FP32-storage modes), else FP64
+cudaError_t launch_env_eig(const EnvEigItem* items, int n_items, int chimax, int fp32, const int* ival,
+                           cudaStream_t s);
 cudaError_t launch_rotate_back(const RotItem* items, int n_items, int chimax, const int* ival,
                                cudaStream_t s);
 }  // namespace pepo

@@ -622,6 +622,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
         ci.nsv = I.nsv + b;
         ci.inst = inst_id;
         ci.eps_cut = I.cfg.eps_cut;
+        ci.mixed_svd = (c->tsize == 4) ? 1 : 0;
         core_all.push_back(ci);
         moves.push_back(chi_idx(b));
         moves.push_back(I.pend0 + b);
@@ -1128,7 +1129,12 @@ pepo_status run_gate_wave_tail(pepo_ctx* c, Inst& I, GateWave& w) {
     int gx = (int)std::min<long long>(std::max<long long>(1, (rows + 63) / 64 * ceil_div(nmax, 64)),
                                       (long long)(2 * 152 * 4 / std::max(1, w.recon.n) + 1));
     gx = std::max(gx, 4);
-    LAUNCH_T(K_RECON, hitems(c, w.recon), w.recon.n, launch_reconstruct<T>(w.recon.d, w.recon.n, gx, 0, c->d_ptrs, c->d_ival, s));
+    if (use_umma<T>(c, chimax))
+      LAUNCH_T(K_RECON, hitems(c, w.recon), w.recon.n,
+               launch_recon_umma(w.recon.d, w.recon.n, chimax, c->d_ptrs, c->d_ival, c->d_kerr, s));
+    else
+      LAUNCH_T(K_RECON, hitems(c, w.recon), w.recon.n,
+               launch_reconstruct<T>(w.recon.d, w.recon.n, gx, 0, c->d_ptrs, c->d_ival, s));
   }
   LAUNCH_N(w.npairs, launch_commit(w.pairs.d, w.npairs, w.moves.d, w.nmoves, c->d_ptrs, c->d_ival, s));
   return PEPO_OK;
@@ -1139,7 +1145,7 @@ pepo_status run_bp_waves(pepo_ctx* c, Inst& I, std::vector<BpWave>& waves) {
   cudaStream_t s = c->stream;
   const int chimax = I.cfg.chi_max;
   for (auto& w : waves) {
-    LAUNCH_T(K_ENV, nullptr, w.eig.n, launch_env_eig(w.eig.d, w.eig.n, c->d_ival, s));
+    LAUNCH_T(K_ENV, nullptr, w.eig.n, launch_env_eig(w.eig.d, w.eig.n, chimax, c->tsize == 4 ? 1 : 0, c->d_ival, s));
     for (int a = 0; a < 4; ++a) {
       int gx = std::max(8, 2 * 152 * 4 / std::max(1, w.leg[a].n));
       LAUNCH_T(K_LEG, hitems(c, w.leg[a]), w.leg[a].n,
