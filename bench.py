@@ -181,11 +181,12 @@ def upload_state(eng, w, seed):
     with ThreadPoolExecutor(max_workers=window) as ex:
         futs = {}
         for v in range(min(window, n)):
-            futs[v] = ex.submit(site_tensor, Lx, Ly, chi, seed, v, np.float32)
+            futs[v] = ex.submit(site_tensor, Lx, Ly, chi, seed, v, np.float32, obs=w["obs"])
         for v in range(n):
             t = futs.pop(v).result()
             if v + window < n:
-                futs[v + window] = ex.submit(site_tensor, Lx, Ly, chi, seed, v + window, np.float32)
+                futs[v + window] = ex.submit(site_tensor, Lx, Ly, chi, seed, v + window, np.float32,
+                                             obs=w["obs"])
             eng.set_site(0, v, t)
             total += t.nbytes
             del t

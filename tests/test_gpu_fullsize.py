@@ -42,7 +42,7 @@ def test_first_colour_bonds_match_oracle_at_chi100(precision, tol):
     g1 = og.site_unitary("ZZ_X", 0.5 * w["h"] * w["dt"])
     for b in sampled:
         v1, v2 = b, b + 1
-        sites = {v: site_tensor(Lx, Ly, chi, bench.SEED, v, np.float32).astype(np.float64)
+        sites = {v: site_tensor(Lx, Ly, chi, bench.SEED, v, np.float32, obs=w["obs"]).astype(np.float64)
                  for v in (v1, v2)}
         net = opepo.from_pauli(Lx, Ly, w["obs"], "Z", sites, bd["chi"], bd["msgs"],
                                sites_subset={v1, v2})
