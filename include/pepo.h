@@ -89,7 +89,7 @@ typedef struct {
   double pinv_rel;         /* rank threshold for message square roots (1e-12) */
   int gates;               /* pepo_gateset */
   int prec;                /* pepo_precision */
-  int warm_start;          /* reserved, 0 */
+  int warm_start;          /* reserved, 0 (the warm start is driven through pepo_ws_*) */
   int inflight_sites;      /* sites updated concurrently (scratch slabs), 0 = auto */
 } pepo_config;
 
@@ -198,6 +198,56 @@ pepo_status pepo_set_site(pepo_ctx* ctx, int inst, int site, const void* data, i
  * Synchronises the stream. */
 pepo_status pepo_set_site_static(pepo_ctx* ctx, int inst, int site, const void* data, int dtype,
                                  size_t count);
+
+/* ---- Learned BP warm start ------------------------------------------------
+ * The paper has no learned part (it motivates one by BP's sweep counts and
+ * fixed-point traps, Sec. 6.3); this is the warm-start proposal of the
+ * hot-path scope.  Rows are (bond b, direction dir, Schmidt index k < chi_b)
+ * in bond order, dir 0 = first site -> second site; pepo_ws_rows gives their
+ * number (sum of 2 chi_b).  A row has PEPO_WS_FEATURES floats:
+ *   log lam_k, k / chi_b, S_b / log chi_b, deg(src) / 4, deg(dst) / 4,
+ *   |src - obs|_1 / (Lx + Ly), |dst - obs|_1 / (Lx + Ly), t = steps * dt, h,
+ *   J, mean and max of S_e / log chi_e over the source site's other bonds.
+ * The MLP maps a row to y = predicted log M_e[k, k] of the converged message
+ * (trace-1 normalised, in the bond's Schmidt basis): widths 12 -> 256 -> 256
+ * -> 1, exact (erf) GELU, weights and activations rounded to BF16 with FP32
+ * accumulation, mean squared error, Adam (0.9, 0.999, 1e-8) on an FP32 master
+ * copy.  Parameters are one float vector: W1 [12 x 256 row-major], b1 [256],
+ * W2 [256 x 256], b2 [256], W3 [256], b3 [1] (pepo_mlp_num_params floats).
+ * All *_dev pointers are device memory owned by the caller; calls are
+ * asynchronous on the stream given at init unless stated otherwise. */
+#define PEPO_WS_FEATURES 12
+#define PEPO_WS_WIDTH 256
+typedef struct pepo_mlp pepo_mlp;
+long long pepo_mlp_num_params(void);
+/* Device bytes for a network that trains / predicts up to max_rows rows. */
+size_t pepo_mlp_required_bytes(int max_rows);
+/* dev_buf: 256-byte aligned, pepo_mlp_required_bytes(max_rows) bytes, owned
+ * by the caller.  params: host floats (initial weights).  Synchronises.
+ * Errors: PEPO_E_INVALID, PEPO_E_OOM, PEPO_E_CUDA. */
+pepo_status pepo_mlp_init(void* dev_buf, size_t bytes, int max_rows, const float* params,
+                          void* cuda_stream, pepo_mlp** out);
+/* FP32 master weights to the host.  Synchronises. */
+pepo_status pepo_mlp_get_params(pepo_mlp* mlp, float* params_out);
+/* y_dev[rows] = MLP(X_dev[rows x 12]). */
+pepo_status pepo_mlp_forward(pepo_mlp* mlp, const float* X_dev, int rows, float* y_dev);
+/* Forward + backward of the mean squared error against t_dev; keeps the
+ * gradient for pepo_mlp_adam_step; loss_out / grad_host (num_params floats)
+ * may be NULL.  Synchronises. */
+pepo_status pepo_mlp_gradient(pepo_mlp* mlp, const float* X_dev, const float* t_dev, int rows,
+                              float* loss_out, float* grad_host);
+/* One Adam update with the last gradient. */
+pepo_status pepo_mlp_adam_step(pepo_mlp* mlp, float lr);
+void pepo_mlp_destroy(pepo_mlp* mlp);
+/* Row count of instance inst (-1 on error).  Synchronises. */
+int pepo_ws_rows(pepo_ctx* ctx, int inst);
+/* Feature rows of the current state into X_dev (rows beyond max_rows dropped). */
+pepo_status pepo_ws_features(pepo_ctx* ctx, int inst, float* X_dev, int max_rows);
+/* Training targets: log of the diagonal of the current (converged) messages. */
+pepo_status pepo_ws_targets(pepo_ctx* ctx, int inst, float* t_dev, int max_rows);
+/* Overwrite every message of the instance with diag(exp(y)) / sum exp(y)
+ * (the warm start; y_dev has pepo_ws_rows entries). */
+pepo_status pepo_ws_apply(pepo_ctx* ctx, int inst, const float* y_dev);
 
 /* Copy one directed message (chi x chi, row-major) to the host. */
 pepo_status pepo_get_message(pepo_ctx* ctx, int inst, int bond, int dir, double* out,

@@ -53,7 +53,10 @@ EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trot
            "pepo_bp_converge", "pepo_correlator", "pepo_get_spectrum", "pepo_get_site",
            "pepo_set_state", "pepo_set_bonds", "pepo_set_site", "pepo_set_site_static", "pepo_get_message", "pepo_num_bonds", "pepo_set_timing",
            "pepo_timing_classes", "pepo_timing_class_name", "pepo_get_timing", "pepo_reset_timing",
-           "pepo_launch_count", "pepo_last_error", "pepo_destroy"]
+           "pepo_launch_count", "pepo_last_error", "pepo_destroy",
+           "pepo_mlp_num_params", "pepo_mlp_required_bytes", "pepo_mlp_init", "pepo_mlp_get_params",
+           "pepo_mlp_forward", "pepo_mlp_gradient", "pepo_mlp_adam_step", "pepo_mlp_destroy",
+           "pepo_ws_rows", "pepo_ws_features", "pepo_ws_targets", "pepo_ws_apply"]
 
 _lib = None
 
@@ -93,6 +96,32 @@ def load_library(path=LIB_PATH):
     lib.pepo_set_site.restype = I
     lib.pepo_set_site_static.argtypes = [P, I, I, P, I, S]
     lib.pepo_set_site_static.restype = I
+    F = ctypes.c_float
+    FP = ctypes.POINTER(ctypes.c_float)
+    lib.pepo_mlp_num_params.argtypes = []
+    lib.pepo_mlp_num_params.restype = ctypes.c_longlong
+    lib.pepo_mlp_required_bytes.argtypes = [I]
+    lib.pepo_mlp_required_bytes.restype = S
+    lib.pepo_mlp_init.argtypes = [P, S, I, FP, P, ctypes.POINTER(P)]
+    lib.pepo_mlp_init.restype = I
+    lib.pepo_mlp_get_params.argtypes = [P, FP]
+    lib.pepo_mlp_get_params.restype = I
+    lib.pepo_mlp_forward.argtypes = [P, P, I, P]
+    lib.pepo_mlp_forward.restype = I
+    lib.pepo_mlp_gradient.argtypes = [P, P, P, I, FP, FP]
+    lib.pepo_mlp_gradient.restype = I
+    lib.pepo_mlp_adam_step.argtypes = [P, F]
+    lib.pepo_mlp_adam_step.restype = I
+    lib.pepo_mlp_destroy.argtypes = [P]
+    lib.pepo_mlp_destroy.restype = None
+    lib.pepo_ws_rows.argtypes = [P, I]
+    lib.pepo_ws_rows.restype = I
+    lib.pepo_ws_features.argtypes = [P, I, P, I]
+    lib.pepo_ws_features.restype = I
+    lib.pepo_ws_targets.argtypes = [P, I, P, I]
+    lib.pepo_ws_targets.restype = I
+    lib.pepo_ws_apply.argtypes = [P, I, P]
+    lib.pepo_ws_apply.restype = I
     lib.pepo_get_message.argtypes = [P, I, I, I, ctypes.POINTER(D), ctypes.POINTER(I)]
     lib.pepo_get_message.restype = I
     lib.pepo_num_bonds.argtypes = [P, I]
@@ -339,6 +368,42 @@ class Engine:
         self._check(self.lib.pepo_set_site_static(self.ctx, inst, v, ctypes.c_void_p(t.ctypes.data), dt,
                                                   t.size), "pepo_set_site_static")
 
+    # -- learned warm start
+    def ws_rows(self, inst=0):
+        r = int(self.lib.pepo_ws_rows(self.ctx, inst))
+        if r < 0:
+            raise PepoError("pepo_ws_rows failed")
+        return r
+
+    def ws_features(self, inst=0, out=None):
+        """Feature rows (torch float32 [rows, 12] on the device)."""
+        import torch
+        r = self.ws_rows(inst)
+        X = out if out is not None else torch.empty((r, WS_FEATURES), dtype=torch.float32, device=self.device)
+        self._check(self.lib.pepo_ws_features(self.ctx, inst, ctypes.c_void_p(X.data_ptr()), X.shape[0]),
+                    "pepo_ws_features")
+        return X
+
+    def ws_targets(self, inst=0, out=None):
+        """log diag of the current messages (torch float32 [rows])."""
+        import torch
+        r = self.ws_rows(inst)
+        t = out if out is not None else torch.empty((r,), dtype=torch.float32, device=self.device)
+        self._check(self.lib.pepo_ws_targets(self.ctx, inst, ctypes.c_void_p(t.data_ptr()), t.shape[0]),
+                    "pepo_ws_targets")
+        return t
+
+    def ws_apply(self, y, inst=0):
+        """Messages <- diag(exp(y)) / sum exp(y) per directed bond."""
+        self._check(self.lib.pepo_ws_apply(self.ctx, inst, ctypes.c_void_p(y.data_ptr())), "pepo_ws_apply")
+
+    def ws_warm_start(self, mlp, inst=0):
+        """Predict the converged message diagonals with `mlp` and install them."""
+        X = self.ws_features(inst)
+        y = mlp.forward(X)
+        self.ws_apply(y, inst)
+        return X.shape[0]
+
     def run(self, nsteps, measure_every=1):
         """Evolve nsteps, measuring C(t) (BP + correlator) every `measure_every` steps."""
         out = []
@@ -353,3 +418,94 @@ class Engine:
                 C, D = self.correlator()
                 out.append(pick(D))
         return out
+
+
+WS_FEATURES = 12
+WS_WIDTH = 256
+
+
+class Mlp:
+    """The warm-start network (device buffer owned here, kernels in libpepo)."""
+
+    def __init__(self, params, max_rows, device="cuda:0"):
+        import torch
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise PepoError("a CUDA device is required (no CPU fallback)")
+        self.device = torch.device(device)
+        self.n = int(self.lib.pepo_mlp_num_params())
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+        if p.size != self.n:
+            raise PepoError("expected %d parameters, got %d" % (self.n, p.size))
+        nbytes = int(self.lib.pepo_mlp_required_bytes(max_rows))
+        with torch.cuda.device(self.device):
+            self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.stream = torch.cuda.current_stream(self.device)
+        self.max_rows = max_rows
+        h = ctypes.c_void_p()
+        st = self.lib.pepo_mlp_init(ctypes.c_void_p(self.buf.data_ptr()), nbytes, max_rows,
+                                    p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise PepoError("pepo_mlp_init failed: %s" % STATUS.get(st, st))
+        self.h = h
+
+    def _ck(self, st, what):
+        if st != 0:
+            raise PepoError("%s failed (%s)" % (what, STATUS.get(st, st)))
+
+    def params(self):
+        out = np.zeros(self.n, dtype=np.float32)
+        self._ck(self.lib.pepo_mlp_get_params(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+                 "pepo_mlp_get_params")
+        return out
+
+    def forward(self, X, out=None):
+        import torch
+        X = X.contiguous()
+        y = out if out is not None else torch.empty((X.shape[0],), dtype=torch.float32, device=self.device)
+        self._ck(self.lib.pepo_mlp_forward(self.h, ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                           ctypes.c_void_p(y.data_ptr())), "pepo_mlp_forward")
+        return y
+
+    def gradient(self, X, t, want_grad=False):
+        X = X.contiguous()
+        t = t.contiguous()
+        loss = ctypes.c_float()
+        g = np.zeros(self.n, dtype=np.float32) if want_grad else None
+        self._ck(self.lib.pepo_mlp_gradient(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                            X.shape[0], ctypes.byref(loss),
+                                            g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if want_grad else None),
+                 "pepo_mlp_gradient")
+        return float(loss.value), g
+
+    def adam_step(self, lr):
+        self._ck(self.lib.pepo_mlp_adam_step(self.h, ctypes.c_float(lr)), "pepo_mlp_adam_step")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pepo_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def flat_params(p):
+    """Flat parameter vector (library order) from a dict W1, b1, W2, b2, W3, b3."""
+    return np.concatenate([np.asarray(p[k], dtype=np.float32).reshape(-1) for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+
+def unflat_params(v):
+    F, W = WS_FEATURES, WS_WIDTH
+    v = np.asarray(v, dtype=np.float64)
+    o = 0
+    out = {}
+    for k, shape in (("W1", (F, W)), ("b1", (W,)), ("W2", (W, W)), ("b2", (W,)), ("W3", (W, 1)), ("b3", (1,))):
+        n = int(np.prod(shape))
+        out[k] = v[o:o + n].reshape(shape)
+        o += n
+    return out

@@ -21,6 +21,7 @@
 #include "bp.h"
 #include "kernels.h"
 #include "linalg.h"
+#include "mlp.h"
 #include "pepo.h"
 
 using namespace pepo;
@@ -119,6 +120,7 @@ struct Inst {
   void* slab[1];       // unused
   std::vector<void*> site_slab;
   double *lam = nullptr, *msg = nullptr, *hat = nullptr, *vec = nullptr, *vhat = nullptr;
+  WsGeom* ws_geom = nullptr;          // 2 nb directed-bond descriptors of the warm-start features
   double *sigma = nullptr, *disc = nullptr, *svals = nullptr, *vs = nullptr, *fv = nullptr;
   double *ze = nullptr, *z2e = nullptr, *bethe_out = nullptr, *ptm = nullptr, *FA = nullptr, *FB = nullptr;
   int* nsv = nullptr;
@@ -357,6 +359,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
   I.ptm = cv.take<double>(I.nb * (size_t)256);
   I.FA = cv.take<double>(I.nb * (size_t)PEPO_RG * 16);
   I.FB = cv.take<double>(I.nb * (size_t)PEPO_RG * 16);
+  I.ws_geom = cv.take<WsGeom>(2 * (size_t)I.nb);
 
   auto chi_idx = [&](int b) { return I.chi0 + b; };
   auto msg_in = [&](int v, int b) {   // message into v on bond b
@@ -1462,6 +1465,32 @@ pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena, size
     ok = ok && cudaMemsetAsync(I.sigma, 0, sizeof(double) * I.N, s) == cudaSuccess;
     ok = ok && cudaMemsetAsync(I.disc, 0, sizeof(double) * I.nb, s) == cudaSuccess;
     ok = ok && cudaMemsetAsync(I.vec, 0, sizeof(double) * 2 * I.nb * chimax, s) == cudaSuccess;
+    {
+      // warm-start geometry of every directed bond (source = v1 for dir 0)
+      std::vector<WsGeom> geom(2 * (size_t)I.nb);
+      std::vector<int> deg(I.N, 0);
+      for (int v = 0; v < I.N; ++v) deg[v] = I.sites[v].deg;
+      const int Lx = I.cfg.Lx;
+      const float norm = (float)(I.cfg.Lx + I.cfg.Ly);
+      auto dist = [&](int v) { return (float)(std::abs(v % Lx - I.cfg.obs_x) + std::abs(v / Lx - I.cfg.obs_y)) / norm; };
+      for (int b = 0; b < I.nb; ++b)
+        for (int dir = 0; dir < 2; ++dir) {
+          const int src = dir == 0 ? I.bonds[b].v1 : I.bonds[b].v2;
+          const int dst = dir == 0 ? I.bonds[b].v2 : I.bonds[b].v1;
+          WsGeom g{};
+          for (int k = 0; k < I.sites[src].deg; ++k) {
+            const int e = I.sites[src].legs[k].bond;
+            if (e != b && g.n_other < 3) g.other[g.n_other++] = e;
+          }
+          g.deg_src = (float)deg[src];
+          g.deg_dst = (float)deg[dst];
+          g.dist_src = dist(src);
+          g.dist_dst = dist(dst);
+          geom[2 * (size_t)b + dir] = g;
+        }
+      ok = ok && cudaMemcpyAsync(I.ws_geom, geom.data(), sizeof(WsGeom) * geom.size(), cudaMemcpyHostToDevice,
+                                 s) == cudaSuccess;
+    }
     if (ok && launch_gates(I.gates.d, I.gates.n, s) != cudaSuccess) ok = false;
     c->launches++;
   }
@@ -1709,6 +1738,121 @@ pepo_status pepo_set_site_static(pepo_ctx* c, int inst, int site, const void* da
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return fail(c, PEPO_E_CUDA, "site permute");
   return PEPO_OK;
+}
+
+// ------------------------------------------------------- learned warm start
+struct pepo_mlp {
+  MlpBuffers B;
+  cudaStream_t stream = nullptr;
+  int max_rows = 0;
+  int adam_t = 0;
+  float last_loss = 0.f;
+};
+
+size_t pepo_mlp_required_bytes(int max_rows) {
+  if (max_rows < 1) return 0;
+  MlpBuffers B;
+  return mlp_layout(nullptr, max_rows, &B) + 256;
+}
+
+long long pepo_mlp_num_params(void) { return mlp_num_params(); }
+
+pepo_status pepo_mlp_init(void* dev_buf, size_t bytes, int max_rows, const float* params, void* cuda_stream,
+                          pepo_mlp** out) {
+  if (!out) return PEPO_E_INVALID;
+  *out = nullptr;
+  if (!dev_buf || !params || max_rows < 1 || (reinterpret_cast<uintptr_t>(dev_buf) & 255)) return PEPO_E_INVALID;
+  if (bytes < pepo_mlp_required_bytes(max_rows)) return PEPO_E_OOM;
+  pepo_mlp* m = new pepo_mlp;
+  mlp_layout(static_cast<char*>(dev_buf), max_rows, &m->B);
+  m->stream = static_cast<cudaStream_t>(cuda_stream);
+  m->max_rows = max_rows;
+  const size_t n = (size_t)mlp_num_params();
+  bool ok = cudaMemcpyAsync(m->B.p, params, sizeof(float) * n, cudaMemcpyHostToDevice, m->stream) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(m->B.m, 0, sizeof(float) * n, m->stream) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(m->B.v, 0, sizeof(float) * n, m->stream) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(m->stream) == cudaSuccess;
+  if (!ok) { delete m; return PEPO_E_CUDA; }
+  *out = m;
+  return PEPO_OK;
+}
+
+pepo_status pepo_mlp_get_params(pepo_mlp* m, float* params) {
+  if (!m || !params) return PEPO_E_INVALID;
+  if (cudaMemcpyAsync(params, m->B.p, sizeof(float) * (size_t)mlp_num_params(), cudaMemcpyDeviceToHost,
+                      m->stream) != cudaSuccess || cudaStreamSynchronize(m->stream) != cudaSuccess)
+    return PEPO_E_CUDA;
+  return PEPO_OK;
+}
+
+pepo_status pepo_mlp_forward(pepo_mlp* m, const float* X_dev, int rows, float* y_dev) {
+  if (!m || !X_dev || !y_dev || rows < 0 || rows > m->max_rows) return PEPO_E_INVALID;
+  if (rows == 0) return PEPO_OK;
+  return mlp_forward(m->B, X_dev, rows, y_dev, m->stream) == cudaSuccess ? PEPO_OK : PEPO_E_CUDA;
+}
+
+pepo_status pepo_mlp_gradient(pepo_mlp* m, const float* X_dev, const float* t_dev, int rows, float* loss_out,
+                              float* grad_host) {
+  if (!m || !X_dev || !t_dev || rows < 1 || rows > m->max_rows) return PEPO_E_INVALID;
+  if (mlp_gradient(m->B, X_dev, t_dev, rows, m->stream) != cudaSuccess) return PEPO_E_CUDA;
+  if (cudaMemcpyAsync(&m->last_loss, m->B.loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess)
+    return PEPO_E_CUDA;
+  if (grad_host && cudaMemcpyAsync(grad_host, m->B.g, sizeof(float) * (size_t)mlp_num_params(),
+                                   cudaMemcpyDeviceToHost, m->stream) != cudaSuccess)
+    return PEPO_E_CUDA;
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return PEPO_E_CUDA;
+  if (loss_out) *loss_out = m->last_loss;
+  return PEPO_OK;
+}
+
+pepo_status pepo_mlp_adam_step(pepo_mlp* m, float lr) {
+  if (!m || !(lr > 0.f)) return PEPO_E_INVALID;
+  m->adam_t++;
+  return mlp_adam(m->B, m->adam_t, lr, m->stream) == cudaSuccess ? PEPO_OK : PEPO_E_CUDA;
+}
+
+void pepo_mlp_destroy(pepo_mlp* m) { delete m; }
+
+int pepo_ws_rows(pepo_ctx* c, int inst) {
+  if (!c || inst < 0 || inst >= c->n_inst) return -1;
+  Inst& I = c->inst[inst];
+  std::vector<int> chi(I.nb);
+  if (cudaMemcpyAsync(chi.data(), c->d_ival + I.chi0, sizeof(int) * I.nb, cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return -1;
+  long long r = 0;
+  for (int x : chi) r += 2LL * x;
+  return (int)r;
+}
+
+pepo_status pepo_ws_features(pepo_ctx* c, int inst, float* X_dev, int max_rows) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst || !X_dev || max_rows < 0) return fail(c, PEPO_E_INVALID, "bad arguments");
+  Inst& I = c->inst[inst];
+  const float t = (float)(I.steps * I.cfg.dt);
+  cudaError_t e = launch_ws_features(I.ws_geom, I.nb, c->d_ival + I.chi0, I.lam, I.cfg.chi_max, t,
+                                     (float)I.cfg.h, (float)I.cfg.J, X_dev, max_rows, c->stream);
+  c->launches++;
+  return e == cudaSuccess ? PEPO_OK : fail(c, PEPO_E_CUDA, "warm-start features: %s", cudaGetErrorString(e));
+}
+
+pepo_status pepo_ws_targets(pepo_ctx* c, int inst, float* t_dev, int max_rows) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst || !t_dev || max_rows < 0) return fail(c, PEPO_E_INVALID, "bad arguments");
+  Inst& I = c->inst[inst];
+  cudaError_t e = launch_ws_targets(I.nb, c->d_ival + I.chi0, I.msg, I.cfg.chi_max, t_dev, max_rows, c->stream);
+  c->launches++;
+  return e == cudaSuccess ? PEPO_OK : fail(c, PEPO_E_CUDA, "warm-start targets: %s", cudaGetErrorString(e));
+}
+
+pepo_status pepo_ws_apply(pepo_ctx* c, int inst, const float* y_dev) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst || !y_dev) return fail(c, PEPO_E_INVALID, "bad arguments");
+  Inst& I = c->inst[inst];
+  cudaError_t e = launch_ws_apply(I.nb, c->d_ival + I.chi0, y_dev, I.msg, I.cfg.chi_max, c->stream);
+  c->launches++;
+  return e == cudaSuccess ? PEPO_OK : fail(c, PEPO_E_CUDA, "warm-start apply: %s", cudaGetErrorString(e));
 }
 
 pepo_status pepo_set_state(pepo_ctx* c, int inst, const double* sites, size_t count, const int* chi,
