@@ -540,10 +540,12 @@ __device__ int jacobi_svd(R* A, int m, int n, R* V, int max_sweeps, int* capped,
   __syncthreads();
   if (n < 2) return 0;
   const int np = (n % 2) ? n + 1 : n;   // players incl. a dummy
-  // orthogonality target: a few units of the working precision times sqrt(m)
-  const double tol = (sizeof(R) == 4 ? 2e-7 : 1e-15) * sqrt((double)m);
-  // columns below 1e-30 of the total squared norm are numerically zero: rotating
-  // them only stirs rounding noise and never converges
+  // orthogonality target: above the rounding noise of a length-m dot product
+  // in the working precision (FP32 columns: ~sqrt(m) 6e-8 relative)
+  const double tol = (sizeof(R) == 4 ? 3e-7 : 1e-15) * sqrt((double)m);
+  // columns below 1e-30 (FP64) or 1e-13 (FP32) of the total squared norm are
+  // numerically zero in that precision: rotating them only stirs rounding
+  // noise and never converges
   double fro = 0.0;
   for (long long e = threadIdx.x; e < (long long)m * n; e += blockDim.x) fro = fma((double)A[e], (double)A[e], fro);
   {
@@ -555,7 +557,7 @@ __device__ int jacobi_svd(R* A, int m, int n, R* V, int max_sweeps, int* capped,
     for (int i = 0; i < nw; ++i) fro += fr[i];
     __syncthreads();
   }
-  const double negligible = 1e-30 * fro;
+  const double negligible = (sizeof(R) == 4 ? 1e-13 : 1e-30) * fro;
   __shared__ int sh_rot;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
