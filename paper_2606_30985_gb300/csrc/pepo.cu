@@ -177,6 +177,22 @@ struct pepo_ctx {
   std::vector<Tot> tot;
   int max_levels = 1;      // TSQR levels
   int rmax = 4, nmax = 4;
+  // grouped execution: every instance's items of one wave / colour / level
+  // concatenated into one launch (plan fields of grp only; grp.cfg.chi_max =
+  // the context-wide chi_max)
+  Inst grp;
+  int* d_active = nullptr;                 // per-instance BP activity mask
+  // CUDA graphs of one Trotter step, one BP sweep and one single-layer sweep
+  // (captured on a private stream at first use, launched on `stream`)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_exec = nullptr, bp_exec = nullptr, sl_exec = nullptr;
+  long long step_launches = 0, bp_launches = 0, sl_launches = 0;
+  bool graphs_failed = false;
+  ~pepo_ctx() {
+    for (cudaGraphExec_t e : {step_exec, bp_exec, sl_exec})
+      if (e) cudaGraphExecDestroy(e);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
 };
 
 namespace {
@@ -896,7 +912,11 @@ void finalize_items(pepo_ctx* c, Planner& P) {
 
 void resolve_all(pepo_ctx* c) {
   char* d = c->d_items;
-  for (auto& I : c->inst) {
+  std::vector<Inst*> all;
+  for (auto& I : c->inst) all.push_back(&I);
+  all.push_back(&c->grp);
+  for (Inst* Ip : all) {
+    Inst& I = *Ip;
     for (int col = 0; col < 4; ++col) resolve(I.gcore[col], d);
     for (int col = 0; col < 4; ++col)
       for (auto& w : I.gwaves[col]) {
@@ -918,6 +938,109 @@ void resolve_all(pepo_ctx* c) {
   }
 }
 
+template <class T> DArr<T> cat_items(Planner& P, const std::vector<const DArr<T>*>& parts) {
+  std::vector<T> v;
+  for (const DArr<T>* a : parts) {
+    const T* src = reinterpret_cast<const T*>(P.st.bytes.data() + a->off);
+    v.insert(v.end(), src, src + a->n);
+  }
+  return stage(P, v);
+}
+
+// Concatenate the item arrays of all instances per colour / wave index /
+// level into the group plan (instances with fewer waves contribute nothing to
+// the higher wave indices).  Instances own disjoint state and scratch, so the
+// items of one grouped launch never touch each other's memory.
+void build_group(Planner& P, pepo_ctx* c) {
+  Inst& G = c->grp;
+  G.cfg = c->inst[0].cfg;
+  G.cfg.chi_max = c->chimax;
+  if (c->n_inst == 1) {
+    const Inst& I = c->inst[0];
+    for (int col = 0; col < 4; ++col) { G.gwaves[col] = I.gwaves[col]; G.gcore[col] = I.gcore[col]; }
+    G.bwaves = I.bwaves;
+    G.fwaves = I.fwaves;
+    for (int l = 0; l < 4; ++l) G.sl[l] = I.sl[l];
+    G.msgs = I.msgs; G.sscal = I.sscal; G.escal = I.escal; G.bethe = I.bethe;
+    return;
+  }
+  for (int col = 0; col < 4; ++col) {
+    size_t nw = 0;
+    for (auto& I : c->inst) nw = std::max(nw, I.gwaves[col].size());
+    G.gwaves[col].assign(nw, GateWave());
+    for (size_t w = 0; w < nw; ++w) {
+      std::vector<const GateWave*> parts;
+      for (auto& I : c->inst) if (w < I.gwaves[col].size()) parts.push_back(&I.gwaves[col][w]);
+      auto pick = [&](auto field) {
+        using A = std::remove_reference_t<decltype(field(*parts[0]))>;
+        std::vector<const A*> v;
+        for (auto* g : parts) v.push_back(&field(*g));
+        return cat_items(P, v);
+      };
+      GateWave& gw = G.gwaves[col][w];
+      gw.env = pick([](const GateWave& g) -> const DArr<EnvFactorItem>& { return g.env; });
+      for (int r = 0; r < 3; ++r) {
+        std::vector<const DArr<LegItem>*> v;
+        for (auto* g : parts) v.push_back(&g->leg[r]);
+        gw.leg[r] = cat_items(P, v);
+      }
+      gw.copy = pick([](const GateWave& g) -> const DArr<TView>& { return g.copy; });
+      gw.copy_out = pick([](const GateWave& g) -> const DArr<int>& { return g.copy_out; });
+      gw.fac = pick([](const GateWave& g) -> const DArr<SiteFacItem>& { return g.fac; });
+      gw.gram = pick([](const GateWave& g) -> const DArr<GramRowsItem>& { return g.gram; });
+      gw.core = pick([](const GateWave& g) -> const DArr<CoreItem>& { return g.core; });
+      gw.recon = pick([](const GateWave& g) -> const DArr<ReconItem>& { return g.recon; });
+      gw.pairs = pick([](const GateWave& g) -> const DArr<int>& { return g.pairs; });
+      gw.moves = pick([](const GateWave& g) -> const DArr<int>& { return g.moves; });
+      gw.npairs = gw.pairs.n / 2;
+      gw.nmoves = gw.moves.n / 2;
+    }
+    std::vector<const DArr<CoreItem>*> cores;
+    for (auto& I : c->inst) cores.push_back(&I.gcore[col]);
+    G.gcore[col] = cat_items(P, cores);
+  }
+  for (int f = 0; f < 2; ++f) {
+    std::vector<BpWave>& out = f ? G.fwaves : G.bwaves;
+    size_t nw = 0;
+    for (auto& I : c->inst) nw = std::max(nw, (f ? I.fwaves : I.bwaves).size());
+    out.assign(nw, BpWave());
+    for (size_t w = 0; w < nw; ++w) {
+      std::vector<const DArr<EnvEigItem>*> eig;
+      std::vector<const DArr<LegItem>*> leg[4];
+      std::vector<const DArr<GramLegItem>*> gram;
+      std::vector<const DArr<RotItem>*> rot;
+      for (auto& I : c->inst) {
+        const std::vector<BpWave>& src = f ? I.fwaves : I.bwaves;
+        if (w >= src.size()) continue;
+        eig.push_back(&src[w].eig);
+        for (int a = 0; a < 4; ++a) leg[a].push_back(&src[w].leg[a]);
+        gram.push_back(&src[w].gram);
+        rot.push_back(&src[w].rot);
+      }
+      out[w].eig = cat_items(P, eig);
+      for (int a = 0; a < 4; ++a) out[w].leg[a] = cat_items(P, leg[a]);
+      out[w].gram = cat_items(P, gram);
+      out[w].rot = cat_items(P, rot);
+    }
+  }
+  for (int l = 0; l < 4; ++l) {
+    std::vector<const DArr<VecItem>*> v;
+    for (auto& I : c->inst) v.push_back(&I.sl[l].items);
+    G.sl[l].items = cat_items(P, v);
+  }
+  {
+    std::vector<const DArr<MsgItem>*> m;
+    std::vector<const DArr<SiteScalarItem>*> ss;
+    std::vector<const DArr<EdgeItem>*> es;
+    std::vector<const DArr<BetheItem>*> be;
+    for (auto& I : c->inst) { m.push_back(&I.msgs); ss.push_back(&I.sscal); es.push_back(&I.escal); be.push_back(&I.bethe); }
+    G.msgs = cat_items(P, m);
+    G.sscal = cat_items(P, ss);
+    G.escal = cat_items(P, es);
+    G.bethe = cat_items(P, be);
+  }
+}
+
 // full arena layout; base == nullptr computes the size only
 size_t layout_arena(pepo_ctx* c, char* base, Planner* keep) {
   Carver cv(base);
@@ -928,6 +1051,7 @@ size_t layout_arena(pepo_ctx* c, char* base, Planner* keep) {
   for (int i = 0; i < c->n_inst; ++i) {
     if (!plan_instance(P, c->inst[i], i)) return 0;
   }
+  build_group(P, c);
   c->n_ptrs = (int)P.ptr_init.size();
   c->n_ival = (int)P.ival_init.size();
   c->d_ptrs = cv.take<void*>(c->n_ptrs);
@@ -936,6 +1060,7 @@ size_t layout_arena(pepo_ctx* c, char* base, Planner* keep) {
   c->d_delta1 = cv.take<unsigned long long>(c->n_inst);
   c->d_flags = cv.take<int>(c->n_inst);
   c->d_kerr = cv.take<int>(1);
+  c->d_active = cv.take<int>(c->n_inst);
   c->d_items = cv.take<char>(P.st.bytes.size() + 256);
   size_t total = cv.off + kAlign;
   if (keep) *keep = std::move(P);
@@ -1173,23 +1298,74 @@ pepo_status run_sl_pass(pepo_ctx* c, Inst& I) {
   return PEPO_OK;
 }
 
+// one Trotter step of every instance (grouped launches)
+template <typename T>
+pepo_status step_launches(pepo_ctx* c) {
+  Inst& G = c->grp;
+  for (int col = 0; col < 4; ++col) {
+    for (auto& w : G.gwaves[col]) {
+      pepo_status st = run_gate_wave<T>(c, G, w);
+      if (st != PEPO_OK) return st;
+    }
+    LAUNCH_T(K_CORE, nullptr, G.gcore[col].n, launch_core(G.gcore[col].d, G.gcore[col].n, c->d_ival, c->d_flags, c->stream));
+    for (auto& w : G.gwaves[col]) {
+      pepo_status st = run_gate_wave_tail<T>(c, G, w);
+      if (st != PEPO_OK) return st;
+    }
+  }
+  return PEPO_OK;
+}
+
+// Capture `body` (launches on c->stream) into a graph on the private capture
+// stream; returns false (and launches nothing) when capture is not possible.
+template <class F>
+bool capture_graph(pepo_ctx* c, cudaGraphExec_t* exec, long long* nlaunch, F body) {
+  if (c->graphs_failed || c->cap_stream == nullptr) return false;
+  cudaStream_t user = c->stream;
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    c->graphs_failed = true;
+    cudaGetLastError();
+    return false;
+  }
+  c->stream = c->cap_stream;
+  const long long l0 = c->launches;
+  const pepo_status st = body();
+  c->stream = user;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  *nlaunch = c->launches - l0;
+  c->launches = l0;
+  if (st != PEPO_OK || e != cudaSuccess || g == nullptr ||
+      cudaGraphInstantiate(exec, g, 0) != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    *exec = nullptr;
+    c->graphs_failed = true;
+    cudaGetLastError();
+    return false;
+  }
+  cudaGraphDestroy(g);
+  return true;
+}
+
 template <typename T>
 pepo_status do_steps(pepo_ctx* c, int n) {
-  for (int step = 0; step < n; ++step)
-    for (auto& I : c->inst) {
-      for (int col = 0; col < 4; ++col) {
-        for (auto& w : I.gwaves[col]) {
-          pepo_status st = run_gate_wave<T>(c, I, w);
-          if (st != PEPO_OK) return st;
-        }
-        LAUNCH_T(K_CORE, nullptr, I.gcore[col].n, launch_core(I.gcore[col].d, I.gcore[col].n, c->d_ival, c->d_flags, c->stream));
-        for (auto& w : I.gwaves[col]) {
-          pepo_status st = run_gate_wave_tail<T>(c, I, w);
-          if (st != PEPO_OK) return st;
-        }
+  for (int step = 0; step < n; ++step) {
+    bool done = false;
+    if (!c->timing) {
+      if (!c->step_exec) capture_graph(c, &c->step_exec, &c->step_launches, [&] { return step_launches<T>(c); });
+      if (c->step_exec) {
+        if (cudaGraphLaunch(c->step_exec, c->stream) != cudaSuccess)
+          return fail(c, PEPO_E_CUDA, "step graph launch: %s", cudaGetErrorString(cudaGetLastError()));
+        c->launches += c->step_launches;
+        done = true;
       }
-      I.steps++;
     }
+    if (!done) {
+      pepo_status st = step_launches<T>(c);
+      if (st != PEPO_OK) return st;
+    }
+    for (auto& I : c->inst) I.steps++;
+  }
   c->stepped = true;
   return PEPO_OK;
 }
@@ -1200,27 +1376,50 @@ double bits_to_double(unsigned long long u) {
   return d;
 }
 
+// one double-layer BP sweep of every active instance
+template <typename T>
+pepo_status bp_sweep_launches(pepo_ctx* c) {
+  cudaStream_t s = c->stream;
+  if (cudaMemsetAsync(c->d_delta2, 0, sizeof(unsigned long long) * c->n_inst, s) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "memset delta");
+  pepo_status st = run_bp_waves<T>(c, c->grp, c->grp.bwaves);
+  if (st != PEPO_OK) return st;
+  LAUNCH_T(K_MSG, nullptr, c->grp.msgs.n,
+           launch_bp_finish(c->grp.msgs.d, c->grp.msgs.n, c->d_ival, c->d_active, c->d_delta2, c->d_flags, s));
+  return PEPO_OK;
+}
+
 template <typename T>
 pepo_status do_bp(pepo_ctx* c, int* sweeps_out, double* delta_out) {
   cudaStream_t s = c->stream;
-  std::vector<int> done(c->n_inst, 0), sweeps(c->n_inst, 0);
+  std::vector<int> done(c->n_inst, 0), sweeps(c->n_inst, 0), active(c->n_inst, 1);
   std::vector<double> delta(c->n_inst, INFINITY);
   std::vector<unsigned long long> hd(c->n_inst);
   int maxs = 0;
   for (auto& I : c->inst) maxs = std::max(maxs, I.cfg.bp_max_sweeps);
   for (int sw = 1; sw <= maxs; ++sw) {
     bool any = false;
-    if (cudaMemsetAsync(c->d_delta2, 0, sizeof(unsigned long long) * c->n_inst, s) != cudaSuccess)
-      return fail(c, PEPO_E_CUDA, "memset delta");
     for (int i = 0; i < c->n_inst; ++i) {
-      Inst& I = c->inst[i];
-      if (done[i] || sw > I.cfg.bp_max_sweeps) continue;
-      any = true;
-      pepo_status st = run_bp_waves<T>(c, I, I.bwaves);
-      if (st != PEPO_OK) return st;
-      LAUNCH_T(K_MSG, nullptr, I.msgs.n, launch_bp_finish(I.msgs.d, I.msgs.n, c->d_ival, nullptr, c->d_delta2, c->d_flags, s));
+      active[i] = (!done[i] && sw <= c->inst[i].cfg.bp_max_sweeps) ? 1 : 0;
+      any = any || active[i];
     }
     if (!any) break;
+    if (cudaMemcpyAsync(c->d_active, active.data(), sizeof(int) * c->n_inst, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return fail(c, PEPO_E_CUDA, "active mask upload");
+    bool launched = false;
+    if (!c->timing) {
+      if (!c->bp_exec) capture_graph(c, &c->bp_exec, &c->bp_launches, [&] { return bp_sweep_launches<T>(c); });
+      if (c->bp_exec) {
+        if (cudaGraphLaunch(c->bp_exec, s) != cudaSuccess)
+          return fail(c, PEPO_E_CUDA, "BP graph launch: %s", cudaGetErrorString(cudaGetLastError()));
+        c->launches += c->bp_launches;
+        launched = true;
+      }
+    }
+    if (!launched) {
+      pepo_status st = bp_sweep_launches<T>(c);
+      if (st != PEPO_OK) return st;
+    }
     int kerr = 0;
     if (cudaMemcpyAsync(hd.data(), c->d_delta2, sizeof(unsigned long long) * c->n_inst,
                         cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -1229,8 +1428,8 @@ pepo_status do_bp(pepo_ctx* c, int* sweeps_out, double* delta_out) {
       return fail(c, PEPO_E_CUDA, "BP delta readback: %s", cudaGetErrorString(cudaGetLastError()));
     if (kerr) return fail(c, PEPO_E_CUDA, "a tensor-core pipeline wait expired (kernel error word %d)", kerr);
     for (int i = 0; i < c->n_inst; ++i) {
+      if (!active[i]) continue;
       Inst& I = c->inst[i];
-      if (done[i] || sw > I.cfg.bp_max_sweeps) continue;
       sweeps[i] = sw;
       delta[i] = bits_to_double(hd[i]);
       if (delta[i] < I.cfg.bp_tol || sw == I.cfg.bp_max_sweeps) done[i] = 1;
@@ -1246,27 +1445,50 @@ pepo_status do_bp(pepo_ctx* c, int* sweeps_out, double* delta_out) {
 }
 
 template <typename T>
+pepo_status sl_sweep_launches(pepo_ctx* c) {
+  cudaStream_t s = c->stream;
+  if (cudaMemsetAsync(c->d_delta1, 0, sizeof(unsigned long long) * c->n_inst, s) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "memset delta");
+  pepo_status st = run_sl_pass<T>(c, c->grp);
+  if (st != PEPO_OK) return st;
+  LAUNCH_T(K_MSG, nullptr, c->grp.msgs.n,
+           launch_sl_finish(c->grp.msgs.d, c->grp.msgs.n, c->d_ival, c->d_active, c->d_delta1, s));
+  return PEPO_OK;
+}
+
+template <typename T>
 pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
   cudaStream_t s = c->stream;
-  for (auto& I : c->inst) LAUNCH_N(I.msgs.n, launch_sl_init(I.msgs.d, I.msgs.n, c->d_ival, s));
-  std::vector<int> done(c->n_inst, 0), sweeps(c->n_inst, 0);
+  Inst& G = c->grp;
+  LAUNCH_N(G.msgs.n, launch_sl_init(G.msgs.d, G.msgs.n, c->d_ival, s));
+  std::vector<int> done(c->n_inst, 0), sweeps(c->n_inst, 0), active(c->n_inst, 1);
   std::vector<double> delta(c->n_inst, INFINITY);
   std::vector<unsigned long long> hd(c->n_inst);
   int maxs = 0;
   for (auto& I : c->inst) maxs = std::max(maxs, I.cfg.bp_max_sweeps);
   for (int sw = 1; sw <= maxs; ++sw) {
     bool any = false;
-    if (cudaMemsetAsync(c->d_delta1, 0, sizeof(unsigned long long) * c->n_inst, s) != cudaSuccess)
-      return fail(c, PEPO_E_CUDA, "memset delta");
     for (int i = 0; i < c->n_inst; ++i) {
-      Inst& I = c->inst[i];
-      if (done[i] || sw > I.cfg.bp_max_sweeps) continue;
-      any = true;
-      pepo_status st = run_sl_pass<T>(c, I);
-      if (st != PEPO_OK) return st;
-      LAUNCH_T(K_MSG, nullptr, I.msgs.n, launch_sl_finish(I.msgs.d, I.msgs.n, c->d_ival, nullptr, c->d_delta1, s));
+      active[i] = (!done[i] && sw <= c->inst[i].cfg.bp_max_sweeps) ? 1 : 0;
+      any = any || active[i];
     }
     if (!any) break;
+    if (cudaMemcpyAsync(c->d_active, active.data(), sizeof(int) * c->n_inst, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return fail(c, PEPO_E_CUDA, "active mask upload");
+    bool launched = false;
+    if (!c->timing) {
+      if (!c->sl_exec) capture_graph(c, &c->sl_exec, &c->sl_launches, [&] { return sl_sweep_launches<T>(c); });
+      if (c->sl_exec) {
+        if (cudaGraphLaunch(c->sl_exec, s) != cudaSuccess)
+          return fail(c, PEPO_E_CUDA, "single-layer graph launch: %s", cudaGetErrorString(cudaGetLastError()));
+        c->launches += c->sl_launches;
+        launched = true;
+      }
+    }
+    if (!launched) {
+      pepo_status st = sl_sweep_launches<T>(c);
+      if (st != PEPO_OK) return st;
+    }
     int kerr = 0;
     if (cudaMemcpyAsync(hd.data(), c->d_delta1, sizeof(unsigned long long) * c->n_inst,
                         cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -1275,22 +1497,22 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
       return fail(c, PEPO_E_CUDA, "single-layer delta readback");
     if (kerr) return fail(c, PEPO_E_CUDA, "a tensor-core pipeline wait expired (kernel error word %d)", kerr);
     for (int i = 0; i < c->n_inst; ++i) {
+      if (!active[i]) continue;
       Inst& I = c->inst[i];
-      if (done[i] || sw > I.cfg.bp_max_sweeps) continue;
       sweeps[i] = sw;
       delta[i] = bits_to_double(hd[i]);
       if (delta[i] < I.cfg.bp_tol || sw == I.cfg.bp_max_sweeps) done[i] = 1;
     }
   }
   // final estimates from the converged messages, then the Bethe sums
-  for (auto& I : c->inst) {
-    pepo_status st = run_sl_pass<T>(c, I);
+  {
+    pepo_status st = run_sl_pass<T>(c, G);
     if (st != PEPO_OK) return st;
-    st = run_bp_waves<T>(c, I, I.fwaves);
+    st = run_bp_waves<T>(c, G, G.fwaves);
     if (st != PEPO_OK) return st;
-    LAUNCH_N(I.sscal.n, launch_site_scalars(I.sscal.d, I.sscal.n, c->d_ival, s));
-    LAUNCH_N(I.escal.n, launch_edge_scalars(I.escal.d, I.escal.n, c->d_ival, s));
-    LAUNCH_N(1, launch_bethe(I.bethe.d, 1, s));
+    LAUNCH_N(G.sscal.n, launch_site_scalars(G.sscal.d, G.sscal.n, c->d_ival, s));
+    LAUNCH_N(G.escal.n, launch_edge_scalars(G.escal.d, G.escal.n, c->d_ival, s));
+    LAUNCH_N(G.bethe.n, launch_bethe(G.bethe.d, G.bethe.n, s));
   }
   std::vector<int> flags(c->n_inst);
   int kerr = 0;
@@ -1443,6 +1665,10 @@ pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena, size
                              s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->d_flags, 0, sizeof(int) * n_inst, s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->d_kerr, 0, sizeof(int), s) == cudaSuccess;
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    c->cap_stream = nullptr;   // graphs off; launches go to the stream directly
+    cudaGetLastError();
+  }
   resolve_all(c);
   // initial state (Sec. 2.3): chi = 1 everywhere, observable Pauli at c, I elsewhere
   for (auto& I : c->inst) {
