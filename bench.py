@@ -36,6 +36,9 @@ def parse():
     ap.add_argument("--grid", type=int, default=None, help="override the grid side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default=None, help="tf32x3 | fp32 | fp64 (default tf32x3)")
+    ap.add_argument("--workload", default="c5", choices=["c5", "c3"],
+                    help="c5: 10x10 chi=100 saturated step (default); c3: 64 batched instances "
+                         "from the initial state (instance-steps/s)")
     return ap.parse_args()
 
 
@@ -347,9 +350,88 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_batched(args, rank, world, local):
+    """64 independent instances (grids 4x4..6x6, chi_max 16/32/48, seeded h) in
+    one context: grouped launches + CUDA graphs; steps from the initial state."""
+    import torch
+    import paper_2606_30985_gb300 as pkg
+    from workloads.configs import c3_instances
+
+    torch.cuda.set_device(local)
+    prec = args.prec or "tf32x3"
+    insts = c3_instances(seed=SEED + rank)
+    cfgs = [pkg.Config(**{k: v for k, v in c.items() if k not in ("nsteps", "precision")}, precision=prec)
+            for c in insts]
+    eng = pkg.Engine(cfgs, device="cuda:%d" % local)
+
+    def one_step():
+        eng.trotter_step(1)
+        sw, de = eng.bp_converge()
+        C, D = eng.correlator()
+        return sw, C
+
+    for i in range(args.warmup):
+        one_step()
+    dist = world > 1 and torch.distributed.is_initialized()
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", "clocks_c3_rank%d.csv" % rank)
+                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks.csv")
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = eng.launches()
+    h0 = time.perf_counter()
+    e0.record(stream)
+    sweeps = []
+    for _ in range(args.steps):
+        sw, C = one_step()
+        sweeps.append(int(np.max(sw)))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - h0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms, wall], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, wall = float(t[0]), float(t[1])
+    n_units = len(cfgs) * args.steps * world
+    out = {
+        "metric": "instance-steps/s, 64 batched TFIM instances (gates + BP + Bethe C(t))",
+        "value": n_units / (ms / 1e3), "unit": "instance-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic (Sec. 2.3 initial state, seeded h)",
+        "config": {"workload": "64 instances: grids 4x4/5x5/6x6, chi_max 16/32/48, h ~ U[0.5, 3] (seed %d), "
+                               "J=1, dt=0.05, order 2, steps %d..%d from the initial state"
+                               % (SEED + rank, args.warmup + 1, args.warmup + args.steps),
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set below L2 at these steps; no flush (launch-bound regime)",
+                   "bp_sweeps_max": sweeps},
+        "clocks": clk,
+        "e2e": {"value": n_units / wall, "unit": "instance-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 8 * 14 * len(cfgs) + 8 * len(cfgs)},
+        "gpu_launches": eng.launches() - l0,
+    }
+    eng.close()
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload == "c3" and args.impl != "reference":
+        if world > 1:
+            import torch
+            torch.distributed.init_process_group("nccl")
+        out = run_batched(args, rank, world, local)
+        if rank == 0:
+            print(json.dumps(out))
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
     if args.impl == "reference":
         if rank != 0:
             return

@@ -92,6 +92,18 @@ __device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag
   }
 }
 
+// warp-uniform wait (every lane agrees, so the warp leaves a loop together)
+__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err) {
+  const bool ok = mbar_wait(b, parity, abort_flag, err);
+  return __all_sync(0xffffffffu, ok);
+}
+// one arrival per warp once every lane's shared-memory writes are ordered
+// before it (the lanes' proxy fences precede the warp barrier)
+__device__ __forceinline__ void warp_arrive(uint64_t* b) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(b);
+}
+
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -156,9 +168,6 @@ __device__ __forceinline__ float tf32_hi(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
-}
-__device__ __forceinline__ float pick(const float4& v, int e) {
-  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
 }
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -274,9 +283,9 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
       acc += L.tiles;
     }
     toff[n_items] = acc;
-    for (int s = 0; s < NS; ++s) { mbar_init(&bars->full[s], kConv); mbar_init(&bars->empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&bars->accfull[b], 1); mbar_init(&bars->accempty[b], 128); }
-    mbar_init(&bars->bfull, kConv);
+    for (int s = 0; s < NS; ++s) { mbar_init(&bars->full[s], kConv / 32); mbar_init(&bars->empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&bars->accfull[b], 1); mbar_init(&bars->accempty[b], 4); }
+    mbar_init(&bars->bfull, kConv / 32);
     mbar_init(&bars->bfree, 1);
     mbar_init(&bars->drain, 1);
     bars->abort_flag = 0;
@@ -354,7 +363,7 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
     long long tc = 0;
     while (live) {
       const int b = (int)(tc & 1);
-      if (!mbar_wait(&bars->accfull[b], (uint32_t)((tc >> 1) & 1), abort_flag, err)) break;
+      if (!warp_wait(&bars->accfull[b], (uint32_t)((tc >> 1) & 1), abort_flag, err)) break;
       tc_after();
       const LegDims& L = c.L;
       const long long rg = c.tile * kM + row;
@@ -378,19 +387,22 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
         }
       }
       tc_before();
-      mbar_arrive(&bars->accempty[b]);
+      warp_arrive(&bars->accempty[b]);
       ++tc;
       if (c.left == 1) break;
       cursor_next(c, toff, n_items, items, ptrs, ival);
     }
   } else if (warp >= 8) {
     // ------------------------------------------------------------ converters
-    // Loads run two chunks ahead of the shared-memory stores (register ring
-    // v0, v1, v2), so three chunks of global reads are in flight per thread.
+    // Each thread owns one row r of the tile and, per chunk, four 4-wide K
+    // groups (jq = jq0 + 2 u): four coalesced 4-byte loads per group (the
+    // lanes of a warp read 32 consecutive rows), then one 16-byte store per
+    // group into the K-major layout (8 consecutive rows per quarter warp: no
+    // bank conflicts).  Loads run two chunks ahead of the stores (register
+    // ring v0, v1, v2).
     const int ct = tid - 256, cw = ct >> 5;
-    const int jj = lane & 3, rq = (lane >> 2) & 1, a = lane >> 3;
-    const int r = 32 * (cw & 3) + 8 * a + 4 * rq;   // this thread's 4-row group
-    const int jq0 = cw >> 2;                        // j quads jq0, jq0 + 2, +4, +6
+    const int r = 32 * (cw & 3) + lane;             // this thread's row
+    const int jq0 = cw >> 2;                        // K groups jq0, jq0 + 2, +4, +6
     // load cursor
     LegCursor lc;
     bool lc_live = cursor_start(lc, toff, n_items, t0, t1, items, ptrs, ival);
@@ -412,10 +424,18 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
 #pragma unroll
       for (int u = 0; u < 4; ++u) v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (!lc_live) return;
+      if (lvalid) {
+        const int J = lc.L.J;
+        const long long Q = lc.L.Q;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = lkc * kKC + 4 * (jq0 + 2 * u) + jj;
-        if (lvalid && j < lc.L.J) v[u] = __ldg(reinterpret_cast<const float4*>(lsrc + (long long)j * lc.L.Q));
+        for (int u = 0; u < 4; ++u) {
+          const int j = lkc * kKC + 4 * (jq0 + 2 * u);
+          const float* p0 = lsrc + (long long)j * Q;
+          if (j < J) v[u].x = __ldg(p0);
+          if (j + 1 < J) v[u].y = __ldg(p0 + Q);
+          if (j + 2 < J) v[u].z = __ldg(p0 + 2 * Q);
+          if (j + 3 < J) v[u].w = __ldg(p0 + 3 * Q);
+        }
       }
       if (++lkc < (lc.L.K8 + kKC - 1) / kKC) return;
       if (lc.left == 1) { lc_live = false; return; }
@@ -435,7 +455,7 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
       const LegDims& L = c.L;
       load_next(v2);
       if (need_b) {
-        if (item_n > 0 && !mbar_wait(&bars->bfree, (uint32_t)((item_n - 1) & 1), abort_flag, err)) break;
+        if (item_n > 0 && !warp_wait(&bars->bfree, (uint32_t)((item_n - 1) & 1), abort_flag, err)) break;
         // [Ah; Al]: rows n < N16 hold hi(A[n, :]), rows N16 + n hold lo(A[n, :])
         const uint32_t lbo_b = (uint32_t)(2 * L.N16 / 8) * 128;
         for (int e = ct; e < L.N16 * L.K8; e += kConv) {
@@ -450,29 +470,24 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
           *reinterpret_cast<float*>(Bs + kb + (size_t)(n2 >> 3) * 128 + (size_t)(n2 & 7) * 16) = l;
         }
         fence_async_smem();
-        mbar_arrive(&bars->bfull);
+        warp_arrive(&bars->bfull);
         need_b = false;
       }
       const int s = (int)(cc % NS);
-      if (!mbar_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) break;
+      if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) break;
       unsigned char* hi = As + (size_t)s * P.stage_bytes;
       unsigned char* lo = hi + P.stage_bytes / 2;
-      const size_t rbase = (size_t)(r >> 3) * 128 + (size_t)jj * 4;
+      const size_t rbase = (size_t)(r >> 3) * 128 + (size_t)(r & 7) * 16;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const size_t kb = (size_t)(jq0 + 2 * u) * 2048 + rbase;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int e = (i + a) & 3;        // rotation keeps the 32 lanes on 32 banks
-          const float x = pick(v0[u], e);
-          const float h = tf32_hi(x);
-          const size_t off = kb + (size_t)(4 * rq + e) * 16;
-          *reinterpret_cast<float*>(hi + off) = h;
-          *reinterpret_cast<float*>(lo + off) = x - h;
-        }
+        const size_t off = (size_t)(jq0 + 2 * u) * 2048 + rbase;
+        const float4 x = v0[u];
+        const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+        *reinterpret_cast<float4*>(hi + off) = h;
+        *reinterpret_cast<float4*>(lo + off) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
       }
       fence_async_smem();
-      mbar_arrive(&bars->full[s]);
+      warp_arrive(&bars->full[s]);
       ++cc;
 #pragma unroll
       for (int u = 0; u < 4; ++u) { v0[u] = v1[u]; v1[u] = v2[u]; }
@@ -597,8 +612,8 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
       a += G.S;
     }
     uoff[n_items] = a;
-    for (int s = 0; s < NS; ++s) { mbar_init(&bars->full[s], kConv); mbar_init(&bars->empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&bars->accfull[b], 1); mbar_init(&bars->accempty[b], 128); }
+    for (int s = 0; s < NS; ++s) { mbar_init(&bars->full[s], kConv / 32); mbar_init(&bars->empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&bars->accfull[b], 1); mbar_init(&bars->accempty[b], 4); }
     mbar_init(&bars->drain, 1);
     bars->abort_flag = 0;
     fence_mbar_init();
@@ -670,7 +685,7 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
         for (int c0 = 0; c0 < F8; ++c0) { acc[(size_t)row * P.ld + c0] = 0.f; cmp[(size_t)row * P.ld + c0] = 0.f; }
       for (long long c = g.c; c < g.c1; c += kRun) {
         const int b = (int)(rc & 1);
-        if (!mbar_wait(&bars->accfull[b], (uint32_t)((rc >> 1) & 1), abort_flag, err)) { ok = false; break; }
+        if (!warp_wait(&bars->accfull[b], (uint32_t)((rc >> 1) & 1), abort_flag, err)) { ok = false; break; }
         tc_after();
         const uint32_t tbase = tmem + lane_base + (uint32_t)(b * 256);
         for (int c0 = 0; c0 < F8; c0 += 16) {
@@ -696,7 +711,7 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
           }
         }
         tc_before();
-        mbar_arrive(&bars->accempty[b]);
+        warp_arrive(&bars->accempty[b]);
         ++rc;
       }
       if (!ok) break;
@@ -708,36 +723,87 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
     }
   } else if (warp >= 8) {
     // ------------------------------------------------------------ converters
-    // Loads (and the weight of the thread's column group) run two chunks
-    // ahead of the shared-memory stores (register ring v0, v1, v2).
+    // Loads (and the weight of the thread's column group) run one chunk
+    // ahead of the shared-memory stores (register pair v0, v1).
     const int cw = (tid - 256) >> 5;
     const int kq = 4 * (cw & 1) + (lane >> 3);     // this thread's 4-wide K group of a chunk
     const int i8_0 = cw >> 1;                      // row groups i8_0 + 4 u, u = 0..3
     const int il = lane & 7;
-    // load cursor
+    // load cursor: the chunk's (o, q) advance incrementally; the weight
+    // prod_{u != k} sw[u][j_u] of this thread's 4-wide column group comes
+    // from digit counters of the outer legs (o) and inner legs (q / 4)
     GramCursor lg;
     lg.item = -1;
     long long lu = blockIdx.x, lcur = 0;
     bool l_live = false;
     int wt_item = -1;
     const double* sw[PEPO_MAXLEG];
-    unsigned dd[PEPO_MAXLEG];
-    long long o_w = -1;     // o of the cached outer weight
-    float w_out = 0.f;
+    int dd[PEPO_MAXLEG];
+    bool weighted = false;
+    long long lo_ = 0;      // o of the current chunk (wide) or of its first column group (narrow)
+    long long lqb = 0;      // chunk index within o (wide)
+    int od[PEPO_MAXLEG];    // digits of this thread's o (outer legs)
+    int id_[PEPO_MAXLEG];   // digits of this thread's q / 4 (inner legs)
+    // add `inc` to the digit counter of legs [lo, hi) (row-major, last fastest)
+    auto odo_add = [&](int* dig, int lo, int hi, long long inc) {
+      long long carry = inc;
+#pragma unroll
+      for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
+        if (uu >= lo && uu < hi && carry) {
+          const long long t = dig[uu] + carry;
+          carry = t / dd[uu];
+          dig[uu] = (int)(t - carry * dd[uu]);
+        }
+      }
+    };
+    auto odo_set = [&](int* dig, int lo, int hi, long long val) {
+#pragma unroll
+      for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
+        if (uu >= lo && uu < hi) {
+          dig[uu] = (int)(val % dd[uu]);
+          val /= dd[uu];
+        } else {
+          dig[uu] = 0;
+        }
+      }
+    };
+    auto odo_w = [&](const int* dig, int lo, int hi) {
+      float w = 1.f;
+#pragma unroll
+      for (int uu = 0; uu < PEPO_MAXLEG; ++uu)
+        if (uu >= lo && uu < hi && sw[uu]) w *= (float)sw[uu][dig[uu]];
+      return w;
+    };
     auto enter_unit = [&]() {
       l_live = lu < U;
       if (!l_live) return;
       gram_unit(lg, lu, uoff, n_items, items, ptrs, ival, splits_max);
+      const GramDims& G = lg.G;
       lcur = lg.c;
       if (lg.item != wt_item) {
         const GramLegItem& it = items[lg.item];
+        weighted = false;
 #pragma unroll
         for (int uu = 0; uu < PEPO_MAXLEG; ++uu) {
-          sw[uu] = (uu < lg.G.nlegs && uu != lg.G.k) ? it.sw[uu] : nullptr;
-          dd[uu] = (unsigned)lg.G.d[uu];
+          sw[uu] = (uu < G.nlegs && uu != G.k) ? it.sw[uu] : nullptr;
+          dd[uu] = G.d[uu];
+          weighted |= sw[uu] != nullptr;
         }
         wt_item = lg.item;
-        o_w = -1;
+      }
+      if (G.wide) {
+        lo_ = lcur / G.qpc;
+        lqb = lcur - lo_ * G.qpc;
+        if (weighted) {
+          odo_set(od, 0, G.k, lo_);
+          odo_set(id_, G.k + 1, G.nlegs, (lqb * kKC + 4 * kq) >> 2);
+        }
+      } else {
+        lo_ = lcur * G.opc;
+        if (weighted) {
+          odo_set(od, 0, G.k, lo_ + (4 * kq) / G.Q);
+          odo_set(id_, G.k + 1, G.nlegs, ((4 * kq) % G.Q) >> 2);   // fixed per thread
+        }
       }
     };
     enter_unit();
@@ -747,61 +813,50 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
       w = 0.f;
       if (!l_live) return;
       const GramDims& G = lg.G;
-      const long long c = lcur;
-      // k group of this thread: legs before the free leg give o, legs after give q
       long long o, q;
       bool kvalid;
       if (G.wide) {
-        o = c / G.qpc;
-        q = (c - o * G.qpc) * kKC + 4 * kq;
+        o = lo_;
+        q = lqb * kKC + 4 * kq;
         kvalid = q < G.Q;
       } else {
-        o = c * G.opc + (4 * kq) / G.Q;
+        o = lo_ + (4 * kq) / G.Q;
         q = (4 * kq) % G.Q;
         kvalid = (4 * kq) / G.Q < G.opc && o < G.O;
       }
-      // weight prod_{u != k} sw[u][j_u]: outer legs from o (cached per o),
-      // inner legs from q / 4 (the Pauli index shares one weight)
       if (kvalid) {
-        if (o != o_w) {
-          float wo = 1.f;
-          unsigned t = (unsigned)o;
-#pragma unroll
-          for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
-            if (uu < G.k) {
-              const unsigned j = t % dd[uu];
-              t /= dd[uu];
-              if (sw[uu]) wo *= (float)sw[uu][j];
-            }
-          }
-          w_out = wo;
-          o_w = o;
-        }
-        float wi = 1.f;
-        unsigned t = (unsigned)(q >> 2);
-#pragma unroll
-        for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
-          if (uu > G.k && uu < G.nlegs) {
-            const unsigned j = t % dd[uu];
-            t /= dd[uu];
-            if (sw[uu]) wi *= (float)sw[uu][j];
-          }
-        }
-        w = w_out * wi;
+        w = weighted ? odo_w(od, 0, G.k) * odo_w(id_, G.k + 1, G.nlegs) : 1.f;
+        const float* base = G.X + (o * G.F) * G.Q + q;
 #pragma unroll
         for (int u4 = 0; u4 < 4; ++u4) {
           const int i = 8 * (i8_0 + 4 * u4) + il;
-          if (i < G.F) v[u4] = __ldg(reinterpret_cast<const float4*>(G.X + (o * G.F + i) * G.Q + q));
+          if (i < G.F) v[u4] = __ldg(reinterpret_cast<const float4*>(base + (long long)i * G.Q));
         }
       }
-      if (++lcur < lg.c1) return;
+      if (++lcur < lg.c1) {
+        if (G.wide) {
+          if (++lqb == G.qpc) {
+            lqb = 0;
+            ++lo_;
+            if (weighted) {
+              odo_add(od, 0, G.k, 1);
+              odo_set(id_, G.k + 1, G.nlegs, kq);
+            }
+          } else if (weighted) {
+            odo_add(id_, G.k + 1, G.nlegs, kKC / 4);
+          }
+        } else {
+          lo_ += G.opc;
+          if (weighted) odo_add(od, 0, G.k, G.opc);
+        }
+        return;
+      }
       lu += gridDim.x;
       enter_unit();
     };
-    float4 v0[4], v1[4], v2[4];
-    float w0, w1, w2;
+    float4 v0[4], v1[4];
+    float w0, w1;
     load_next(v0, w0);
-    load_next(v1, w1);
     // store cursor
     GramCursor g;
     g.item = -1;
@@ -812,9 +867,9 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
       const int F8 = g.G.F8;
       const size_t lbo = (size_t)(2 * F8 / 8) * 128;
       for (long long c = g.c; c < g.c1; ++c, ++cc) {
-        load_next(v2, w2);
+        load_next(v1, w1);
         const int s = (int)(cc % NS);
-        if (!mbar_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
+        if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
         unsigned char* st = Xs + (size_t)s * P.stage_bytes + (size_t)kq * lbo;
 #pragma unroll
         for (int u4 = 0; u4 < 4; ++u4) {
@@ -829,11 +884,10 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
           }
         }
         fence_async_smem();
-        mbar_arrive(&bars->full[s]);
+        warp_arrive(&bars->full[s]);
 #pragma unroll
-        for (int u4 = 0; u4 < 4; ++u4) { v0[u4] = v1[u4]; v1[u4] = v2[u4]; }
+        for (int u4 = 0; u4 < 4; ++u4) v0[u4] = v1[u4];
         w0 = w1;
-        w1 = w2;
       }
     }
   }
@@ -960,8 +1014,8 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
       acc += D.tiles;
     }
     toff[n_items] = acc;
-    for (int s = 0; s < NS; ++s) { mbar_init(&bars->full[s], kConv); mbar_init(&bars->empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&bars->accfull[b], 1); mbar_init(&bars->accempty[b], 128); }
+    for (int s = 0; s < NS; ++s) { mbar_init(&bars->full[s], kConv / 32); mbar_init(&bars->empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&bars->accfull[b], 1); mbar_init(&bars->accempty[b], 4); }
     mbar_init(&bars->drain, 1);
     bars->abort_flag = 0;
     fence_mbar_init();
@@ -1026,7 +1080,7 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
     long long tc = 0;
     while (live) {
       const int b = (int)(tc & 1);
-      if (!mbar_wait(&bars->accfull[b], (uint32_t)((tc >> 1) & 1), abort_flag, err)) break;
+      if (!warp_wait(&bars->accfull[b], (uint32_t)((tc >> 1) & 1), abort_flag, err)) break;
       tc_after();
       const RecDims& D = c.D;
       const long long rb = c.tile / D.nnb;
@@ -1060,7 +1114,7 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
         }
       }
       tc_before();
-      mbar_arrive(&bars->accempty[b]);
+      warp_arrive(&bars->accempty[b]);
       ++tc;
       if (c.left == 1) break;
       rec_next(c, toff, n_items, items, ptrs, ival);
@@ -1091,7 +1145,7 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
           if (r < D.R && k < D.n) v[u] = __ldg(reinterpret_cast<const float4*>(D.in + r * D.n + k));
         }
         const int s = (int)(cc % NS);
-        if (!mbar_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
+        if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
         unsigned char* hi = smem + (size_t)s * P.stage_bytes;
         unsigned char* lo = hi + P.a_bytes;
         unsigned char* bs = hi + 2 * P.a_bytes;
@@ -1118,7 +1172,7 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
           *reinterpret_cast<float*>(bs + kb + (size_t)(c2 >> 3) * 128 + (size_t)(c2 & 7) * 16) = x - h;
         }
         fence_async_smem();
-        mbar_arrive(&bars->full[s]);
+        warp_arrive(&bars->full[s]);
       }
       if (!ok) break;
       if (c.left == 1) break;
