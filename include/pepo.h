@@ -109,7 +109,11 @@ typedef struct {
   int norm_exploded;       /* exp(log_norm) >= 2 */
   int flags;               /* bit 0: rank-deficient message met (env projector
                               skipped), bit 1: non-finite value seen,
-                              bit 2: a Jacobi SVD hit its sweep cap */
+                              bit 2: a Jacobi SVD hit its sweep cap,
+                              bit 3: gate rank above the bound (init only),
+                              bit 4: a mixed-precision bond-core SVD fell
+                              back to FP64 (kept set not resolved in FP32),
+                              bit 5: ... because its FP32 pass hit the cap */
   int steps;               /* Trotter steps taken so far */
 } pepo_diag;
 

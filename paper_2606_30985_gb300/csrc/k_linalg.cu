@@ -578,12 +578,20 @@ __device__ int jacobi_svd(R* A, int m, int n, R* V, int max_sweeps, int* capped,
           R x = Ap[i], y = Aq[i];
           al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
         }
-        al = (R)warp_sum((double)al); be = (R)warp_sum((double)be); ga = (R)warp_sum((double)ga);
-        if (ga != R(0) && al > negligible && be > negligible && fabs((double)ga) > tol * sqrt((double)al * be)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        // rotation parameters in the working precision (FP64 division and
+        // square root are slow on this part; FP32 columns need no more)
+        if (ga != R(0) && al > (R)negligible && be > (R)negligible &&
+            fabs(ga) > (R)tol * sqrt(al * be)) {
           rotated = 1;
-          const double zeta = ((double)be - al) / (2.0 * ga);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const R c = (R)(1.0 / sqrt(1.0 + t * t)), s = (R)((1.0 / sqrt(1.0 + t * t)) * t);
+          const R zeta = (be - al) / (R(2) * ga);
+          const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+          const R c = R(1) / sqrt(R(1) + t * t), s = c * t;
           for (int i = lane; i < m; i += 32) {
             R x = Ap[i], y = Aq[i];
             Ap[i] = c * x - s * y;
@@ -688,8 +696,10 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
     }
     __syncthreads();
     const int nk = N < it.chimax ? N : it.chimax;
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
       sh_resolved = (!sh_capped32 && sv[order[0]] > 0.0 && sv[order[nk - 1]] >= 1e-5 * sv[order[0]]) ? 1 : 0;
+      if (!sh_resolved) atomicOr(flags, sh_capped32 ? 48 : 16);   // bit 4: FP64 fallback, bit 5: FP32 sweep cap
+    }
     __syncthreads();
     if (sh_resolved) {
       // exact ||T||_F^2 (FP64) for the discarded weight

@@ -451,11 +451,14 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
     long long cc = 0;
     int item_n = 0, kc = 0;
     bool need_b = true;
-    while (live) {
+    // one chunk: issue the loads two chunks ahead into vl, convert and store
+    // vs (the ring is rotated by unrolling, never by copying registers, so
+    // no load is waited on before its turn); returns false at the end
+    auto step = [&](float4 (&vl)[4], float4 (&vs)[4]) -> bool {
       const LegDims& L = c.L;
-      load_next(v2);
+      load_next(vl);
       if (need_b) {
-        if (item_n > 0 && !warp_wait(&bars->bfree, (uint32_t)((item_n - 1) & 1), abort_flag, err)) break;
+        if (item_n > 0 && !warp_wait(&bars->bfree, (uint32_t)((item_n - 1) & 1), abort_flag, err)) return false;
         // [Ah; Al]: rows n < N16 hold hi(A[n, :]), rows N16 + n hold lo(A[n, :])
         const uint32_t lbo_b = (uint32_t)(2 * L.N16 / 8) * 128;
         for (int e = ct; e < L.N16 * L.K8; e += kConv) {
@@ -474,14 +477,14 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
         need_b = false;
       }
       const int s = (int)(cc % NS);
-      if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) break;
+      if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) return false;
       unsigned char* hi = As + (size_t)s * P.stage_bytes;
       unsigned char* lo = hi + P.stage_bytes / 2;
       const size_t rbase = (size_t)(r >> 3) * 128 + (size_t)(r & 7) * 16;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const size_t off = (size_t)(jq0 + 2 * u) * 2048 + rbase;
-        const float4 x = v0[u];
+        const float4 x = vs[u];
         const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
         *reinterpret_cast<float4*>(hi + off) = h;
         *reinterpret_cast<float4*>(lo + off) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
@@ -489,12 +492,16 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
       fence_async_smem();
       warp_arrive(&bars->full[s]);
       ++cc;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) { v0[u] = v1[u]; v1[u] = v2[u]; }
-      if (++kc < (L.K8 + kKC - 1) / kKC) continue;
+      if (++kc < (L.K8 + kKC - 1) / kKC) return true;
       kc = 0;
-      if (c.left == 1) break;
+      if (c.left == 1) return false;
       if (cursor_next(c, toff, n_items, items, ptrs, ival)) { ++item_n; need_b = true; }
+      return true;
+    };
+    while (live) {
+      if (!step(v2, v0)) break;
+      if (!step(v0, v1)) break;
+      if (!step(v1, v2)) break;
     }
   }
   tc_before();
@@ -860,35 +867,43 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
     // store cursor
     GramCursor g;
     g.item = -1;
-    long long cc = 0;
-    bool ok = true;
-    for (long long u = blockIdx.x; u < U && ok; u += gridDim.x) {
-      gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max);
+    long long cc = 0, u = blockIdx.x, c = 0;
+    bool live = u < U;
+    if (live) { gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max); c = g.c; }
+    // one chunk: loads for the next chunk into vl / wl, store vs / ws (ring
+    // rotated by unrolling, not by register copies)
+    auto step = [&](float4 (&vl)[4], float& wl, float4 (&vs)[4], float ws) -> bool {
+      load_next(vl, wl);
       const int F8 = g.G.F8;
       const size_t lbo = (size_t)(2 * F8 / 8) * 128;
-      for (long long c = g.c; c < g.c1; ++c, ++cc) {
-        load_next(v1, w1);
-        const int s = (int)(cc % NS);
-        if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
-        unsigned char* st = Xs + (size_t)s * P.stage_bytes + (size_t)kq * lbo;
+      const int s = (int)(cc % NS);
+      if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) return false;
+      unsigned char* st = Xs + (size_t)s * P.stage_bytes + (size_t)kq * lbo;
 #pragma unroll
-        for (int u4 = 0; u4 < 4; ++u4) {
-          const int i = 8 * (i8_0 + 4 * u4) + il;
-          if (i < F8) {
-            const float4 x = make_float4(v0[u4].x * w0, v0[u4].y * w0, v0[u4].z * w0, v0[u4].w * w0);
-            const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-            const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-            const int i2 = i + F8;
-            *reinterpret_cast<float4*>(st + (size_t)(i >> 3) * 128 + (size_t)(i & 7) * 16) = h;
-            *reinterpret_cast<float4*>(st + (size_t)(i2 >> 3) * 128 + (size_t)(i2 & 7) * 16) = l;
-          }
+      for (int u4 = 0; u4 < 4; ++u4) {
+        const int i = 8 * (i8_0 + 4 * u4) + il;
+        if (i < F8) {
+          const float4 x = make_float4(vs[u4].x * ws, vs[u4].y * ws, vs[u4].z * ws, vs[u4].w * ws);
+          const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+          const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+          const int i2 = i + F8;
+          *reinterpret_cast<float4*>(st + (size_t)(i >> 3) * 128 + (size_t)(i & 7) * 16) = h;
+          *reinterpret_cast<float4*>(st + (size_t)(i2 >> 3) * 128 + (size_t)(i2 & 7) * 16) = l;
         }
-        fence_async_smem();
-        warp_arrive(&bars->full[s]);
-#pragma unroll
-        for (int u4 = 0; u4 < 4; ++u4) v0[u4] = v1[u4];
-        w0 = w1;
       }
+      fence_async_smem();
+      warp_arrive(&bars->full[s]);
+      ++cc;
+      if (++c < g.c1) return true;
+      u += gridDim.x;
+      if (u >= U) return false;
+      gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max);
+      c = g.c;
+      return true;
+    };
+    while (live) {
+      if (!step(v1, w1, v0, w0)) break;
+      if (!step(v0, w0, v1, w1)) break;
     }
   }
   tc_before();
