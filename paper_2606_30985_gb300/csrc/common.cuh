@@ -102,6 +102,7 @@ struct ReconItem {
   const double* W;         // n x n', row-major, leading dimension ldw
   int ldw;
   double* scale_sq;        // optional: sum of squares of the output (may be null)
+  float* Wp;               // tensor-core path: W packed into swizzled B blocks (recon_packed_floats(nmax))
 };
 
 // Vector contraction of one leg of an FP64 tensor: out[o, q] = sum_j in[o, j, q] v[j].

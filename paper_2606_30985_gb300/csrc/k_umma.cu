@@ -33,11 +33,14 @@
 // in *err, every role leaves its loop, the MMA issuer drains its outstanding
 // MMAs (bounded), tensor memory is freed and the kernel returns.
 //
-// Shared-memory operand layout (K-major, no swizzle): a core matrix is 8 rows
-// x 16 bytes (4 TF32 along K) stored contiguously, row r at byte 16 r.  Core
-// matrices adjacent along M/N are SBO = 128 bytes apart, adjacent along K are
-// LBO bytes apart (LBO = 128 x number of M/N core rows), so element (n, k) of
-// an operand sits at (k / 4) LBO + (n / 8) 128 + (n % 8) 16 + (k % 4) 4.
+// Shared-memory operand layout: K-major with the 128-byte swizzle.  A row of
+// an operand holds the 32 FP32 (TF32) values of one K chunk in 128 bytes;
+// 8 rows form a 1024-byte atom (atoms SBO = 1024 bytes apart along M/N); the
+// 16-byte piece c of row r sits at piece position c ^ (r % 8).  One MMA
+// covers K = 8 (32 bytes): its descriptor starts 32 bytes further per K step
+// inside the atom (the hardware applies the XOR to the absolute address, so
+// every tile is 1024-byte aligned).  Element (n, k) of a tile sits at
+// (n / 8) 1024 + (n % 8) 128 + (((k / 4) ^ (n % 8)) 16) + (k % 4) 4.
 #include "kernels.h"
 
 namespace pepo {
@@ -104,6 +107,18 @@ __device__ __forceinline__ void warp_arrive(uint64_t* b) {
   if ((threadIdx.x & 31) == 0) mbar_arrive(b);
 }
 
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy (16-byte aligned, size a multiple of 16) that
+// completes `bytes` of the barrier's transaction count
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(b))
+               : "memory");
+}
+
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -119,13 +134,20 @@ __device__ __forceinline__ void tmem_free(uint32_t taddr) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
 }
 
-// shared-memory matrix descriptor: K-major, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, atoms 1024
+// bytes apart (the leading offset is unused for this layout: one atom spans
+// the MMA's K)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;   // descriptor version of the sm_100 family
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused), 16 bytes
+  d |= (uint64_t)(1024u >> 4) << 32;        // stride byte offset: 8-row atoms
+  d |= (uint64_t)1 << 46;                   // descriptor version of the sm_100 family
+  d |= (uint64_t)2 << 61;                   // layout: 128-byte swizzle
   return d;
+}
+// byte offset of the 16-byte piece `piece` (K / 4) of row `row` in a tile
+__host__ __device__ __forceinline__ uint32_t swz(int row, int piece) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((piece ^ (row & 7)) << 4));
 }
 // instruction descriptor: kind::tf32, FP32 accumulator, A and B TF32 K-major
 __device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {
@@ -211,8 +233,9 @@ __host__ __device__ inline LegSmem leg_smem(int chimax) {
   LegSmem p;
   p.k8max = round_up(chimax, 8);
   p.n16max = round_up(chimax, 16);
-  p.b_bytes = (size_t)(p.k8max / 4) * (2 * p.n16max / 8) * 128;   // [Ah; Al] of the small matrix
-  p.stage_bytes = 2 * (size_t)(kKC / 4) * (kM / 8) * 128;          // hi + lo tile, 2 x 16 KB
+  // [Ah; Al] of the small matrix: one (2 N16 rows x 128 B) block per K chunk
+  p.b_bytes = (size_t)((p.k8max + kKC - 1) / kKC) * (2 * p.n16max) * 128;
+  p.stage_bytes = 2 * (size_t)kM * 128;                             // hi + lo tile, 2 x 16 KB
   const size_t budget = 227 * 1024 - 1024 - 8 * kMaxItems - 512;
   p.stages = (int)((budget - p.b_bytes) / p.stage_bytes);
   if (p.stages > 4) p.stages = 4;
@@ -314,7 +337,7 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
         tc_after();
         const uint32_t d_tmem = tmem + (uint32_t)(b * 256);
         const int N16 = c.L.N16, K8 = c.L.K8;
-        const uint32_t lbo_b = (uint32_t)(2 * N16 / 8) * 128;
+        const uint32_t bblk = (uint32_t)(2 * N16) * 128;   // B block per K chunk
         const uint32_t id_wide = idesc_tf32(kM, 2 * N16), id_half = idesc_tf32(kM, N16);
         const int nkc = (K8 + kKC - 1) / kKC;
         for (int kc = 0; kc < nkc && ok; ++kc, ++cc) {
@@ -326,11 +349,9 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
           const uint32_t b0 = su32(Bs);
           const int ksteps = min(kKC, K8 - kc * kKC) / 8;
           for (int st = 0; st < ksteps; ++st) {
-            const uint32_t koff_a = (uint32_t)(st * 2) * 2048u;
-            const uint32_t koff_b = (uint32_t)(kc * 8 + st * 2) * lbo_b;
-            const uint64_t dah = sdesc(a_hi + koff_a, 2048u, 128u);
-            const uint64_t dal = sdesc(a_lo + koff_a, 2048u, 128u);
-            const uint64_t db = sdesc(b0 + koff_b, lbo_b, 128u);
+            const uint64_t dah = sdesc(a_hi + (uint32_t)st * 32u);
+            const uint64_t dal = sdesc(a_lo + (uint32_t)st * 32u);
+            const uint64_t db = sdesc(b0 + (uint32_t)kc * bblk + (uint32_t)st * 32u);
             mma_tf32(d_tmem, dah, db, id_wide, (kc > 0 || st > 0) ? 1u : 0u);
             mma_tf32(d_tmem, dal, db, id_half, 1u);
           }
@@ -459,18 +480,20 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
       load_next(vl);
       if (need_b) {
         if (item_n > 0 && !warp_wait(&bars->bfree, (uint32_t)((item_n - 1) & 1), abort_flag, err)) return false;
-        // [Ah; Al]: rows n < N16 hold hi(A[n, :]), rows N16 + n hold lo(A[n, :])
-        const uint32_t lbo_b = (uint32_t)(2 * L.N16 / 8) * 128;
-        for (int e = ct; e < L.N16 * L.K8; e += kConv) {
-          const int n = e / L.K8, j = e - n * L.K8;
+        // [Ah; Al]: rows n < N16 hold hi(A[n, :]), rows N16 + n hold lo(A[n, :]);
+        // one block of 2 N16 rows per 32-wide K chunk
+        const size_t bblk = (size_t)(2 * L.N16) * 128;
+        const int K32 = (L.K8 + kKC - 1) / kKC * kKC;
+        for (int e = ct; e < L.N16 * K32; e += kConv) {
+          const int n = e / K32, j = e - n * K32;
           float x = 0.f;
           if (n < L.Jout && j < L.J) x = (float)L.A[(long long)n * L.lda + j];
           const float h = tf32_hi(x);
           const float l = x - h;
-          const size_t kb = (size_t)(j >> 2) * lbo_b + (size_t)(j & 3) * 4;
-          *reinterpret_cast<float*>(Bs + kb + (size_t)(n >> 3) * 128 + (size_t)(n & 7) * 16) = h;
-          const int n2 = n + L.N16;
-          *reinterpret_cast<float*>(Bs + kb + (size_t)(n2 >> 3) * 128 + (size_t)(n2 & 7) * 16) = l;
+          unsigned char* blk = Bs + (size_t)(j / kKC) * bblk + (size_t)(j & 3) * 4;
+          const int piece = (j % kKC) >> 2;
+          *reinterpret_cast<float*>(blk + swz(n, piece)) = h;
+          *reinterpret_cast<float*>(blk + swz(n + L.N16, piece)) = l;
         }
         fence_async_smem();
         warp_arrive(&bars->bfull);
@@ -480,10 +503,9 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
       if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) return false;
       unsigned char* hi = As + (size_t)s * P.stage_bytes;
       unsigned char* lo = hi + P.stage_bytes / 2;
-      const size_t rbase = (size_t)(r >> 3) * 128 + (size_t)(r & 7) * 16;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const size_t off = (size_t)(jq0 + 2 * u) * 2048 + rbase;
+        const size_t off = swz(r, jq0 + 2 * u);
         const float4 x = vs[u];
         const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
         *reinterpret_cast<float4*>(hi + off) = h;
@@ -550,10 +572,11 @@ struct GramSmem {
 __host__ __device__ inline GramSmem gram_smem(int chimax) {
   GramSmem p;
   p.f8max = round_up(chimax, 8);
-  p.stage_bytes = (size_t)(kKC / 4) * (2 * p.f8max / 8) * 128;   // [Xh; Xl]
+  // [Xh; Xl] rows x 128 B; at least the 128 rows the A operand (M = 128) reads
+  p.stage_bytes = (size_t)(2 * p.f8max > kM ? 2 * p.f8max : kM) * 128;
   p.ld = p.f8max + 1;                                               // odd row stride (words)
   const size_t acc_bytes = 2 * (size_t)p.f8max * p.ld * 4;          // sum + compensation
-  const size_t pad = 2048;                                          // A-operand rows past 2 F8
+  const size_t pad = 0;
   const size_t budget = 227 * 1024 - 1024 - 8 * (kMaxItems + 1) - 512 - 1024;
   p.stages = (int)((budget - acc_bytes - pad) / p.stage_bytes);
   if (p.stages > 4) p.stages = 4;
@@ -646,7 +669,6 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
       for (long long u = blockIdx.x; u < U && ok; u += gridDim.x) {
         gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max);
         const int F8 = g.G.F8;
-        const uint32_t lbo = (uint32_t)(2 * F8 / 8) * 128;
         const uint32_t id = idesc_tf32(kM, 2 * F8);
         for (long long c = g.c; c < g.c1 && ok;) {
           const int b = (int)(rc & 1);
@@ -661,7 +683,7 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
             const uint32_t x0 = su32(Xs + (size_t)s * P.stage_bytes);
 #pragma unroll
             for (int st = 0; st < kKC / 8; ++st) {
-              const uint64_t d = sdesc(x0 + (uint32_t)(2 * st) * lbo, lbo, 128u);
+              const uint64_t d = sdesc(x0 + (uint32_t)st * 32u);
               mma_tf32(d_tmem, d, d, id, (cr > c || st > 0) ? 1u : 0u);
             }
             mma_commit(&bars->empty[s]);
@@ -875,10 +897,9 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
     auto step = [&](float4 (&vl)[4], float& wl, float4 (&vs)[4], float ws) -> bool {
       load_next(vl, wl);
       const int F8 = g.G.F8;
-      const size_t lbo = (size_t)(2 * F8 / 8) * 128;
       const int s = (int)(cc % NS);
       if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) return false;
-      unsigned char* st = Xs + (size_t)s * P.stage_bytes + (size_t)kq * lbo;
+      unsigned char* st = Xs + (size_t)s * P.stage_bytes;
 #pragma unroll
       for (int u4 = 0; u4 < 4; ++u4) {
         const int i = 8 * (i8_0 + 4 * u4) + il;
@@ -886,9 +907,8 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
           const float4 x = make_float4(vs[u4].x * ws, vs[u4].y * ws, vs[u4].z * ws, vs[u4].w * ws);
           const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
           const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-          const int i2 = i + F8;
-          *reinterpret_cast<float4*>(st + (size_t)(i >> 3) * 128 + (size_t)(i & 7) * 16) = h;
-          *reinterpret_cast<float4*>(st + (size_t)(i2 >> 3) * 128 + (size_t)(i2 & 7) * 16) = l;
+          *reinterpret_cast<float4*>(st + swz(i, kq)) = h;
+          *reinterpret_cast<float4*>(st + swz(i + F8, kq)) = l;
         }
       }
       fence_async_smem();
@@ -919,8 +939,9 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
 // site tensor (cut leg last), k = (cut, Pauli), c = (new cut, Pauli) written
 // into the next update's layout.  Tiles are (128 rows, one N block of at most
 // 128 columns); both operands stream in 32-wide K chunks: A through the
-// converters (row-contiguous, 16-byte loads), B = [hi(W^T); lo(W^T)] for the
-// tile's N block converted from the FP64 W (L2-resident) by the same warps.
+// converters (row-contiguous, 16-byte loads), B = [hi(W^T); lo(W^T)] of the
+// tile's N block as one bulk copy of a block pre-packed by k_pack_w (the
+// swizzled shared-memory image, so the copy is linear).
 struct RecDims {
   long long R, tiles, nrb;
   int n, np, K8, nnb, NB, cut, nl;
@@ -930,6 +951,8 @@ struct RecDims {
   float* out;
   const double* W;
   int ldw;
+  const float* Wp;
+  int nkc;
 };
 
 __device__ inline void rec_dims(const ReconItem& it, void* const* ptrs, const int* ival, RecDims& D) {
@@ -960,6 +983,8 @@ __device__ inline void rec_dims(const ReconItem& it, void* const* ptrs, const in
   D.out = static_cast<float*>(ptrs[it.out_ref]);
   D.W = it.W;
   D.ldw = it.ldw;
+  D.Wp = it.Wp;
+  D.nkc = (D.K8 + kKC - 1) / kKC;
 }
 
 struct RecSmem {
@@ -968,8 +993,8 @@ struct RecSmem {
 };
 __host__ __device__ inline RecSmem rec_smem() {
   RecSmem p;
-  p.a_bytes = (size_t)(kKC / 4) * (kM / 8) * 128;                 // 16 KB per hi / lo
-  p.stage_bytes = 2 * p.a_bytes + (size_t)(kKC / 4) * (256 / 8) * 128;   // + [Bh; Bl], NB <= 128
+  p.a_bytes = (size_t)kM * 128;                                   // 16 KB per hi / lo
+  p.stage_bytes = 2 * p.a_bytes + (size_t)256 * 128;               // + [Bh; Bl], 2 NB <= 256 rows
   p.stages = 3;
   p.bar_off = p.stages * p.stage_bytes;
   p.total = p.bar_off + 512 + 8 * (size_t)(kMaxItems + 1) + 1024;
@@ -1029,7 +1054,7 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
       acc += D.tiles;
     }
     toff[n_items] = acc;
-    for (int s = 0; s < NS; ++s) { mbar_init(&bars->full[s], kConv / 32); mbar_init(&bars->empty[s], 1); }
+    for (int s = 0; s < NS; ++s) { mbar_init(&bars->full[s], kConv / 32 + 1); mbar_init(&bars->empty[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&bars->accfull[b], 1); mbar_init(&bars->accempty[b], 4); }
     mbar_init(&bars->drain, 1);
     bars->abort_flag = 0;
@@ -1056,7 +1081,6 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
         tc_after();
         const uint32_t d_tmem = tmem + (uint32_t)(b * 256);
         const int NB = c.D.NB, K8 = c.D.K8;
-        const uint32_t lbo_b = (uint32_t)(2 * NB / 8) * 128;
         const uint32_t id_wide = idesc_tf32(kM, 2 * NB), id_half = idesc_tf32(kM, NB);
         const int nkc = (K8 + kKC - 1) / kKC;
         for (int kc = 0; kc < nkc; ++kc, ++cc) {
@@ -1068,9 +1092,9 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
           const uint32_t bb = a_hi + (uint32_t)(2 * P.a_bytes);
           const int ksteps = min(kKC, K8 - kc * kKC) / 8;
           for (int st = 0; st < ksteps; ++st) {
-            const uint64_t dah = sdesc(a_hi + (uint32_t)(st * 2) * 2048u, 2048u, 128u);
-            const uint64_t dal = sdesc(a_lo + (uint32_t)(st * 2) * 2048u, 2048u, 128u);
-            const uint64_t db = sdesc(bb + (uint32_t)(st * 2) * lbo_b, lbo_b, 128u);
+            const uint64_t dah = sdesc(a_hi + (uint32_t)st * 32u);
+            const uint64_t dal = sdesc(a_lo + (uint32_t)st * 32u);
+            const uint64_t db = sdesc(bb + (uint32_t)st * 32u);
             mma_tf32(d_tmem, dah, db, id_wide, (kc > 0 || st > 0) ? 1u : 0u);
             mma_tf32(d_tmem, dal, db, id_half, 1u);
           }
@@ -1136,62 +1160,74 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
     }
   } else if (warp >= 8) {
     // ------------------------------------------------------------ converters
-    const int ct = tid - 256, cw = ct >> 5;
+    const int cw = (tid - 256) >> 5;
     const int kq = 4 * (cw & 1) + (lane >> 3);     // 4-wide K group of A handled by this thread
     const int i8_0 = cw >> 1;                      // A row groups i8_0 + 4 u
     const int il = lane & 7;
+    const bool issuer = (tid == 256);               // issues the bulk copy of the B block
     RecCursor c;
     bool live = rec_start(c, toff, n_items, t0, t1, items, ptrs, ival);
     long long cc = 0;
-    while (live) {
+    int kc = 0;
+    // loads of the next chunk run one chunk ahead (ring rotated by unrolling)
+    RecCursor lcur = c;
+    int lkc = 0;
+    bool l_live = live;
+    auto load_next = [&](float4 (&v)[4]) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!l_live) return;
+      const RecDims& D = lcur.D;
+      const long long rb = lcur.tile / D.nnb;
+      const int k = lkc * kKC + 4 * kq;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long r = rb * kM + 8 * (i8_0 + 4 * u) + il;
+        if (r < D.R && k < D.n) v[u] = __ldg(reinterpret_cast<const float4*>(D.in + r * D.n + k));
+      }
+      if (++lkc < D.nkc) return;
+      lkc = 0;
+      if (lcur.left == 1) { l_live = false; return; }
+      rec_next(lcur, toff, n_items, items, ptrs, ival);
+    };
+    auto step = [&](float4 (&vl)[4], float4 (&vs)[4]) -> bool {
+      load_next(vl);
       const RecDims& D = c.D;
       const long long rb = c.tile / D.nnb;
       const int nb = (int)(c.tile - rb * D.nnb);
-      const int nkc = (D.K8 + kKC - 1) / kKC;
-      const uint32_t lbo_b = (uint32_t)(2 * D.NB / 8) * 128;
-      bool ok = true;
-      for (int kc = 0; kc < nkc; ++kc, ++cc) {
-        float4 v[4];
-        const int k = kc * kKC + 4 * kq;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const long long r = rb * kM + 8 * (i8_0 + 4 * u) + il;
-          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (r < D.R && k < D.n) v[u] = __ldg(reinterpret_cast<const float4*>(D.in + r * D.n + k));
-        }
-        const int s = (int)(cc % NS);
-        if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
-        unsigned char* hi = smem + (size_t)s * P.stage_bytes;
-        unsigned char* lo = hi + P.a_bytes;
-        unsigned char* bs = hi + 2 * P.a_bytes;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = 8 * (i8_0 + 4 * u) + il;
-          const float4 x = v[u];
-          const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-          const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-          const size_t off = (size_t)kq * 2048 + (size_t)(i >> 3) * 128 + (size_t)(i & 7) * 16;
-          *reinterpret_cast<float4*>(hi + off) = h;
-          *reinterpret_cast<float4*>(lo + off) = l;
-        }
-        // B chunk: rows c < NB hold hi(W[k, nb NB + c]), rows NB + c the lo part
-        for (int e = ct; e < D.NB * kKC; e += kConv) {
-          const int kk = e / D.NB, cl = e - kk * D.NB;
-          const int kg = kc * kKC + kk, cg = nb * D.NB + cl;
-          float x = 0.f;
-          if (kg < D.n && cg < D.np) x = (float)D.W[(long long)kg * D.ldw + cg];
-          const float h = tf32_hi(x);
-          const size_t kb = (size_t)(kk >> 2) * lbo_b + (size_t)(kk & 3) * 4;
-          *reinterpret_cast<float*>(bs + kb + (size_t)(cl >> 3) * 128 + (size_t)(cl & 7) * 16) = h;
-          const int c2 = cl + D.NB;
-          *reinterpret_cast<float*>(bs + kb + (size_t)(c2 >> 3) * 128 + (size_t)(c2 & 7) * 16) = x - h;
-        }
-        fence_async_smem();
-        warp_arrive(&bars->full[s]);
+      const int s = (int)(cc % NS);
+      if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) return false;
+      unsigned char* hi = smem + (size_t)s * P.stage_bytes;
+      unsigned char* lo = hi + P.a_bytes;
+      unsigned char* bs = hi + 2 * P.a_bytes;
+      if (issuer) {
+        const uint32_t bytes = (uint32_t)(2 * D.NB) * 128u;
+        mbar_arrive_tx(&bars->full[s], bytes);
+        bulk_g2s(bs, D.Wp + ((size_t)nb * D.nkc + kc) * (size_t)(2 * D.NB) * 32, bytes, &bars->full[s]);
       }
-      if (!ok) break;
-      if (c.left == 1) break;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = 8 * (i8_0 + 4 * u) + il;
+        const float4 x = vs[u];
+        const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+        const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        *reinterpret_cast<float4*>(hi + swz(i, kq)) = h;
+        *reinterpret_cast<float4*>(lo + swz(i, kq)) = l;
+      }
+      fence_async_smem();
+      warp_arrive(&bars->full[s]);
+      ++cc;
+      if (++kc < D.nkc) return true;
+      kc = 0;
+      if (c.left == 1) return false;
       rec_next(c, toff, n_items, items, ptrs, ival);
+      return true;
+    };
+    float4 v0[4], v1[4];
+    load_next(v0);
+    while (live) {
+      if (!step(v1, v0)) break;
+      if (!step(v0, v1)) break;
     }
   }
   tc_before();
@@ -1210,6 +1246,32 @@ int sm_count() {
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
   }
   return n;
+}
+
+// Pack W (FP64, n x np) into the swizzled B blocks of k_recon_umma: for
+// N block nb and K chunk kc a (2 NB rows x 128 B) image with rows c < NB
+// = hi(W[k, nb NB + c]) and rows NB + c = the lo part, k in the chunk.
+__global__ void k_pack_w(const ReconItem* __restrict__ items, void* const* ptrs, const int* __restrict__ ival) {
+  const ReconItem it = items[blockIdx.y];
+  RecDims D;
+  rec_dims(it, ptrs, ival, D);
+  const long long per_blk = (long long)(2 * D.NB) * 32;
+  const long long total = (long long)D.nnb * D.nkc * per_blk;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long blk = e / per_blk;
+    const int w = (int)(e - blk * per_blk);
+    const int nb = (int)(blk / D.nkc), kc = (int)(blk - (long long)nb * D.nkc);
+    const int row = w / 32, kk = w % 32;          // row of the block image, K within the chunk
+    const int cl = row < D.NB ? row : row - D.NB;
+    const int kg = kc * kKC + kk, cg = nb * D.NB + cl;
+    float x = 0.f;
+    if (kg < D.n && cg < D.np) x = (float)D.W[(long long)kg * D.ldw + cg];
+    const float h = tf32_hi(x);
+    const float v = row < D.NB ? h : x - h;
+    float* img = const_cast<float*>(D.Wp) + blk * per_blk;
+    img[(swz(row, kk >> 2) >> 2) + (kk & 3)] = v;
+  }
 }
 
 }  // namespace um
@@ -1233,12 +1295,27 @@ cudaError_t launch_leg_umma(const LegItem* items, int n_items, int chimax, void*
   return cudaSuccess;
 }
 
+size_t recon_packed_floats(int nmax) {
+  // the N blocking depends on the live n' <= nmax: take the largest layout
+  size_t blocks_n = 0;
+  for (int np = 1; np <= nmax; ++np) {
+    const int nnb = (np + 127) / 128;
+    const int NB = um::round_up((np + nnb - 1) / nnb, 8);
+    blocks_n = std::max(blocks_n, (size_t)nnb * NB);
+  }
+  const int nkc = (um::round_up(nmax, 8) + um::kKC - 1) / um::kKC;
+  return blocks_n * nkc * 2 * 32;
+}
+
 cudaError_t launch_recon_umma(const ReconItem* items, int n_items, int chimax, void* const* ptrs,
                               const int* ival, int* err, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   if (!umma_supported(chimax)) return cudaErrorInvalidValue;
   const um::RecSmem P = um::rec_smem();
-  cudaError_t e = cudaFuncSetAttribute(um::k_recon_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.total);
+  um::k_pack_w<<<dim3(64, n_items), 256, 0, s>>>(items, ptrs, ival);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(um::k_recon_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.total);
   if (e != cudaSuccess) return e;
   for (int i0 = 0; i0 < n_items; i0 += um::kMaxItems) {
     const int n = std::min(um::kMaxItems, n_items - i0);

@@ -44,6 +44,8 @@ bool umma_supported(int chimax);
 // err: device int; bit 0 is set when a pipeline wait of the kernel expired
 cudaError_t launch_leg_umma(const LegItem* items, int n_items, int chimax, void* const* ptrs, const int* ival,
                             int* err, cudaStream_t s);
+// floats of the packed W workspace of one reconstruct item for n, n' <= nmax
+size_t recon_packed_floats(int nmax);
 // psi_new = psi W into the next layout (Q-less reconstruct), W from the bond core
 cudaError_t launch_recon_umma(const ReconItem* items, int n_items, int chimax, void* const* ptrs,
                               const int* ival, int* err, cudaStream_t s);

@@ -452,7 +452,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
   }
 
   // ---- per-site factor workspaces (live from the factorisation to the reconstruct)
-  struct SiteWS { double* C; double* T; int* perm; double* W; int branch_idx, kfac_idx, rankT_idx; };
+  struct SiteWS { double* C; double* T; int* perm; double* W; float* Wp; int branch_idx, kfac_idx, rankT_idx; };
   std::vector<SiteWS> sws(I.N);
   for (int v = 0; v < I.N; ++v) {
     SiteWS& q = sws[v];
@@ -460,6 +460,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
     q.T = cv.take<double>((size_t)4 * nmax * rmax);
     q.perm = cv.take<int>(rmax);
     q.W = cv.take<double>((size_t)nmax * nmax);
+    q.Wp = (ts == 4 && umma_supported(chimax)) ? cv.take<float>(recon_packed_floats(nmax)) : nullptr;
     q.branch_idx = P.new_ival(0);
     q.kfac_idx = P.new_ival(0);
     q.rankT_idx = P.new_ival(0);
@@ -605,6 +606,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
             rc.out_perm[kk] = pos_in;
           }
           rc.W = sws[v].W;
+          rc.Wp = sws[v].Wp;
           rc.ldw = nmax;
           rc.scale_sq = nullptr;
           recon.push_back(rc);
