@@ -671,7 +671,8 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
     // the kept set: column j of Tc becomes T v32_j in FP64 and its norm the
     // singular value (second-order accurate in the FP32 vector error).  Valid
     // when every kept FP32 singular value stands well above FP32 noise
-    // (>= 1e-5 s_0): the truncation count then cannot change; else the full
+    // (>= 1e-6 s_0, ten times the FP32 resolution of one-sided Jacobi and far
+    // above eps_cut): the truncation count then cannot change; else the full
     // FP64 Jacobi below runs.
     float* T32 = reinterpret_cast<float*>(R2o);
     float* V32 = T32 + (long long)M * N;
@@ -697,7 +698,7 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
     __syncthreads();
     const int nk = N < it.chimax ? N : it.chimax;
     if (threadIdx.x == 0) {
-      sh_resolved = (!sh_capped32 && sv[order[0]] > 0.0 && sv[order[nk - 1]] >= 1e-5 * sv[order[0]]) ? 1 : 0;
+      sh_resolved = (!sh_capped32 && sv[order[0]] > 0.0 && sv[order[nk - 1]] >= 1e-6 * sv[order[0]]) ? 1 : 0;
       if (!sh_resolved) atomicOr(flags, sh_capped32 ? 48 : 16);   // bit 4: FP64 fallback, bit 5: FP32 sweep cap
     }
     __syncthreads();

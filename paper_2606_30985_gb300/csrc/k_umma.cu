@@ -175,6 +175,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
       : "r"(taddr)
       : "memory");
 }
+// completes outstanding tcgen05.ld of two 16-column blocks at once; both
+// register sets are threaded through so no use is scheduled before the wait
+__device__ __forceinline__ void tmem_wait32(uint32_t* r, uint32_t* q) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(q[0]), "+r"(q[1]), "+r"(q[2]), "+r"(q[3]), "+r"(q[4]), "+r"(q[5]), "+r"(q[6]),
+                 "+r"(q[7]), "+r"(q[8]), "+r"(q[9]), "+r"(q[10]), "+r"(q[11]), "+r"(q[12]), "+r"(q[13]), "+r"(q[14]),
+                 "+r"(q[15])
+               :
+               : "memory");
+}
 // completes outstanding tcgen05.ld; the registers are threaded through so no
 // use of them is scheduled before the wait
 __device__ __forceinline__ void tmem_wait16(uint32_t* r) {
@@ -396,9 +408,8 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
       for (int c0 = 0; c0 < L.N16; c0 += 16) {
         uint32_t v1[16], v2[16];
         tmem_ld16(tbase + (uint32_t)c0, v1);
-        tmem_wait16(v1);
         tmem_ld16(tbase + (uint32_t)(L.N16 + c0), v2);
-        tmem_wait16(v2);
+        tmem_wait32(v1, v2);
         if (valid) {
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
@@ -720,9 +731,8 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
         for (int c0 = 0; c0 < F8; c0 += 16) {
           uint32_t v1[16], v2[16];
           tmem_ld16(tbase + (uint32_t)c0, v1);
-          tmem_wait16(v1);
           tmem_ld16(tbase + (uint32_t)(F8 + c0), v2);
-          tmem_wait16(v2);
+          tmem_wait32(v1, v2);
           if (live_row) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
@@ -1140,9 +1150,8 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
       for (int c0 = 0; c0 < D.NB; c0 += 16) {
         uint32_t v1[16], v2[16];
         tmem_ld16(tbase + (uint32_t)c0, v1);
-        tmem_wait16(v1);
         tmem_ld16(tbase + (uint32_t)(D.NB + c0), v2);
-        tmem_wait16(v2);
+        tmem_wait32(v1, v2);
         if (valid) {
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
