@@ -110,10 +110,7 @@ typedef struct {
   int flags;               /* bit 0: rank-deficient message met (env projector
                               skipped), bit 1: non-finite value seen,
                               bit 2: a Jacobi SVD hit its sweep cap,
-                              bit 3: gate rank above the bound (init only),
-                              bit 4: a mixed-precision bond-core SVD fell
-                              back to FP64 (kept set not resolved in FP32),
-                              bit 5: ... because its FP32 pass hit the cap */
+                              bit 3: gate rank above the bound (init only) */
   int steps;               /* Trotter steps taken so far */
 } pepo_diag;
 
@@ -249,9 +246,11 @@ int pepo_ws_rows(pepo_ctx* ctx, int inst);
 pepo_status pepo_ws_features(pepo_ctx* ctx, int inst, float* X_dev, int max_rows);
 /* Training targets: log of the diagonal of the current (converged) messages. */
 pepo_status pepo_ws_targets(pepo_ctx* ctx, int inst, float* t_dev, int max_rows);
-/* Overwrite every message of the instance with diag(exp(y)) / sum exp(y)
- * (the warm start; y_dev has pepo_ws_rows entries). */
-pepo_status pepo_ws_apply(pepo_ctx* ctx, int inst, const float* y_dev);
+/* Warm start: overwrite every message of the instance with the diagonal
+ * (1 - gamma) d / sum d + gamma exp(y) / sum exp(y), d = the current diagonal
+ * (diag(lambda) right after a Trotter step); gamma in [0, 1] (1 = the
+ * prediction alone).  y_dev has pepo_ws_rows entries. */
+pepo_status pepo_ws_apply(pepo_ctx* ctx, int inst, const float* y_dev, float gamma);
 
 /* Copy one directed message (chi x chi, row-major) to the host. */
 pepo_status pepo_get_message(pepo_ctx* ctx, int inst, int bond, int dir, double* out,

@@ -5,7 +5,8 @@ the GPU kernels of the warm start compute.  The paper has no learned part; the
 method is specified by the task's scope (a proposal): per directed bond e and
 Schmidt index k, a small MLP predicts the log of the diagonal of the converged
 double-layer message in the bond's Schmidt basis, and damped BP then runs
-from M = diag(exp(y)) / sum(exp(y)) to its tolerance.
+to its tolerance from the trace-1 diagonal that blends the prediction
+exp(y) / sum(exp(y)) with the diag(lambda) start by a weight gamma.
 
 Rows: (bond b, direction dir, k) for k < chi_b.  Features (NF = 12):
   0  log lam_k (Vidal-normalised spectrum, Eq. 12; clamped at 1e-30)
@@ -173,7 +174,13 @@ class Adam:
             params[k] = params[k] - self.lr * mh / (np.sqrt(vh) + self.eps)
 
 
-def warm_message(y):
-    """Initial message of one directed bond from its predicted log-diagonal."""
+def warm_message(y, plain_diag=None, gamma=1.0):
+    """Initial message of one directed bond: the trace-1 diagonal
+    (1 - gamma) d / sum(d) + gamma exp(y) / sum(exp(y)), d = the current
+    (diag(lambda)) diagonal; gamma = 1 uses the prediction alone."""
     e = np.exp(y - np.max(y))
-    return np.diag(e / e.sum())
+    p = e / e.sum()
+    if plain_diag is not None and gamma < 1.0:
+        d = np.asarray(plain_diag, dtype=np.float64)
+        p = (1.0 - gamma) * d / d.sum() + gamma * p
+    return np.diag(p)

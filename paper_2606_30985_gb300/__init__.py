@@ -60,6 +60,12 @@ EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trot
 
 _lib = None
 
+# learned warm start: feature count, hidden width, default blend of the
+# prediction with the diag(lambda) start (best of {1, 0.5, 0.25} in the 6x6 study)
+WS_FEATURES = 12
+WS_WIDTH = 256
+WS_GAMMA = 0.25
+
 
 def load_library(path=LIB_PATH):
     """Load libpepo.so (raises if it has not been built)."""
@@ -120,7 +126,7 @@ def load_library(path=LIB_PATH):
     lib.pepo_ws_features.restype = I
     lib.pepo_ws_targets.argtypes = [P, I, P, I]
     lib.pepo_ws_targets.restype = I
-    lib.pepo_ws_apply.argtypes = [P, I, P]
+    lib.pepo_ws_apply.argtypes = [P, I, P, F]
     lib.pepo_ws_apply.restype = I
     lib.pepo_get_message.argtypes = [P, I, I, I, ctypes.POINTER(D), ctypes.POINTER(I)]
     lib.pepo_get_message.restype = I
@@ -393,15 +399,17 @@ class Engine:
                     "pepo_ws_targets")
         return t
 
-    def ws_apply(self, y, inst=0):
-        """Messages <- diag(exp(y)) / sum exp(y) per directed bond."""
-        self._check(self.lib.pepo_ws_apply(self.ctx, inst, ctypes.c_void_p(y.data_ptr())), "pepo_ws_apply")
+    def ws_apply(self, y, inst=0, gamma=1.0):
+        """Messages <- diag((1-gamma) d/sum d + gamma exp(y)/sum exp(y)) per directed bond."""
+        self._check(self.lib.pepo_ws_apply(self.ctx, inst, ctypes.c_void_p(y.data_ptr()), ctypes.c_float(gamma)),
+                    "pepo_ws_apply")
 
-    def ws_warm_start(self, mlp, inst=0):
-        """Predict the converged message diagonals with `mlp` and install them."""
+    def ws_warm_start(self, mlp, inst=0, gamma=WS_GAMMA):
+        """Predict the converged message diagonals with `mlp` and install them
+        (blended with the current diag(lambda) start by gamma)."""
         X = self.ws_features(inst)
         y = mlp.forward(X)
-        self.ws_apply(y, inst)
+        self.ws_apply(y, inst, gamma)
         return X.shape[0]
 
     def run(self, nsteps, measure_every=1):
@@ -419,9 +427,6 @@ class Engine:
                 out.append(pick(D))
         return out
 
-
-WS_FEATURES = 12
-WS_WIDTH = 256
 
 
 class Mlp:

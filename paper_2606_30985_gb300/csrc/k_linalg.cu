@@ -661,85 +661,33 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
   __syncthreads();
   for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) V[e] = Tc[e];   // copy of Tcore
   __syncthreads();
-  __shared__ int sh_resolved;
-  __shared__ double sh_fro2;
-  if (threadIdx.x == 0) { sh_resolved = 0; sh_fro2 = -1.0; }
-  __syncthreads();
   if (it.mixed_svd) {
     // FP32 one-sided Jacobi with accumulated right vectors V32 (in the R2
-    // block, free until the reconstruct step), then an FP64 Rayleigh step on
-    // the kept set: column j of Tc becomes T v32_j in FP64 and its norm the
-    // singular value (second-order accurate in the FP32 vector error).  Valid
-    // when every kept FP32 singular value stands well above FP32 noise
-    // (>= 1e-6 s_0, ten times the FP32 resolution of one-sided Jacobi and far
-    // above eps_cut): the truncation count then cannot change; else the full
-    // FP64 Jacobi below runs.
+    // block, free until the reconstruct step) as a preconditioner: Tc <- T V32
+    // in FP64, whose columns are orthogonal to FP32 accuracy, so the FP64
+    // Jacobi below converges in a couple of sweeps.  V32 is orthogonal to
+    // ~1e-7, which moves every singular value by ~1e-7 relative (tiny ones
+    // included) and the vectors by ~1e-7 / gap; the other side's vectors are
+    // recovered from the original T as in the FP64 path.
     float* T32 = reinterpret_cast<float*>(R2o);
     float* V32 = T32 + (long long)M * N;
     for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) T32[e] = (float)Tc[e];
     __syncthreads();
-    __shared__ int sh_capped32;   // a capped FP32 pass only means the FP64 path runs
+    __shared__ int sh_capped32;   // a capped FP32 pass only costs FP64 sweeps below
     if (threadIdx.x == 0) sh_capped32 = 0;
     __syncthreads();
     jacobi_svd<float>(T32, M, N, V32, 60, &sh_capped32, red);
     __syncthreads();
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-      double s = 0.0;
-      const float* col = T32 + (long long)j * M;
-      for (int i = 0; i < M; ++i) s = fma((double)col[i], (double)col[i], s);
-      sv[j] = sqrt(s);
+    for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) {
+      const int j = (int)(e / M), i = (int)(e - (long long)j * M);
+      const float* vj = V32 + (long long)j * N;
+      double acc = 0.0;
+      for (int k = 0; k < N; ++k) acc = fma(V[(long long)k * M + i], (double)vj[k], acc);
+      Tc[e] = acc;
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-      int rk = 0;
-      for (int i = 0; i < N; ++i) if (sv[i] > sv[j] || (sv[i] == sv[j] && i < j)) ++rk;
-      order[rk] = j;
-    }
-    __syncthreads();
-    const int nk = N < it.chimax ? N : it.chimax;
-    if (threadIdx.x == 0) {
-      sh_resolved = (!sh_capped32 && sv[order[0]] > 0.0 && sv[order[nk - 1]] >= 1e-6 * sv[order[0]]) ? 1 : 0;
-      if (!sh_resolved) atomicOr(flags, sh_capped32 ? 48 : 16);   // bit 4: FP64 fallback, bit 5: FP32 sweep cap
-    }
-    __syncthreads();
-    if (sh_resolved) {
-      // exact ||T||_F^2 (FP64) for the discarded weight
-      double f = 0.0;
-      for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) f = fma(V[e], V[e], f);
-      f = block_sum(f, red);
-      if (threadIdx.x == 0) sh_fro2 = f;
-      // kept columns: Tc[:, j] = T v32_j (FP64)
-      for (long long e = threadIdx.x; e < (long long)nk * M; e += blockDim.x) {
-        const int c = (int)(e / M), i = (int)(e % M);
-        const int j = order[c];
-        const float* vj = V32 + (long long)j * N;
-        double acc = 0.0;
-        for (int k = 0; k < N; ++k) acc = fma(V[(long long)k * M + i], (double)vj[k], acc);
-        Tc[(long long)j * M + i] = acc;
-      }
-      __syncthreads();
-      for (int c = threadIdx.x; c < nk; c += blockDim.x) {
-        const int j = order[c];
-        double s = 0.0;
-        const double* col = Tc + (long long)j * M;
-        for (int i = 0; i < M; ++i) s = fma(col[i], col[i], s);
-        sv[j] = sqrt(s);
-      }
-      __syncthreads();
-      // re-rank the kept set by its FP64 values (the rest keep FP32 values
-      // and their FP32 ranks, used for diagnostics only)
-      if (threadIdx.x == 0) {
-        for (int a = 1; a < nk; ++a) {
-          const int j = order[a];
-          int b = a - 1;
-          while (b >= 0 && sv[order[b]] < sv[j]) { order[b + 1] = order[b]; --b; }
-          order[b + 1] = j;
-        }
-      }
-      __syncthreads();
-    }
   }
-  if (!sh_resolved) {   // Tc still holds Tcore (the FP32 pass worked on a copy)
+  {   // FP64 one-sided Jacobi on Tcore (or on its FP32-preconditioned form)
     jacobi_svd<double>(Tc, M, N, nullptr, 60, &sh_capped, red);
     __syncthreads();
     // singular values (column norms) and descending order
@@ -769,7 +717,6 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
       tot += s * s;
       if (s >= it.eps_cut * s0 && s > 0.0) ++cnt;
     }
-    if (sh_fro2 >= 0.0) tot = sh_fro2;   // mixed path: exact Frobenius norm
     int chi = cnt < it.chimax ? cnt : it.chimax;
     if (chi < 1) chi = 1;
     double kept = 0.0, ksum = 0.0;

@@ -218,12 +218,15 @@ __global__ void k_ws_targets(int nb, const int* __restrict__ chi, const double* 
   }
 }
 
-// messages <- diag(exp(y)) / sum exp(y) (max-shifted), zero elsewhere
-__global__ void k_ws_apply(int nb, const int* __restrict__ chi, const float* __restrict__ y, double* msg, int ldm) {
+// messages <- diag((1 - gamma) d / sum d + gamma exp(y) / sum exp(y)), zero
+// elsewhere; d = diagonal of the current message (the diag(lambda) written by
+// the bond updates), exp(y) max-shifted
+__global__ void k_ws_apply(int nb, const int* __restrict__ chi, const float* __restrict__ y, double* msg, int ldm,
+                           float gamma) {
   const int db = blockIdx.x;
   const int b = db >> 1, dir = db & 1;
   __shared__ long long off;
-  __shared__ double red[256];
+  __shared__ double red[256], red2[256];
   __shared__ float ymax;
   if (threadIdx.x == 0) {
     long long o = 0;
@@ -232,26 +235,43 @@ __global__ void k_ws_apply(int nb, const int* __restrict__ chi, const float* __r
   }
   __syncthreads();
   const int c = chi[b];
+  double* M = msg + (long long)db * ldm * ldm;
   if (threadIdx.x == 0) {
     float m = -INFINITY;
     for (int k = 0; k < c; ++k) m = fmaxf(m, y[off + k]);
     ymax = m;
   }
   __syncthreads();
-  double s = 0.0;
-  for (int k = threadIdx.x; k < c; k += blockDim.x) s += exp((double)(y[off + k] - ymax));
+  double s = 0.0, sd = 0.0;
+  for (int k = threadIdx.x; k < c; k += blockDim.x) {
+    s += exp((double)(y[off + k] - ymax));
+    sd += M[(long long)k * ldm + k];
+  }
   red[threadIdx.x] = s;
+  red2[threadIdx.x] = sd;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    if (threadIdx.x < o) { red[threadIdx.x] += red[threadIdx.x + o]; red2[threadIdx.x] += red2[threadIdx.x + o]; }
     __syncthreads();
   }
-  const double tot = red[0];
-  double* M = msg + (long long)db * ldm * ldm;
+  const double tot = red[0], totd = red2[0];
+  // diagonal first (read before the overwrite), then the rest
+  double dk[8];
+  int nk = 0;
+  for (int k = threadIdx.x; k < c && nk < 8; k += blockDim.x) dk[nk++] = M[(long long)k * ldm + k];
+  __syncthreads();
+  nk = 0;
+  for (int k = threadIdx.x; k < c && nk < 8; k += blockDim.x) {
+    const double plain = totd > 0.0 ? dk[nk] / totd : 0.0;
+    dk[nk++] = (1.0 - gamma) * plain + gamma * exp((double)(y[off + k] - ymax)) / tot;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < ldm * ldm; e += blockDim.x) {
     const int i = e / ldm, j = e - i * ldm;
-    M[e] = (i == j && i < c) ? exp((double)(y[off + i] - ymax)) / tot : 0.0;
+    if (i != j || i >= c) M[e] = 0.0;
   }
+  nk = 0;
+  for (int k = threadIdx.x; k < c && nk < 8; k += blockDim.x) M[(long long)k * ldm + k] = dk[nk++];
 }
 
 // ------------------------------------------------------------------ launchers
@@ -267,9 +287,10 @@ cudaError_t launch_ws_targets(int nb, const int* chi, const double* msg, int ldm
   k_ws_targets<<<2 * nb, 128, 0, s>>>(nb, chi, msg, ldm, out, max_rows);
   return cudaGetLastError();
 }
-cudaError_t launch_ws_apply(int nb, const int* chi, const float* y, double* msg, int ldm, cudaStream_t s) {
+cudaError_t launch_ws_apply(int nb, const int* chi, const float* y, double* msg, int ldm, float gamma,
+                            cudaStream_t s) {
   if (nb == 0) return cudaSuccess;
-  k_ws_apply<<<2 * nb, 256, 0, s>>>(nb, chi, y, msg, ldm);
+  k_ws_apply<<<2 * nb, 256, 0, s>>>(nb, chi, y, msg, ldm, gamma);
   return cudaGetLastError();
 }
 

@@ -25,12 +25,13 @@
 //   warps 4-7     epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
 //                 lanes 32 (w % 4) .. +31), store to global memory (leg) or
 //                 add into compensated FP32 sums in shared memory (Gram)
-//   warps 8-15    converters: coalesced 16-byte global loads, weight, split,
-//                 and 16-byte / conflict-free stores into the K-major
-//                 no-swizzle core-matrix layout the MMA descriptors describe
+//   warps 8-15    converters: coalesced global loads, weight, split, and
+//                 16-byte conflict-free stores into the swizzled K-major
+//                 layout the MMA descriptors describe (below)
 // Stages and accumulators are handed over with mbarriers.  Every wait is
 // bounded (a few seconds of %globaltimer); on expiry the kernel records bit 0
-// in *err, every role leaves its loop, the MMA issuer drains its outstanding
+// in *err (bit 1 marks a reconstruct item without its packed-W workspace),
+// every role leaves its loop, the MMA issuer drains its outstanding
 // MMAs (bounded), tensor memory is freed and the kernel returns.
 //
 // Shared-memory operand layout: K-major with the 128-byte swizzle.  A row of
@@ -1210,9 +1211,14 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
       unsigned char* lo = hi + P.a_bytes;
       unsigned char* bs = hi + 2 * P.a_bytes;
       if (issuer) {
-        const uint32_t bytes = (uint32_t)(2 * D.NB) * 128u;
-        mbar_arrive_tx(&bars->full[s], bytes);
-        bulk_g2s(bs, D.Wp + ((size_t)nb * D.nkc + kc) * (size_t)(2 * D.NB) * 32, bytes, &bars->full[s]);
+        if (D.Wp) {
+          const uint32_t bytes = (uint32_t)(2 * D.NB) * 128u;
+          mbar_arrive_tx(&bars->full[s], bytes);
+          bulk_g2s(bs, D.Wp + ((size_t)nb * D.nkc + kc) * (size_t)(2 * D.NB) * 32, bytes, &bars->full[s]);
+        } else {   // no packed W workspace: flag it and keep the pipeline moving
+          atomicOr(err, 2);
+          mbar_arrive(&bars->full[s]);
+        }
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -1262,6 +1268,7 @@ int sm_count() {
 // = hi(W[k, nb NB + c]) and rows NB + c = the lo part, k in the chunk.
 __global__ void k_pack_w(const ReconItem* __restrict__ items, void* const* ptrs, const int* __restrict__ ival) {
   const ReconItem it = items[blockIdx.y];
+  if (it.Wp == nullptr) return;
   RecDims D;
   rec_dims(it, ptrs, ival, D);
   const long long per_blk = (long long)(2 * D.NB) * 32;

@@ -33,6 +33,7 @@ cudaError_t launch_ws_features(const WsGeom* geom, int nb, const int* chi, const
                                float h, float J, float* X, int max_rows, cudaStream_t s);
 cudaError_t launch_ws_targets(int nb, const int* chi, const double* msg, int ldm, float* out, int max_rows,
                               cudaStream_t s);
-cudaError_t launch_ws_apply(int nb, const int* chi, const float* y, double* msg, int ldm, cudaStream_t s);
+cudaError_t launch_ws_apply(int nb, const int* chi, const float* y, double* msg, int ldm, float gamma,
+                            cudaStream_t s);
 
 }  // namespace pepo

@@ -1428,7 +1428,7 @@ pepo_status do_bp(pepo_ctx* c, int* sweeps_out, double* delta_out) {
         cudaMemcpyAsync(&kerr, c->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return fail(c, PEPO_E_CUDA, "BP delta readback: %s", cudaGetErrorString(cudaGetLastError()));
-    if (kerr) return fail(c, PEPO_E_CUDA, "a tensor-core pipeline wait expired (kernel error word %d)", kerr);
+    if (kerr) return fail(c, PEPO_E_CUDA, "tensor-core kernel error word %d (bit 0: a pipeline wait expired, bit 1: missing packed-W workspace)", kerr);
     for (int i = 0; i < c->n_inst; ++i) {
       if (!active[i]) continue;
       Inst& I = c->inst[i];
@@ -1497,7 +1497,7 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
         cudaMemcpyAsync(&kerr, c->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return fail(c, PEPO_E_CUDA, "single-layer delta readback");
-    if (kerr) return fail(c, PEPO_E_CUDA, "a tensor-core pipeline wait expired (kernel error word %d)", kerr);
+    if (kerr) return fail(c, PEPO_E_CUDA, "tensor-core kernel error word %d (bit 0: a pipeline wait expired, bit 1: missing packed-W workspace)", kerr);
     for (int i = 0; i < c->n_inst; ++i) {
       if (!active[i]) continue;
       Inst& I = c->inst[i];
@@ -1523,7 +1523,7 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
       cudaMemcpyAsync(&kerr, c->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return fail(c, PEPO_E_CUDA, "flags readback");
-  if (kerr) return fail(c, PEPO_E_CUDA, "a tensor-core pipeline wait expired (kernel error word %d)", kerr);
+  if (kerr) return fail(c, PEPO_E_CUDA, "tensor-core kernel error word %d (bit 0: a pipeline wait expired, bit 1: missing packed-W workspace)", kerr);
   for (int i = 0; i < c->n_inst; ++i) {
     Inst& I = c->inst[i];
     double out[8];
@@ -2074,11 +2074,12 @@ pepo_status pepo_ws_targets(pepo_ctx* c, int inst, float* t_dev, int max_rows) {
   return e == cudaSuccess ? PEPO_OK : fail(c, PEPO_E_CUDA, "warm-start targets: %s", cudaGetErrorString(e));
 }
 
-pepo_status pepo_ws_apply(pepo_ctx* c, int inst, const float* y_dev) {
+pepo_status pepo_ws_apply(pepo_ctx* c, int inst, const float* y_dev, float gamma) {
   if (!c) return PEPO_E_INVALID;
-  if (inst < 0 || inst >= c->n_inst || !y_dev) return fail(c, PEPO_E_INVALID, "bad arguments");
+  if (inst < 0 || inst >= c->n_inst || !y_dev || !(gamma >= 0.f && gamma <= 1.f))
+    return fail(c, PEPO_E_INVALID, "bad arguments");
   Inst& I = c->inst[inst];
-  cudaError_t e = launch_ws_apply(I.nb, c->d_ival + I.chi0, y_dev, I.msg, I.cfg.chi_max, c->stream);
+  cudaError_t e = launch_ws_apply(I.nb, c->d_ival + I.chi0, y_dev, I.msg, I.cfg.chi_max, gamma, c->stream);
   c->launches++;
   return e == cudaSuccess ? PEPO_OK : fail(c, PEPO_E_CUDA, "warm-start apply: %s", cudaGetErrorString(e));
 }

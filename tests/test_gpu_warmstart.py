@@ -84,12 +84,64 @@ def test_features_targets_and_apply_on_an_evolved_state():
         M = eng.message(0, b, d)
         assert abs(t[r] - np.log(max(M[k, k], 1e-300))) < 1e-5
     y = torch.linspace(-1.0, 1.0, X.shape[0], device="cuda", dtype=torch.float32)
-    eng.ws_apply(y)
     yh = y.cpu().numpy()
+    before = {(b, d): np.diag(eng.message(0, b, d)).copy() for b in range(nb) for d in range(2)}
+    eng.ws_apply(y, gamma=0.25)
     for b in range(nb):
         for d in range(2):
             rows = [r for r in range(len(idx)) if idx[r][0] == b and idx[r][1] == d]
             M = eng.message(0, b, d)
-            ref = om.warm_message(yh[rows].astype(np.float64))
+            ref = om.warm_message(yh[rows].astype(np.float64), plain_diag=before[(b, d)], gamma=0.25)
             assert M.shape == ref.shape and np.max(np.abs(M - ref)) < 1e-6
+    eng.ws_apply(y, gamma=1.0)
+    for b in range(nb):
+        for d in range(2):
+            rows = [r for r in range(len(idx)) if idx[r][0] == b and idx[r][1] == d]
+            ref = om.warm_message(yh[rows].astype(np.float64))
+            assert np.max(np.abs(eng.message(0, b, d) - ref)) < 1e-6
     eng.close()
+
+
+def _trajectory(h, obs, steps, net=None, gamma=pkg.WS_GAMMA, collect=None):
+    cfg = pkg.Config(Lx=6, Ly=6, J=1.0, h=h, dt=0.05, order=2, obs=obs, chi_max=12, precision="fp32")
+    eng = pkg.Engine(cfg)
+    sweeps, Cs = [], []
+    for _ in range(steps):
+        eng.trotter_step(1)
+        X = eng.ws_features().clone()
+        if net is not None:
+            eng.ws_apply(net.forward(X), gamma=gamma)
+        sw, _ = eng.bp_converge()
+        C, _ = eng.correlator()
+        sweeps.append(sw[0])
+        Cs.append(C[0])
+        if collect is not None:
+            collect.append((X, eng.ws_targets().clone()))
+    eng.close()
+    return sweeps, Cs
+
+
+def test_trained_network_saves_bp_sweeps():
+    """Train on two 6x6 trajectories (the GPU's own forward / backward / Adam
+    kernels), then run a held-out trajectory (other h, other observable site)
+    with and without the warm start: fewer total BP sweeps, same C(t)."""
+    import torch
+    data = []
+    for h, obs in ((1.5, (2, 2)), (2.5, (3, 2))):
+        _trajectory(h, obs, 20, collect=data)
+    X = torch.cat([d[0] for d in data])
+    T = torch.cat([d[1] for d in data])
+    net = pkg.Mlp(pkg.flat_params(om.init_params(seed=0)), max_rows=4096)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    first = None
+    for it in range(1500):
+        idx = torch.randint(0, X.shape[0], (4096,), device="cuda", generator=g)
+        loss, _ = net.gradient(X[idx], T[idx])
+        first = loss if first is None else first
+        net.adam_step(1e-3)
+    assert loss < 1e-2 * first
+    plain, Cp = _trajectory(2.0, (3, 3), 20)
+    warm, Cw = _trajectory(2.0, (3, 3), 20, net=net)
+    print("BP sweeps over 20 held-out steps: plain %d, warm start %d (%s vs %s)" % (sum(plain), sum(warm), plain, warm))
+    assert sum(warm) < sum(plain)
+    assert max(abs(a - b) for a, b in zip(Cp, Cw)) < 1e-3

@@ -100,3 +100,9 @@ def test_features_of_a_hand_built_3x3_state():
 def test_warm_message_is_trace_one_diagonal():
     M = mlp.warm_message(np.log(np.array([4.0, 2.0, 2.0])))
     assert np.allclose(M, np.diag([0.5, 0.25, 0.25]))
+
+
+def test_warm_message_blend():
+    M = mlp.warm_message(np.log(np.array([4.0, 2.0, 2.0])), plain_diag=np.array([1.0, 1.0, 0.0]), gamma=0.5)
+    assert np.allclose(np.diag(M), [0.5 * 0.5 + 0.5 * 0.5, 0.5 * 0.5 + 0.5 * 0.25, 0.5 * 0.25])
+    assert abs(np.trace(M) - 1.0) < 1e-15
