@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpepo.so")
-SOURCES = ["pepo.cu", "k_tensor.cu", "k_contract.cu", "k_mma.cu", "k_umma.cu", "k_linalg.cu", "k_bp.cu", "k_mlp.cu"]
+SOURCES = ["pepo.cu", "k_tensor.cu", "k_contract.cu", "k_umma.cu", "k_linalg.cu", "k_bp.cu", "k_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

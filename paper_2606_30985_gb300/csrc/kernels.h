@@ -33,12 +33,6 @@ template <typename T>
 cudaError_t launch_vec_contract(const VecItem* items, int n_items, int grid_x,
                                 void* const* ptrs, const int* ival, cudaStream_t s);
 
-// ---- k_mma.cu (FP32 storage, TF32x3 tensor-core arithmetic) -------------
-cudaError_t launch_leg_contract_tc(const LegItem* items, int n_items, int grid_x, void* const* ptrs,
-                                   const int* ival, cudaStream_t s);
-cudaError_t launch_gram_leg_tc(const GramLegItem* items, int n_items, int splits_max, void* const* ptrs,
-                               const int* ival, cudaStream_t s);
-
 // ---- k_umma.cu (FP32 storage, TF32x3 on tcgen05 tensor cores, chi <= 128)
 bool umma_supported(int chimax);
 // err: device int; bit 0 is set when a pipeline wait of the kernel expired
