@@ -406,18 +406,37 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
       if (valid) { o = rg / L.Q; q = rg - o * L.Q; }
       float* dst = L.out + (o * L.Jout) * L.Q + q;
       const uint32_t tbase = tmem + lane_base + (uint32_t)(b * 256);
-      for (int c0 = 0; c0 < L.N16; c0 += 16) {
-        uint32_t v1[16], v2[16];
-        tmem_ld16(tbase + (uint32_t)c0, v1);
-        tmem_ld16(tbase + (uint32_t)(L.N16 + c0), v2);
-        tmem_wait32(v1, v2);
-        if (valid) {
+      // 16-column blocks; the TMEM loads of block i+1 are in flight while
+      // block i is stored (two register sets, unrolled so none is copied)
+      uint32_t a1[16], a2[16], b1[16], b2[16];
+      auto store_blk = [&](const uint32_t* p1, const uint32_t* p2, int c0) {
+        if (!valid) return;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int col = c0 + i;
-            if (col < L.Jout) dst[(long long)col * L.Q] = __uint_as_float(v1[i]) + __uint_as_float(v2[i]);
-          }
+        for (int i = 0; i < 16; ++i) {
+          const int col = c0 + i;
+          if (col < L.Jout) dst[(long long)col * L.Q] = __uint_as_float(p1[i]) + __uint_as_float(p2[i]);
         }
+      };
+      tmem_ld16(tbase, a1);
+      tmem_ld16(tbase + (uint32_t)L.N16, a2);
+      tmem_wait32(a1, a2);
+      for (int c0 = 0; c0 < L.N16; c0 += 32) {
+        const bool m1 = c0 + 16 < L.N16;
+        if (m1) {
+          tmem_ld16(tbase + (uint32_t)(c0 + 16), b1);
+          tmem_ld16(tbase + (uint32_t)(L.N16 + c0 + 16), b2);
+        }
+        store_blk(a1, a2, c0);
+        if (!m1) break;
+        tmem_wait32(b1, b2);
+        const bool m2 = c0 + 32 < L.N16;
+        if (m2) {
+          tmem_ld16(tbase + (uint32_t)(c0 + 32), a1);
+          tmem_ld16(tbase + (uint32_t)(L.N16 + c0 + 32), a2);
+        }
+        store_blk(b1, b2, c0 + 16);
+        if (!m2) break;
+        tmem_wait32(a1, a2);
       }
       tc_before();
       warp_arrive(&bars->accempty[b]);
@@ -1148,19 +1167,37 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
       }
       const long long ocut = D.ostride[D.cut];
       const uint32_t tbase = tmem + lane_base + (uint32_t)(b * 256);
-      for (int c0 = 0; c0 < D.NB; c0 += 16) {
-        uint32_t v1[16], v2[16];
-        tmem_ld16(tbase + (uint32_t)c0, v1);
-        tmem_ld16(tbase + (uint32_t)(D.NB + c0), v2);
-        tmem_wait32(v1, v2);
-        if (valid) {
+      // 16-column blocks, loads of block i+1 in flight while block i is stored
+      uint32_t a1[16], a2[16], b1[16], b2[16];
+      auto store_blk = [&](const uint32_t* p1, const uint32_t* p2, int c0) {
+        if (!valid) return;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int cg = nb * D.NB + c0 + i;
-            if (c0 + i < D.NB && cg < D.np)
-              D.out[base + (long long)(cg >> 2) * ocut + (cg & 3)] = __uint_as_float(v1[i]) + __uint_as_float(v2[i]);
-          }
+        for (int i = 0; i < 16; ++i) {
+          const int cg = nb * D.NB + c0 + i;
+          if (c0 + i < D.NB && cg < D.np)
+            D.out[base + (long long)(cg >> 2) * ocut + (cg & 3)] = __uint_as_float(p1[i]) + __uint_as_float(p2[i]);
         }
+      };
+      tmem_ld16(tbase, a1);
+      tmem_ld16(tbase + (uint32_t)D.NB, a2);
+      tmem_wait32(a1, a2);
+      for (int c0 = 0; c0 < D.NB; c0 += 32) {
+        const bool m1 = c0 + 16 < D.NB;
+        if (m1) {
+          tmem_ld16(tbase + (uint32_t)(c0 + 16), b1);
+          tmem_ld16(tbase + (uint32_t)(D.NB + c0 + 16), b2);
+        }
+        store_blk(a1, a2, c0);
+        if (!m1) break;
+        tmem_wait32(b1, b2);
+        const bool m2 = c0 + 32 < D.NB;
+        if (m2) {
+          tmem_ld16(tbase + (uint32_t)(c0 + 32), a1);
+          tmem_ld16(tbase + (uint32_t)(D.NB + c0 + 32), a2);
+        }
+        store_blk(b1, b2, c0 + 16);
+        if (!m2) break;
+        tmem_wait32(a1, a2);
       }
       tc_before();
       warp_arrive(&bars->accempty[b]);
