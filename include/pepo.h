@@ -183,6 +183,17 @@ pepo_status pepo_set_bonds(pepo_ctx* ctx, int inst, const int* chi, const double
 pepo_status pepo_set_site(pepo_ctx* ctx, int inst, int site, const void* data, int dtype,
                           size_t count);
 
+/* Snapshot of one instance's state (site tensors at their slab capacity,
+ * live bond dimensions, lambda, double- and single-layer messages,
+ * log-scales, discarded weights) for restarting from the same state.
+ * dev_buf: device memory owned by the caller, at least pepo_state_bytes
+ * bytes.  Device-to-device copies on the context's stream (asynchronous after
+ * one synchronising read of the site pointers).  Not a step of the paper's
+ * method. */
+size_t pepo_state_bytes(const pepo_ctx* ctx, int inst);
+pepo_status pepo_save_state(pepo_ctx* ctx, int inst, void* dev_buf, size_t bytes);
+pepo_status pepo_load_state(pepo_ctx* ctx, int inst, const void* dev_buf, size_t bytes);
+
 /* pepo_set_site without any memory allocation (the paper has no counterpart:
  * it is an interface variant, not a step of the method).  Same arguments and
  * result as pepo_set_site, but the host data is staged in a fixed 16 MiB

@@ -51,7 +51,8 @@ class _Diag(ctypes.Structure):
 
 EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trotter_step",
            "pepo_bp_converge", "pepo_correlator", "pepo_get_spectrum", "pepo_get_site",
-           "pepo_set_state", "pepo_set_bonds", "pepo_set_site", "pepo_set_site_static", "pepo_get_message", "pepo_num_bonds", "pepo_set_timing",
+           "pepo_set_state", "pepo_set_bonds", "pepo_set_site", "pepo_set_site_static", "pepo_state_bytes", "pepo_save_state", "pepo_load_state",
+           "pepo_get_message", "pepo_num_bonds", "pepo_set_timing",
            "pepo_timing_classes", "pepo_timing_class_name", "pepo_get_timing", "pepo_reset_timing",
            "pepo_launch_count", "pepo_last_error", "pepo_destroy",
            "pepo_mlp_num_params", "pepo_mlp_required_bytes", "pepo_mlp_init", "pepo_mlp_get_params",
@@ -102,6 +103,12 @@ def load_library(path=LIB_PATH):
     lib.pepo_set_site.restype = I
     lib.pepo_set_site_static.argtypes = [P, I, I, P, I, S]
     lib.pepo_set_site_static.restype = I
+    lib.pepo_state_bytes.argtypes = [P, I]
+    lib.pepo_state_bytes.restype = S
+    lib.pepo_save_state.argtypes = [P, I, P, S]
+    lib.pepo_save_state.restype = I
+    lib.pepo_load_state.argtypes = [P, I, P, S]
+    lib.pepo_load_state.restype = I
     F = ctypes.c_float
     FP = ctypes.POINTER(ctypes.c_float)
     lib.pepo_mlp_num_params.argtypes = []
@@ -373,6 +380,19 @@ class Engine:
         dt = 0 if t.dtype == np.float32 else 1
         self._check(self.lib.pepo_set_site_static(self.ctx, inst, v, ctypes.c_void_p(t.ctypes.data), dt,
                                                   t.size), "pepo_set_site_static")
+
+    # -- state snapshot
+    def state_bytes(self, inst=0):
+        return int(self.lib.pepo_state_bytes(self.ctx, inst))
+
+    def save_state(self, buf, inst=0):
+        """Copy the instance's state into the device tensor `buf` (uint8)."""
+        self._check(self.lib.pepo_save_state(self.ctx, inst, ctypes.c_void_p(buf.data_ptr()), buf.numel()),
+                    "pepo_save_state")
+
+    def load_state(self, buf, inst=0):
+        self._check(self.lib.pepo_load_state(self.ctx, inst, ctypes.c_void_p(buf.data_ptr()), buf.numel()),
+                    "pepo_load_state")
 
     # -- learned warm start
     def ws_rows(self, inst=0):

@@ -137,6 +137,7 @@ struct Inst {
   DArr<GateItem> gates;
   // diagnostics
   int steps = 0;
+  int saved_steps = 0;       // step count stored with the last pepo_save_state
   int last_sweeps = 0, last_sweeps1 = 0;
   double last_delta = 0, last_delta1 = 0;
   int cap[5] = {0, 0, 0, 0, 0};   // in-flight sites per degree class
@@ -1966,6 +1967,80 @@ pepo_status pepo_set_site_static(pepo_ctx* c, int inst, int site, const void* da
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return fail(c, PEPO_E_CUDA, "site permute");
   return PEPO_OK;
+}
+
+// ------------------------------------------------------- state snapshot
+// Device-to-device copy of one instance's state (site tensors at slab
+// capacity, live bond dimensions, lambda, messages, single-layer vectors,
+// log-scales, discarded weights) to / from a caller buffer.
+static size_t state_layout(const pepo_ctx* c, const Inst& I, size_t* off /* 7 entries or null */) {
+  size_t o = 0;
+  auto sec = [&](int i, size_t bytes) {
+    o = (o + 255) / 256 * 256;
+    if (off) off[i] = o;
+    o += bytes;
+  };
+  size_t site_bytes = 0;
+  for (int v = 0; v < I.N; ++v) site_bytes += 4 * pow_sz(I.cfg.chi_max, I.sites[v].deg) * c->tsize;
+  const size_t cm = I.cfg.chi_max;
+  sec(0, site_bytes);
+  sec(1, sizeof(int) * I.nb);
+  sec(2, sizeof(double) * I.nb * cm);
+  sec(3, sizeof(double) * 2 * I.nb * cm * cm);
+  sec(4, sizeof(double) * 2 * I.nb * cm);
+  sec(5, sizeof(double) * I.N);
+  sec(6, sizeof(double) * I.nb);
+  return o;
+}
+
+size_t pepo_state_bytes(const pepo_ctx* c, int inst) {
+  if (!c || inst < 0 || inst >= c->n_inst) return 0;
+  return state_layout(c, c->inst[inst], nullptr);
+}
+
+static pepo_status state_copy(pepo_ctx* c, int inst, char* buf, size_t bytes, bool save) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst || !buf) return fail(c, PEPO_E_INVALID, "bad arguments");
+  Inst& I = c->inst[inst];
+  size_t off[7];
+  const size_t need = state_layout(c, I, off);
+  if (bytes < need) return fail(c, PEPO_E_INVALID, "state buffer holds %zu bytes, needs %zu", bytes, need);
+  std::vector<void*> sp(I.N);
+  if (cudaMemcpyAsync(sp.data(), c->d_ptrs + I.site_ref0, sizeof(void*) * I.N, cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "site pointer readback");
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  auto cp = [&](void* dev, size_t o, size_t n) {
+    return save ? cudaMemcpyAsync(buf + o, dev, n, k, c->stream) : cudaMemcpyAsync(dev, buf + o, n, k, c->stream);
+  };
+  const size_t cm = I.cfg.chi_max;
+  size_t so = off[0];
+  for (int v = 0; v < I.N; ++v) {
+    const size_t n = 4 * pow_sz(cm, I.sites[v].deg) * c->tsize;
+    if (cp(sp[v], so, n) != cudaSuccess) return fail(c, PEPO_E_CUDA, "site copy");
+    so += n;
+  }
+  if (cp(c->d_ival + I.chi0, off[1], sizeof(int) * I.nb) != cudaSuccess ||
+      cp(I.lam, off[2], sizeof(double) * I.nb * cm) != cudaSuccess ||
+      cp(I.msg, off[3], sizeof(double) * 2 * I.nb * cm * cm) != cudaSuccess ||
+      cp(I.vec, off[4], sizeof(double) * 2 * I.nb * cm) != cudaSuccess ||
+      cp(I.sigma, off[5], sizeof(double) * I.N) != cudaSuccess ||
+      cp(I.disc, off[6], sizeof(double) * I.nb) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "state copy");
+  return PEPO_OK;
+}
+
+pepo_status pepo_save_state(pepo_ctx* c, int inst, void* dev_buf, size_t bytes) {
+  pepo_status st = state_copy(c, inst, static_cast<char*>(dev_buf), bytes, true);
+  if (st == PEPO_OK) c->inst[inst].saved_steps = c->inst[inst].steps;
+  return st;
+}
+
+pepo_status pepo_load_state(pepo_ctx* c, int inst, const void* dev_buf, size_t bytes) {
+  pepo_status st = state_copy(c, inst, const_cast<char*>(static_cast<const char*>(dev_buf)), bytes, false);
+  if (st == PEPO_OK) c->inst[inst].steps = c->inst[inst].saved_steps;
+  return st;
 }
 
 // ------------------------------------------------------- learned warm start

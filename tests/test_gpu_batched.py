@@ -58,3 +58,18 @@ def test_graph_replay_matches_direct_launches():
     b.close()
     assert ga == gb
     assert la == lb                          # graph replays are counted launch by launch
+
+
+def test_state_snapshot_restores_the_trajectory():
+    import torch
+    cfg = pkg.Config(precision="tf32x3", **CFGS[0])
+    eng = pkg.Engine(cfg)
+    eng.trotter_step(3)
+    eng.bp_converge()
+    snap = torch.empty(eng.state_bytes(), dtype=torch.uint8, device="cuda")
+    eng.save_state(snap)
+    first = _trajectory(eng, 3)
+    eng.load_state(snap)
+    again = _trajectory(eng, 3)
+    eng.close()
+    assert first == again
