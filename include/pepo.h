@@ -112,6 +112,8 @@ typedef struct {
                               bit 2: a Jacobi SVD hit its sweep cap,
                               bit 3: gate rank above the bound (init only) */
   int steps;               /* Trotter steps taken so far */
+  int core_sweeps32_max;   /* max FP32 (preconditioning) Jacobi sweeps of a bond core, last step */
+  int core_sweeps64_max;   /* max FP64 Jacobi sweeps of a bond core, last step */
 } pepo_diag;
 
 /* Fill *cfg with the paper's defaults (Sec. 6: eps_cut 1e-11, tol 1e-5,

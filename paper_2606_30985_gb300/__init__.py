@@ -46,7 +46,8 @@ class _Diag(ctypes.Structure):
                 ("bp_delta", ctypes.c_double), ("bp1_sweeps", ctypes.c_int),
                 ("bp1_delta", ctypes.c_double), ("entropy_frac_max", ctypes.c_double),
                 ("trap_type1", ctypes.c_int), ("trap_type2", ctypes.c_int),
-                ("norm_exploded", ctypes.c_int), ("flags", ctypes.c_int), ("steps", ctypes.c_int)]
+                ("norm_exploded", ctypes.c_int), ("flags", ctypes.c_int), ("steps", ctypes.c_int),
+                ("core_sweeps32_max", ctypes.c_int), ("core_sweeps64_max", ctypes.c_int)]
 
 
 EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trotter_step",

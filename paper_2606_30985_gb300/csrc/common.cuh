@@ -175,7 +175,8 @@ struct CoreItem {
   int* nsv;                // number of singular values
   int inst;                // instance (its flag word is flags_base[inst])
   double eps_cut;
-  int mixed_svd;           // 1: FP32 Jacobi + FP64 Rayleigh step (FP32-storage modes)
+  int mixed_svd;           // 1: FP32 Jacobi preconditioning before FP64 Jacobi (FP32-storage modes)
+  int* sweeps;             // 2 ints: FP32 and FP64 Jacobi sweeps of this core
 };
 
 // ------------------------------------------------------------------- BP

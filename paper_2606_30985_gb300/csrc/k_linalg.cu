@@ -676,7 +676,8 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
     __shared__ int sh_capped32;   // a capped FP32 pass only costs FP64 sweeps below
     if (threadIdx.x == 0) sh_capped32 = 0;
     __syncthreads();
-    jacobi_svd<float>(T32, M, N, V32, 60, &sh_capped32, red);
+    const int sw32 = jacobi_svd<float>(T32, M, N, V32, 60, &sh_capped32, red);
+    if (threadIdx.x == 0 && it.sweeps) it.sweeps[0] = sw32;
     __syncthreads();
     for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) {
       const int j = (int)(e / M), i = (int)(e - (long long)j * M);
@@ -688,7 +689,11 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
     __syncthreads();
   }
   {   // FP64 one-sided Jacobi on Tcore (or on its FP32-preconditioned form)
-    jacobi_svd<double>(Tc, M, N, nullptr, 60, &sh_capped, red);
+    const int sw64 = jacobi_svd<double>(Tc, M, N, nullptr, 60, &sh_capped, red);
+    if (threadIdx.x == 0 && it.sweeps) {
+      it.sweeps[1] = sw64;
+      if (!it.mixed_svd) it.sweeps[0] = 0;
+    }
     __syncthreads();
     // singular values (column norms) and descending order
     for (int j = threadIdx.x; j < N; j += blockDim.x) {

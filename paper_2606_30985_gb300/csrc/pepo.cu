@@ -121,6 +121,7 @@ struct Inst {
   std::vector<void*> site_slab;
   double *lam = nullptr, *msg = nullptr, *hat = nullptr, *vec = nullptr, *vhat = nullptr;
   WsGeom* ws_geom = nullptr;          // 2 nb directed-bond descriptors of the warm-start features
+  int* core_sweeps = nullptr;         // 2 nb: FP32 / FP64 Jacobi sweeps of each bond core
   double *sigma = nullptr, *disc = nullptr, *svals = nullptr, *vs = nullptr, *fv = nullptr;
   double *ze = nullptr, *z2e = nullptr, *bethe_out = nullptr, *ptm = nullptr, *FA = nullptr, *FB = nullptr;
   int* nsv = nullptr;
@@ -377,6 +378,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
   I.FA = cv.take<double>(I.nb * (size_t)PEPO_RG * 16);
   I.FB = cv.take<double>(I.nb * (size_t)PEPO_RG * 16);
   I.ws_geom = cv.take<WsGeom>(2 * (size_t)I.nb);
+  I.core_sweeps = cv.take<int>(2 * (size_t)I.nb);
 
   auto chi_idx = [&](int b) { return I.chi0 + b; };
   auto msg_in = [&](int v, int b) {   // message into v on bond b
@@ -645,6 +647,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
         ci.inst = inst_id;
         ci.eps_cut = I.cfg.eps_cut;
         ci.mixed_svd = (c->tsize == 4) ? 1 : 0;
+        ci.sweeps = I.core_sweeps + 2 * (size_t)b;
         core_all.push_back(ci);
         moves.push_back(chi_idx(b));
         moves.push_back(I.pend0 + b);
@@ -1529,8 +1532,9 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
     Inst& I = c->inst[i];
     double out[8];
     std::vector<double> disc(I.nb), lam((size_t)I.nb * I.cfg.chi_max);
-    std::vector<int> chi(I.nb);
+    std::vector<int> chi(I.nb), csw(2 * (size_t)I.nb);
     if (cudaMemcpyAsync(out, I.bethe_out, sizeof(out), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(csw.data(), I.core_sweeps, sizeof(int) * csw.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(disc.data(), I.disc, sizeof(double) * I.nb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(lam.data(), I.lam, sizeof(double) * lam.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(chi.data(), c->d_ival + I.chi0, sizeof(int) * I.nb, cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -1570,6 +1574,10 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
       d.norm_exploded = (out[4] >= std::log(2.0)) ? 1 : 0;
       d.flags = flags[i];
       d.steps = I.steps;
+      for (int b = 0; b < I.nb; ++b) {
+        d.core_sweeps32_max = std::max(d.core_sweeps32_max, csw[2 * (size_t)b]);
+        d.core_sweeps64_max = std::max(d.core_sweeps64_max, csw[2 * (size_t)b + 1]);
+      }
     }
   }
   return PEPO_OK;
@@ -1693,6 +1701,7 @@ pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena, size
     ok = ok && cudaMemcpyAsync(I.msg, msg.data(), sizeof(double) * msg.size(), cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaMemsetAsync(I.sigma, 0, sizeof(double) * I.N, s) == cudaSuccess;
     ok = ok && cudaMemsetAsync(I.disc, 0, sizeof(double) * I.nb, s) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(I.core_sweeps, 0, sizeof(int) * 2 * I.nb, s) == cudaSuccess;
     ok = ok && cudaMemsetAsync(I.vec, 0, sizeof(double) * 2 * I.nb * chimax, s) == cudaSuccess;
     {
       // warm-start geometry of every directed bond (source = v1 for dir 0)
