@@ -529,9 +529,15 @@ cudaError_t launch_factor(const SiteFacItem* items, int n_items, int rmax, int n
 // ===================================================================== core
 // One-sided Jacobi (Hestenes) on the columns of A (m x n, column-major, m >= n),
 // accumulating V (n x n, column-major).  Returns the sweep count; sets
-// *capped when the sweep budget ran out.
+// *capped when the sweep budget ran out.  abs_rel > 0 also skips a pair whose
+// coupling |a_p . a_q| is below abs_rel ||A||_F^2: such a pair moves no
+// singular value by more than that absolute amount, and without the cut the
+// columns of tiny singular values (their content mostly rounding noise from
+// rotations with the large ones) are chased for many sweeps without ever
+// reaching relative orthogonality.
 template <typename R>
-__device__ int jacobi_svd(R* A, int m, int n, R* V, int max_sweeps, int* capped, double* red) {
+__device__ int jacobi_svd(R* A, int m, int n, R* V, int max_sweeps, int* capped, double* red,
+                          double abs_rel = 0.0) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   // V == nullptr: rotations are not accumulated (the caller recovers the other
   // side's vectors from a copy of the input)
@@ -558,6 +564,7 @@ __device__ int jacobi_svd(R* A, int m, int n, R* V, int max_sweeps, int* capped,
     __syncthreads();
   }
   const double negligible = (sizeof(R) == 4 ? 1e-13 : 1e-30) * fro;
+  const R abs_cut = (R)(abs_rel * fro);
   __shared__ int sh_rot;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
@@ -587,7 +594,7 @@ __device__ int jacobi_svd(R* A, int m, int n, R* V, int max_sweeps, int* capped,
         // rotation parameters in the working precision (FP64 division and
         // square root are slow on this part; FP32 columns need no more)
         if (ga != R(0) && al > (R)negligible && be > (R)negligible &&
-            fabs(ga) > (R)tol * sqrt(al * be)) {
+            fabs(ga) > (R)tol * sqrt(al * be) && fabs(ga) > abs_cut) {
           rotated = 1;
           const R zeta = (be - al) / (R(2) * ga);
           const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
@@ -661,17 +668,30 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
   __syncthreads();
   for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) V[e] = Tc[e];   // copy of Tcore
   __syncthreads();
+  // columns the FP64 Jacobi below works on (all N, or the mixed path's subspace)
+  int NK = N;
+  __shared__ double sh_fro;
   if (it.mixed_svd) {
     // FP32 one-sided Jacobi with accumulated right vectors V32 (in the R2
-    // block, free until the reconstruct step) as a preconditioner: Tc <- T V32
-    // in FP64, whose columns are orthogonal to FP32 accuracy, so the FP64
-    // Jacobi below converges in a couple of sweeps.  V32 is orthogonal to
-    // ~1e-7, which moves every singular value by ~1e-7 relative (tiny ones
-    // included) and the vectors by ~1e-7 / gap; the other side's vectors are
-    // recovered from the original T as in the FP64 path.
+    // block, free until the reconstruct step) finds the dominant right
+    // singular subspace to FP32 accuracy.  Its leading NK = chimax + margin
+    // directions are re-orthonormalised in FP64 (Cholesky QR; V32 itself is
+    // orthogonal only to ~1e-5 after thousands of FP32 rotations) and the FP64
+    // Jacobi then runs on T Q (M x NK) instead of T (M x N): the singular
+    // values of T Q are those of T restricted to an exactly orthonormal basis,
+    // so the kept values carry no error from V32's non-orthogonality, and the
+    // FP64 work (GB300's FP64 rate is ~1/64 of its FP32 rate) drops by
+    // (N / NK)^2 per sweep.  The columns are then nearly orthogonal, so few
+    // FP64 sweeps follow.  Values past NK (never kept: NK > chimax) keep their
+    // FP32 estimates for the diagnostic spectrum; the discarded weight of the
+    // truncation uses ||T||_F^2 computed in FP64.
     float* T32 = reinterpret_cast<float*>(R2o);
     float* V32 = T32 + (long long)M * N;
     for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) T32[e] = (float)Tc[e];
+    double f2 = 0.0;
+    for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) f2 = fma(Tc[e], Tc[e], f2);
+    f2 = block_sum(f2, red);
+    if (threadIdx.x == 0) sh_fro = f2;
     __syncthreads();
     __shared__ int sh_capped32;   // a capped FP32 pass only costs FP64 sweeps below
     if (threadIdx.x == 0) sh_capped32 = 0;
@@ -679,33 +699,98 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
     const int sw32 = jacobi_svd<float>(T32, M, N, V32, 60, &sh_capped32, red);
     if (threadIdx.x == 0 && it.sweeps) it.sweeps[0] = sw32;
     __syncthreads();
-    for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) {
-      const int j = (int)(e / M), i = (int)(e - (long long)j * M);
-      const float* vj = V32 + (long long)j * N;
+    // FP32 singular-value estimates (unsorted at sv[512 + j]) and their order
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      double s = 0.0;
+      const float* col = T32 + (long long)j * M;
+      for (int i = 0; i < M; ++i) s = fma((double)col[i], (double)col[i], s);
+      sv[512 + j] = sqrt(s);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      int rk = 0;
+      for (int i = 0; i < N; ++i) if (sv[512 + i] > sv[512 + j] || (sv[512 + i] == sv[512 + j] && i < j)) ++rk;
+      order[rk] = j;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < N; c += blockDim.x) sv[c] = sv[512 + order[c]];
+    __syncthreads();
+    for (int c = threadIdx.x; c < N; c += blockDim.x) sv[512 + c] = sv[c];   // sorted FP32 values
+    const int margin = it.chimax / 4 > 16 ? it.chimax / 4 : 16;
+    NK = it.chimax + margin < N ? it.chimax + margin : N;
+    // Q = leading NK columns of V32 in FP64 (N x NK, column-major, in Z)
+    double* Qk = Z;
+    for (long long e = threadIdx.x; e < (long long)N * NK; e += blockDim.x) {
+      const int c = (int)(e / N), i = (int)(e - (long long)c * N);
+      Qk[e] = (double)V32[(long long)order[c] * N + i];
+    }
+    __syncthreads();
+    // Cholesky QR: G = Q^T Q = L L^T (lower triangle of G in the Tc block), Q <- Q L^-T
+    double* G = Tc;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (long long pq = wid; pq < (long long)NK * NK; pq += nw) {
+      const int a = (int)(pq / NK), b = (int)(pq - (long long)a * NK);
+      if (b > a) continue;
+      const double* qa = Qk + (long long)a * N;
+      const double* qb = Qk + (long long)b * N;
       double acc = 0.0;
-      for (int k = 0; k < N; ++k) acc = fma(V[(long long)k * M + i], (double)vj[k], acc);
+      for (int i = lane; i < N; i += 32) acc = fma(qa[i], qb[i], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) G[(long long)a * NK + b] = acc;
+    }
+    __syncthreads();
+    for (int j = 0; j < NK; ++j) {
+      if (threadIdx.x == 0) G[(long long)j * NK + j] = sqrt(G[(long long)j * NK + j]);
+      __syncthreads();
+      const double djj = G[(long long)j * NK + j];
+      for (int i = j + 1 + threadIdx.x; i < NK; i += blockDim.x) G[(long long)i * NK + j] /= djj;
+      __syncthreads();
+      const int w = NK - j - 1;   // trailing lower triangle: rows i > j, columns j < l <= i
+      for (long long e = threadIdx.x; e < (long long)w * w; e += blockDim.x) {
+        const int i = j + 1 + (int)(e / w), l = j + 1 + (int)(e % w);
+        if (l <= i) G[(long long)i * NK + l] -= G[(long long)i * NK + j] * G[(long long)l * NK + j];
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {   // row i of Q solves x L^T = q
+      for (int c = 0; c < NK; ++c) {
+        double x = Qk[(long long)c * N + i];
+        const double* lc = G + (long long)c * NK;
+        for (int l = 0; l < c; ++l) x -= Qk[(long long)l * N + i] * lc[l];
+        Qk[(long long)c * N + i] = x / lc[c];
+      }
+    }
+    __syncthreads();
+    // Tc <- T Q (M x NK, column-major), T = the copy in V
+    for (long long e = threadIdx.x; e < (long long)M * NK; e += blockDim.x) {
+      const int c = (int)(e / M), i = (int)(e - (long long)c * M);
+      const double* qc = Qk + (long long)c * N;
+      double acc = 0.0;
+      for (int k = 0; k < N; ++k) acc = fma(V[(long long)k * M + i], qc[k], acc);
       Tc[e] = acc;
     }
     __syncthreads();
   }
-  {   // FP64 one-sided Jacobi on Tcore (or on its FP32-preconditioned form)
-    const int sw64 = jacobi_svd<double>(Tc, M, N, nullptr, 60, &sh_capped, red);
+  {   // FP64 one-sided Jacobi on Tcore (or on its restriction T Q)
+    // mixed path: the rotations W64 (NK x NK) are accumulated in the V block
+    // (the copy of T is no longer needed); the right vectors are then Q W64
+    const int sw64 = jacobi_svd<double>(Tc, M, NK, it.mixed_svd ? V : nullptr, 60, &sh_capped, red, 1e-17);
     if (threadIdx.x == 0 && it.sweeps) {
       it.sweeps[1] = sw64;
       if (!it.mixed_svd) it.sweeps[0] = 0;
     }
     __syncthreads();
     // singular values (column norms) and descending order
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    for (int j = threadIdx.x; j < NK; j += blockDim.x) {
       double s = 0.0;
       const double* col = Tc + (long long)j * M;
       for (int i = 0; i < M; ++i) s = fma(col[i], col[i], s);
       sv[j] = sqrt(s);
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    for (int j = threadIdx.x; j < NK; j += blockDim.x) {
       int rk = 0;
-      for (int i = 0; i < N; ++i) if (sv[i] > sv[j] || (sv[i] == sv[j] && i < j)) ++rk;
+      for (int i = 0; i < NK; ++i) if (sv[i] > sv[j] || (sv[i] == sv[j] && i < j)) ++rk;
       order[rk] = j;
     }
     __syncthreads();
@@ -717,11 +802,12 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
   if (threadIdx.x == 0) {
     int cnt = 0;
     double tot = 0.0;
-    for (int i = 0; i < N; ++i) {
+    for (int i = 0; i < NK; ++i) {
       double s = sv[order[i]];
       tot += s * s;
       if (s >= it.eps_cut * s0 && s > 0.0) ++cnt;
     }
+    if (it.mixed_svd) tot = sh_fro;
     int chi = cnt < it.chimax ? cnt : it.chimax;
     if (chi < 1) chi = 1;
     double kept = 0.0, ksum = 0.0;
@@ -736,7 +822,7 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
     if (sh_capped) atomicOr(flags, 4);
     const double nrm = sqrt(kept);
     for (int i = 0; i < it.chimax; ++i) it.lam[i] = (i < chi) ? sv[order[i]] / nrm : 0.0;
-    for (int i = 0; i < N; ++i) it.svals[i] = sv[order[i]];
+    for (int i = 0; i < N; ++i) it.svals[i] = i < NK ? sv[order[i]] : sv[512 + i];
     // stored psi = true psi * exp(-sigma); the raw sqrt(S) split gives both
     // sites half of the pair's combined scale plus the normalisation of W
     const double ls = 0.5 * log(ksum) + 0.5 * (*it.sigma1 + *it.sigma2);
@@ -752,6 +838,25 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
     double x = (i == j && i < chi) ? it.lam[i] : 0.0;
     it.msg12[e] = x;
     it.msg21[e] = x;
+  }
+  if (it.mixed_svd) {
+    // Right (N-space) vectors of the kept pairs: v_c = Q W64 e_order[c] (N x chi,
+    // row-major by N index), first into the R2 block, then into the V block
+    // once W64 is consumed.  These are the Ritz vectors of the subspace, so
+    // T v_c = s_c u_c holds exactly for every kept pair; recovering them as
+    // T^T u_c / s_c instead would divide the subspace's FP32-level residual
+    // by s_c^2 for values near the FP32 resolution (~1e-7 of the largest).
+    double* Vr = R2o;
+    for (long long e = threadIdx.x; e < (long long)N * chi; e += blockDim.x) {
+      const int a = (int)(e / chi), c = (int)(e - (long long)a * chi);
+      const double* w = V + (long long)order[c] * NK;
+      double acc = 0.0;
+      for (int l = 0; l < NK; ++l) acc = fma(Z[(long long)l * N + a], w[l], acc);
+      Vr[e] = acc;
+    }
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)N * chi; e += blockDim.x) V[e] = Vr[e];
+    __syncthreads();
   }
   // For each side: Zs = T_s11^{-1} (singular vectors of that side) sqrt(s) / sqrt(sum s)
   // side 1 vectors: left vectors of Tcore (rows of R1 space, length k1)
@@ -774,6 +879,8 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
       double x;
       if (from_cols) {
         x = s > 0.0 ? Tc[(long long)j * M + a] / s : 0.0;
+      } else if (it.mixed_svd) {
+        x = V[(long long)a * chi + c];                  // Ritz right vector (above)
       } else {
         // other side: (copy^T u_j)_a / s_j, copy = Tcore column-major M x N, u_j = column j / s_j
         double acc = 0.0;

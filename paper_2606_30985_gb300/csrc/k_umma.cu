@@ -120,6 +120,27 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros
+// without reading the source
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most n of this thread's copy groups are pending (n <= 7)
+__device__ __forceinline__ void cp_async_wait(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+    case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+    case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
+  }
+}
+
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -596,9 +617,17 @@ __device__ inline void gram_dims(const GramLegItem& it, void* const* ptrs, const
   G.partial = it.partial;
 }
 
+// Converter raw staging: each converter thread copies its four 16-byte
+// pieces of a chunk with cp.async into its own slots of a raw stage (piece u
+// of thread t at (u kConv + t) 16 bytes, then one FP32 weight per thread),
+// kRawMax chunks ahead of the chunk it converts, so the loads of several
+// chunks are in flight without holding registers.
+constexpr int kRawMax = 6;
+constexpr size_t kRawBytes = (size_t)kConv * 4 * 16 + (size_t)kConv * 4;
+
 struct GramSmem {
-  int f8max, stages, ld;
-  size_t stage_bytes, acc_off, bar_off, total;
+  int f8max, stages, ld, raw;
+  size_t stage_bytes, raw_off, acc_off, bar_off, total;
 };
 __host__ __device__ inline GramSmem gram_smem(int chimax) {
   GramSmem p;
@@ -607,11 +636,13 @@ __host__ __device__ inline GramSmem gram_smem(int chimax) {
   p.stage_bytes = (size_t)(2 * p.f8max > kM ? 2 * p.f8max : kM) * 128;
   p.ld = p.f8max + 1;                                               // odd row stride (words)
   const size_t acc_bytes = 2 * (size_t)p.f8max * p.ld * 4;          // sum + compensation
-  const size_t pad = 0;
   const size_t budget = 227 * 1024 - 1024 - 8 * (kMaxItems + 1) - 512 - 1024;
-  p.stages = (int)((budget - acc_bytes - pad) / p.stage_bytes);
-  if (p.stages > 4) p.stages = 4;
-  p.acc_off = p.stages * p.stage_bytes + pad;
+  p.stages = 2;
+  const size_t fixed = acc_bytes + 2 * p.stage_bytes;
+  p.raw = fixed < budget ? (int)((budget - fixed) / kRawBytes) : 0;
+  if (p.raw > kRawMax) p.raw = kRawMax;
+  p.raw_off = p.stages * p.stage_bytes;
+  p.acc_off = p.raw_off + (size_t)p.raw * kRawBytes;
   p.bar_off = p.acc_off + acc_bytes;
   p.total = p.bar_off + 512 + 8 * (size_t)(kMaxItems + 1) + 1024 + 1024;
   return p;
@@ -782,8 +813,9 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
     }
   } else if (warp >= 8) {
     // ------------------------------------------------------------ converters
-    // Loads (and the weight of the thread's column group) run one chunk
-    // ahead of the shared-memory stores (register pair v0, v1).
+    // Loads run P.raw chunks ahead of the conversion through this thread's
+    // cp.async slots of the raw stages; the weight of the thread's column
+    // group for a chunk is stored beside its pieces.
     const int cw = (tid - 256) >> 5;
     const int kq = 4 * (cw & 1) + (lane >> 3);     // this thread's 4-wide K group of a chunk
     const int i8_0 = cw >> 1;                      // row groups i8_0 + 4 u, u = 0..3
@@ -866,11 +898,16 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
       }
     };
     enter_unit();
-    auto load_next = [&](float4* v, float& w) {
-#pragma unroll
-      for (int u4 = 0; u4 < 4; ++u4) v[u4] = make_float4(0.f, 0.f, 0.f, 0.f);
-      w = 0.f;
-      if (!l_live) return;
+    const int ct = tid - 256;
+    unsigned char* raw = smem + P.raw_off;
+    const int DR = P.raw;
+    // copy the chunk at the load cursor into raw stage rs (one copy group)
+    auto issue_next = [&](int rs) {
+      unsigned char* rb = raw + (size_t)rs * kRawBytes;
+      if (!l_live) {
+        cp_async_commit();   // empty group: keeps one group per chunk slot
+        return;
+      }
       const GramDims& G = lg.G;
       long long o, q;
       bool kvalid;
@@ -883,15 +920,21 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
         q = (4 * kq) % G.Q;
         kvalid = (4 * kq) / G.Q < G.opc && o < G.O;
       }
+      float w = 0.f;
+      const float* base = G.X;
       if (kvalid) {
         w = weighted ? odo_w(od, 0, G.k) * odo_w(id_, G.k + 1, G.nlegs) : 1.f;
-        const float* base = G.X + (o * G.F) * G.Q + q;
-#pragma unroll
-        for (int u4 = 0; u4 < 4; ++u4) {
-          const int i = 8 * (i8_0 + 4 * u4) + il;
-          if (i < G.F) v[u4] = __ldg(reinterpret_cast<const float4*>(base + (long long)i * G.Q));
-        }
+        base = G.X + (o * G.F) * G.Q + q;
       }
+#pragma unroll
+      for (int u4 = 0; u4 < 4; ++u4) {
+        const int i = 8 * (i8_0 + 4 * u4) + il;
+        const bool ok = kvalid && i < G.F;
+        cp_async16(rb + ((size_t)u4 * kConv + ct) * 16, ok ? (const void*)(base + (long long)i * G.Q) : (const void*)G.X,
+                   ok ? 16 : 0);
+      }
+      *reinterpret_cast<float*>(rb + (size_t)kConv * 64 + (size_t)ct * 4) = w;
+      cp_async_commit();
       if (++lcur < lg.c1) {
         if (G.wide) {
           if (++lqb == G.qpc) {
@@ -913,22 +956,26 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
       lu += gridDim.x;
       enter_unit();
     };
-    float4 v0[4], v1[4];
-    float w0, w1;
-    load_next(v0, w0);
+    for (int d = 0; d < DR; ++d) issue_next(d);
     // store cursor
     GramCursor g;
     g.item = -1;
     long long cc = 0, u = blockIdx.x, c = 0;
     bool live = u < U;
     if (live) { gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max); c = g.c; }
-    // one chunk: loads for the next chunk into vl / wl, store vs / ws (ring
-    // rotated by unrolling, not by register copies)
-    auto step = [&](float4 (&vl)[4], float& wl, float4 (&vs)[4], float ws) -> bool {
-      load_next(vl, wl);
+    // one chunk: wait for this thread's copies of chunk cc, convert it into
+    // the operand stage, then refill its raw stage with chunk cc + DR
+    while (live) {
+      const int rs = (int)(cc % DR);
+      cp_async_wait(DR - 1);
+      const unsigned char* rb = raw + (size_t)rs * kRawBytes;
+      float4 vs[4];
+#pragma unroll
+      for (int u4 = 0; u4 < 4; ++u4) vs[u4] = *reinterpret_cast<const float4*>(rb + ((size_t)u4 * kConv + ct) * 16);
+      const float ws = *reinterpret_cast<const float*>(rb + (size_t)kConv * 64 + (size_t)ct * 4);
       const int F8 = g.G.F8;
       const int s = (int)(cc % NS);
-      if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) return false;
+      if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) break;
       unsigned char* st = Xs + (size_t)s * P.stage_bytes;
 #pragma unroll
       for (int u4 = 0; u4 < 4; ++u4) {
@@ -943,18 +990,15 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
       }
       fence_async_smem();
       warp_arrive(&bars->full[s]);
+      issue_next(rs);
       ++cc;
-      if (++c < g.c1) return true;
+      if (++c < g.c1) continue;
       u += gridDim.x;
-      if (u >= U) return false;
+      if (u >= U) break;
       gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max);
       c = g.c;
-      return true;
-    };
-    while (live) {
-      if (!step(v1, w1, v0, w0)) break;
-      if (!step(v0, w0, v1, w1)) break;
     }
+    cp_async_wait(0);   // no copy may land after the kernel's shared memory is gone
   }
   tc_before();
   __syncthreads();
@@ -1384,7 +1428,7 @@ cudaError_t launch_gram_umma(const GramLegItem* items, int n_items, int splits_m
   if (n_items == 0) return cudaSuccess;
   if (!umma_supported(chimax)) return cudaErrorInvalidValue;
   const um::GramSmem P = um::gram_smem(chimax);
-  if (P.stages < 2) return cudaErrorInvalidValue;
+  if (P.raw < 1) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(um::k_gram_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.total);
   if (e != cudaSuccess) return e;
   for (int i0 = 0; i0 < n_items; i0 += um::kMaxItems) {
