@@ -361,7 +361,9 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
     if (lane == 0) {
       LegCursor c;
       bool live = cursor_start(c, toff, n_items, t0, t1, items, ptrs, ival);
-      long long cc = 0, tc = 0;
+      long long tc = 0;
+      int st_i = 0;            // operand stage and its phase parity (advanced per chunk)
+      uint32_t st_ph = 0;
       int item_n = 0;
       bool ok = true;
       if (live) ok = mbar_wait(&bars->bfull, 0, abort_flag, err);
@@ -374,9 +376,10 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
         const uint32_t bblk = (uint32_t)(2 * N16) * 128;   // B block per K chunk
         const uint32_t id_wide = idesc_tf32(kM, 2 * N16), id_half = idesc_tf32(kM, N16);
         const int nkc = (K8 + kKC - 1) / kKC;
-        for (int kc = 0; kc < nkc && ok; ++kc, ++cc) {
-          const int s = (int)(cc % NS);
-          if (!mbar_wait(&bars->full[s], (uint32_t)((cc / NS) & 1), abort_flag, err)) { ok = false; break; }
+        for (int kc = 0; kc < nkc && ok; ++kc) {
+          const int s = st_i;
+          if (!mbar_wait(&bars->full[s], st_ph, abort_flag, err)) { ok = false; break; }
+          if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
           tc_after();
           const uint32_t a_hi = su32(As + (size_t)s * P.stage_bytes);
           const uint32_t a_lo = a_hi + (uint32_t)(P.stage_bytes / 2);
@@ -521,7 +524,8 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
     // store cursor
     LegCursor c;
     bool live = cursor_start(c, toff, n_items, t0, t1, items, ptrs, ival);
-    long long cc = 0;
+    int st_i = 0;              // operand stage and its phase parity
+    uint32_t st_ph = 0;
     int item_n = 0, kc = 0;
     bool need_b = true;
     // one chunk: issue the loads two chunks ahead into vl, convert and store
@@ -551,8 +555,9 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
         warp_arrive(&bars->bfull);
         need_b = false;
       }
-      const int s = (int)(cc % NS);
-      if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) return false;
+      const int s = st_i;
+      if (!warp_wait(&bars->empty[s], st_ph ^ 1u, abort_flag, err)) return false;
+      if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
       unsigned char* hi = As + (size_t)s * P.stage_bytes;
       unsigned char* lo = hi + P.stage_bytes / 2;
 #pragma unroll
@@ -565,7 +570,6 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
       }
       fence_async_smem();
       warp_arrive(&bars->full[s]);
-      ++cc;
       if (++kc < (L.K8 + kKC - 1) / kKC) return true;
       kc = 0;
       if (c.left == 1) return false;
@@ -600,14 +604,20 @@ struct GramDims {
 __device__ inline void gram_dims(const GramLegItem& it, void* const* ptrs, const int* ival, int splits_max,
                                  GramDims& G) {
   G.nlegs = it.x.nlegs;
-  for (int k = 0; k < PEPO_MAXLEG; ++k) G.d[k] = (k < it.x.nlegs) ? ival[it.x.dim[k]] : 1;
   G.k = it.leg;
-  G.F = G.d[G.k];
-  G.F8 = round_up(G.F, 8);
+  G.F = 1;
   G.O = 1;
   G.Q = 4;
-  for (int i = 0; i < G.k; ++i) G.O *= G.d[i];
-  for (int i = G.k + 1; i < G.nlegs; ++i) G.Q *= G.d[i];
+  // constant indices only (unrolled selects), so the dims stay in registers
+#pragma unroll
+  for (int k = 0; k < PEPO_MAXLEG; ++k) {
+    const int dk = (k < it.x.nlegs) ? ival[it.x.dim[k]] : 1;
+    G.d[k] = dk;
+    if (k == G.k) G.F = dk;
+    else if (k < G.k) G.O *= dk;
+    else if (k < G.nlegs) G.Q *= dk;
+  }
+  G.F8 = round_up(G.F, 8);
   G.NC = gram_leg_chunks(G.O, G.Q);
   G.S = gram_leg_splits_k(G.O * G.Q, splits_max);
   G.wide = G.Q >= kKC;
@@ -619,11 +629,12 @@ __device__ inline void gram_dims(const GramLegItem& it, void* const* ptrs, const
 
 // Converter raw staging: each converter thread copies its four 16-byte
 // pieces of a chunk with cp.async into its own slots of a raw stage (piece u
-// of thread t at (u kConv + t) 16 bytes, then one FP32 weight per thread),
+// of thread t at (u kConv + t) 16 bytes, then one FP32 weight and the item's
+// padded row count per thread),
 // kRawMax chunks ahead of the chunk it converts, so the loads of several
 // chunks are in flight without holding registers.
 constexpr int kRawMax = 6;
-constexpr size_t kRawBytes = (size_t)kConv * 4 * 16 + (size_t)kConv * 4;
+constexpr size_t kRawBytes = (size_t)kConv * 4 * 16 + (size_t)kConv * 8;   // pieces, weight, F8
 
 struct GramSmem {
   int f8max, stages, ld, raw;
@@ -680,6 +691,154 @@ struct Odo {
   int dig[PEPO_MAXLEG];
 };
 
+// Load side of the Gram converters: the cursor of one converter thread over
+// the chunks of its CTA's units (items x splits), kept in registers.  Per
+// chunk, issue() copies the thread's column group (4 K values) of its four
+// rows with cp.async into its slots of a raw stage, with the group's weight
+// and the item's padded row count F8 (0 once the CTA's work is done).  The
+// flattened index g of the column group over the non-free legs (the outer
+// legs of o, then the legs of q / 4) is kept as three mixed-radix digits
+// advanced by small additions; the source pointer advances incrementally; the
+// weights of the digits are loaded one chunk before they are used (indices
+// clamped into the tables: the value only matters for valid columns, whose
+// digits are in range).
+struct GramLoader {
+  int kq, row0;
+  long long lu, lcur, lend, stride_u;
+  bool live;
+  int item, F, F8, Q4, qpc, opc;
+  bool wide;
+  long long Q, O, FQ;
+  const float* X;
+  long long roff0, roff1, roff2, roff3;
+  bool rv0, rv1, rv2, rv3;
+  int rd0, rd1, rd2, dg0, dg1, dg2, lqb;
+  long long lo;
+  const double *ws0, *ws1, *ws2;
+  float pw0, pw1, pw2;
+  const float* lp;
+
+  __device__ __forceinline__ void init(int kq_, int row0_, long long first_unit) {
+    kq = kq_;
+    row0 = row0_;
+    lu = first_unit;
+    stride_u = gridDim.x;
+    item = -1;
+    live = false;
+    pw0 = pw1 = pw2 = 1.f;
+  }
+  __device__ __forceinline__ void dig_set(long long gv) {
+    dg2 = (int)(gv % rd2); gv /= rd2;
+    dg1 = (int)(gv % rd1); gv /= rd1;
+    dg0 = (int)gv;
+  }
+  __device__ __forceinline__ void dig_add(int inc) {
+    dg2 += inc;
+    while (dg2 >= rd2) { dg2 -= rd2; ++dg1; }
+    while (dg1 >= rd1) { dg1 -= rd1; ++dg0; }
+  }
+  __device__ __forceinline__ void prefetch_w() {
+    pw0 = ws0 ? (float)__ldg(ws0 + min(dg0, rd0 - 1)) : 1.f;
+    pw1 = ws1 ? (float)__ldg(ws1 + min(dg1, rd1 - 1)) : 1.f;
+    pw2 = ws2 ? (float)__ldg(ws2 + min(dg2, rd2 - 1)) : 1.f;
+  }
+  // position the cursor at the first chunk of unit lu (item constants are
+  // reloaded when the item changes)
+  __device__ __forceinline__ void enter_unit(const GramLegItem* items, int n_items, const long long* uoff, long long U,
+                                             void* const* ptrs, const int* ival, int splits_max) {
+    live = lu < U;
+    if (!live) return;
+    int i = 0;
+    while (i + 1 < n_items && uoff[i + 1] <= lu) ++i;
+    if (i != item) {
+      item = i;
+      GramDims G;
+      gram_dims(items[i], ptrs, ival, splits_max, G);
+      F = G.F; F8 = G.F8; Q = G.Q; O = G.O; X = G.X; wide = G.wide;
+      Q4 = (int)(G.Q / 4);
+      qpc = (int)G.qpc; opc = G.opc;
+      FQ = (long long)G.F * G.Q;
+      const int r0 = row0, r1 = row0 + 32, r2 = row0 + 64, r3 = row0 + 96;
+      roff0 = (long long)r0 * Q; roff1 = (long long)r1 * Q; roff2 = (long long)r2 * Q; roff3 = (long long)r3 * Q;
+      rv0 = r0 < F; rv1 = r1 < F; rv2 = r2 < F; rv3 = r3 < F;
+      // digit slots: the non-free legs in layout order, right-aligned
+      int slot = 2;
+      rd0 = rd1 = rd2 = 1;
+      ws0 = ws1 = ws2 = nullptr;
+      const GramLegItem& it = items[i];
+#pragma unroll
+      for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
+        if (uu >= G.nlegs || uu == G.k) continue;
+        const double* w = it.sw[uu];
+        if (slot == 2) { rd2 = G.d[uu]; ws2 = w; }
+        else if (slot == 1) { rd1 = G.d[uu]; ws1 = w; }
+        else { rd0 = G.d[uu]; ws0 = w; }
+        --slot;
+      }
+    }
+    const long long NC = gram_leg_chunks(O, Q);
+    const int S = gram_leg_splits_k(O * Q, splits_max);
+    const int sp = (int)(lu - uoff[item]);
+    lcur = NC * sp / S;
+    lend = NC * (sp + 1) / S;
+    if (wide) {
+      lo = lcur / qpc;
+      lqb = (int)(lcur - lo * qpc);
+      dig_set(lo * Q4 + (long long)lqb * 8 + kq);
+      lp = X + lo * FQ + (long long)lqb * kKC + 4 * kq;
+    } else {
+      lo = lcur * opc;
+      const int ooff = kq / Q4, q4 = kq - ooff * Q4;
+      dig_set((lo + ooff) * Q4 + q4);
+      lp = X + (lo + ooff) * FQ + 4 * q4;
+    }
+    prefetch_w();
+  }
+  // copy the chunk at the cursor into raw stage rb (one copy group) and
+  // advance; returns true when the unit is finished (the caller then enters
+  // the next one)
+  __device__ __forceinline__ bool issue(unsigned char* rb, int ct) {
+    int* f8slot = reinterpret_cast<int*>(rb + (size_t)kConv * 68 + (size_t)ct * 4);
+    if (!live) {
+      *f8slot = 0;
+      cp_async_commit();   // empty group: keeps one group per chunk slot
+      return false;
+    }
+    const bool kvalid = wide ? (lqb * 8 + kq < Q4) : (kq / Q4 < opc && lo + kq / Q4 < O);
+    const float w = kvalid ? pw0 * pw1 * pw2 : 0.f;
+    const void* z = (const void*)X;
+    cp_async16(rb + ((size_t)0 * kConv + ct) * 16, (kvalid && rv0) ? (const void*)(lp + roff0) : z, (kvalid && rv0) ? 16 : 0);
+    cp_async16(rb + ((size_t)1 * kConv + ct) * 16, (kvalid && rv1) ? (const void*)(lp + roff1) : z, (kvalid && rv1) ? 16 : 0);
+    cp_async16(rb + ((size_t)2 * kConv + ct) * 16, (kvalid && rv2) ? (const void*)(lp + roff2) : z, (kvalid && rv2) ? 16 : 0);
+    cp_async16(rb + ((size_t)3 * kConv + ct) * 16, (kvalid && rv3) ? (const void*)(lp + roff3) : z, (kvalid && rv3) ? 16 : 0);
+    *reinterpret_cast<float*>(rb + (size_t)kConv * 64 + (size_t)ct * 4) = w;
+    *f8slot = F8;
+    cp_async_commit();
+    if (++lcur < lend) {
+      if (wide) {
+        if (++lqb == qpc) {
+          const int inc = Q4 - 8 * (qpc - 1);
+          lqb = 0;
+          ++lo;
+          lp += FQ - (long long)(qpc - 1) * kKC;
+          dig_add(inc);
+        } else {
+          lp += kKC;
+          dig_add(8);
+        }
+      } else {
+        lo += opc;
+        lp += (long long)opc * FQ;
+        dig_add(opc * Q4);
+      }
+      prefetch_w();
+      return false;
+    }
+    lu += stride_u;
+    return true;
+  }
+};
+
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, int chimax, void* const* ptrs,
             const int* __restrict__ ival, int* err) {
@@ -726,7 +885,9 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
     if (lane == 0) {
       GramCursor g;
       g.item = -1;
-      long long cc = 0, rc = 0;
+      long long rc = 0;
+      int st_i = 0;            // operand stage and its phase parity (advanced per chunk)
+      uint32_t st_ph = 0;
       bool ok = true;
       for (long long u = blockIdx.x; u < U && ok; u += gridDim.x) {
         gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max);
@@ -738,9 +899,10 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
           tc_after();
           const uint32_t d_tmem = tmem + (uint32_t)(b * 256);
           const long long cend = min(g.c1, c + kRun);
-          for (long long cr = c; cr < cend; ++cr, ++cc) {
-            const int s = (int)(cc % NS);
-            if (!mbar_wait(&bars->full[s], (uint32_t)((cc / NS) & 1), abort_flag, err)) { ok = false; break; }
+          for (long long cr = c; cr < cend; ++cr) {
+            const int s = st_i;
+            if (!mbar_wait(&bars->full[s], st_ph, abort_flag, err)) { ok = false; break; }
+            if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
             tc_after();
             const uint32_t x0 = su32(Xs + (size_t)s * P.stage_bytes);
 #pragma unroll
@@ -813,169 +975,45 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
     }
   } else if (warp >= 8) {
     // ------------------------------------------------------------ converters
-    // Loads run P.raw chunks ahead of the conversion through this thread's
-    // cp.async slots of the raw stages; the weight of the thread's column
-    // group for a chunk is stored beside its pieces.
-    const int cw = (tid - 256) >> 5;
+    // Load side: this thread's column group of each chunk (4 K values) for
+    // its four rows is copied with cp.async into its own slots of a raw stage,
+    // P.raw chunks ahead of the conversion, together with the group's weight
+    // and the item's padded row count F8 (0 marks the end of the CTA's work).
+    // All cursor state lives in registers: the flattened index g of the
+    // column group over the non-free legs (outer legs of o, then the legs of
+    // q / 4) is kept as three mixed-radix digits advanced by small additions,
+    // and the source pointer advances incrementally.
+    const int ct = tid - 256, cw = ct >> 5;
     const int kq = 4 * (cw & 1) + (lane >> 3);     // this thread's 4-wide K group of a chunk
     const int i8_0 = cw >> 1;                      // row groups i8_0 + 4 u, u = 0..3
     const int il = lane & 7;
-    // load cursor: the chunk's (o, q) advance incrementally; the weight
-    // prod_{u != k} sw[u][j_u] of this thread's 4-wide column group comes
-    // from digit counters of the outer legs (o) and inner legs (q / 4)
-    GramCursor lg;
-    lg.item = -1;
-    long long lu = blockIdx.x, lcur = 0;
-    bool l_live = false;
-    int wt_item = -1;
-    const double* sw[PEPO_MAXLEG];
-    int dd[PEPO_MAXLEG];
-    bool weighted = false;
-    long long lo_ = 0;      // o of the current chunk (wide) or of its first column group (narrow)
-    long long lqb = 0;      // chunk index within o (wide)
-    int od[PEPO_MAXLEG];    // digits of this thread's o (outer legs)
-    int id_[PEPO_MAXLEG];   // digits of this thread's q / 4 (inner legs)
-    // add `inc` to the digit counter of legs [lo, hi) (row-major, last fastest)
-    auto odo_add = [&](int* dig, int lo, int hi, long long inc) {
-      long long carry = inc;
-#pragma unroll
-      for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
-        if (uu >= lo && uu < hi && carry) {
-          const long long t = dig[uu] + carry;
-          carry = t / dd[uu];
-          dig[uu] = (int)(t - carry * dd[uu]);
-        }
-      }
-    };
-    auto odo_set = [&](int* dig, int lo, int hi, long long val) {
-#pragma unroll
-      for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
-        if (uu >= lo && uu < hi) {
-          dig[uu] = (int)(val % dd[uu]);
-          val /= dd[uu];
-        } else {
-          dig[uu] = 0;
-        }
-      }
-    };
-    auto odo_w = [&](const int* dig, int lo, int hi) {
-      float w = 1.f;
-#pragma unroll
-      for (int uu = 0; uu < PEPO_MAXLEG; ++uu)
-        if (uu >= lo && uu < hi && sw[uu]) w *= (float)sw[uu][dig[uu]];
-      return w;
-    };
-    auto enter_unit = [&]() {
-      l_live = lu < U;
-      if (!l_live) return;
-      gram_unit(lg, lu, uoff, n_items, items, ptrs, ival, splits_max);
-      const GramDims& G = lg.G;
-      lcur = lg.c;
-      if (lg.item != wt_item) {
-        const GramLegItem& it = items[lg.item];
-        weighted = false;
-#pragma unroll
-        for (int uu = 0; uu < PEPO_MAXLEG; ++uu) {
-          sw[uu] = (uu < G.nlegs && uu != G.k) ? it.sw[uu] : nullptr;
-          dd[uu] = G.d[uu];
-          weighted |= sw[uu] != nullptr;
-        }
-        wt_item = lg.item;
-      }
-      if (G.wide) {
-        lo_ = lcur / G.qpc;
-        lqb = lcur - lo_ * G.qpc;
-        if (weighted) {
-          odo_set(od, 0, G.k, lo_);
-          odo_set(id_, G.k + 1, G.nlegs, (lqb * kKC + 4 * kq) >> 2);
-        }
-      } else {
-        lo_ = lcur * G.opc;
-        if (weighted) {
-          odo_set(od, 0, G.k, lo_ + (4 * kq) / G.Q);
-          odo_set(id_, G.k + 1, G.nlegs, ((4 * kq) % G.Q) >> 2);   // fixed per thread
-        }
-      }
-    };
-    enter_unit();
-    const int ct = tid - 256;
     unsigned char* raw = smem + P.raw_off;
     const int DR = P.raw;
-    // copy the chunk at the load cursor into raw stage rs (one copy group)
+    GramLoader ld;
+    ld.init(kq, 8 * i8_0 + il, blockIdx.x);
+    ld.enter_unit(items, n_items, uoff, U, ptrs, ival, splits_max);
     auto issue_next = [&](int rs) {
-      unsigned char* rb = raw + (size_t)rs * kRawBytes;
-      if (!l_live) {
-        cp_async_commit();   // empty group: keeps one group per chunk slot
-        return;
-      }
-      const GramDims& G = lg.G;
-      long long o, q;
-      bool kvalid;
-      if (G.wide) {
-        o = lo_;
-        q = lqb * kKC + 4 * kq;
-        kvalid = q < G.Q;
-      } else {
-        o = lo_ + (4 * kq) / G.Q;
-        q = (4 * kq) % G.Q;
-        kvalid = (4 * kq) / G.Q < G.opc && o < G.O;
-      }
-      float w = 0.f;
-      const float* base = G.X;
-      if (kvalid) {
-        w = weighted ? odo_w(od, 0, G.k) * odo_w(id_, G.k + 1, G.nlegs) : 1.f;
-        base = G.X + (o * G.F) * G.Q + q;
-      }
-#pragma unroll
-      for (int u4 = 0; u4 < 4; ++u4) {
-        const int i = 8 * (i8_0 + 4 * u4) + il;
-        const bool ok = kvalid && i < G.F;
-        cp_async16(rb + ((size_t)u4 * kConv + ct) * 16, ok ? (const void*)(base + (long long)i * G.Q) : (const void*)G.X,
-                   ok ? 16 : 0);
-      }
-      *reinterpret_cast<float*>(rb + (size_t)kConv * 64 + (size_t)ct * 4) = w;
-      cp_async_commit();
-      if (++lcur < lg.c1) {
-        if (G.wide) {
-          if (++lqb == G.qpc) {
-            lqb = 0;
-            ++lo_;
-            if (weighted) {
-              odo_add(od, 0, G.k, 1);
-              odo_set(id_, G.k + 1, G.nlegs, kq);
-            }
-          } else if (weighted) {
-            odo_add(id_, G.k + 1, G.nlegs, kKC / 4);
-          }
-        } else {
-          lo_ += G.opc;
-          if (weighted) odo_add(od, 0, G.k, G.opc);
-        }
-        return;
-      }
-      lu += gridDim.x;
-      enter_unit();
+      if (ld.issue(raw + (size_t)rs * kRawBytes, ct))
+        ld.enter_unit(items, n_items, uoff, U, ptrs, ival, splits_max);
     };
     for (int d = 0; d < DR; ++d) issue_next(d);
-    // store cursor
-    GramCursor g;
-    g.item = -1;
-    long long cc = 0, u = blockIdx.x, c = 0;
-    bool live = u < U;
-    if (live) { gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max); c = g.c; }
-    // one chunk: wait for this thread's copies of chunk cc, convert it into
-    // the operand stage, then refill its raw stage with chunk cc + DR
-    while (live) {
-      const int rs = (int)(cc % DR);
+    // conversion side: wait for this thread's copies of chunk cc, weight,
+    // split and store into the operand stage, then refill the raw stage
+    int rs = 0;                // raw stage of the chunk being converted
+    int st_i = 0;              // operand stage and its phase parity
+    uint32_t st_ph = 0;
+    while (true) {
       cp_async_wait(DR - 1);
       const unsigned char* rb = raw + (size_t)rs * kRawBytes;
+      const int F8 = *reinterpret_cast<const int*>(rb + (size_t)kConv * 68 + (size_t)ct * 4);
+      if (F8 == 0) break;
       float4 vs[4];
 #pragma unroll
       for (int u4 = 0; u4 < 4; ++u4) vs[u4] = *reinterpret_cast<const float4*>(rb + ((size_t)u4 * kConv + ct) * 16);
       const float ws = *reinterpret_cast<const float*>(rb + (size_t)kConv * 64 + (size_t)ct * 4);
-      const int F8 = g.G.F8;
-      const int s = (int)(cc % NS);
-      if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) break;
+      const int s = st_i;
+      if (!warp_wait(&bars->empty[s], st_ph ^ 1u, abort_flag, err)) break;
+      if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
       unsigned char* st = Xs + (size_t)s * P.stage_bytes;
 #pragma unroll
       for (int u4 = 0; u4 < 4; ++u4) {
@@ -991,12 +1029,7 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
       fence_async_smem();
       warp_arrive(&bars->full[s]);
       issue_next(rs);
-      ++cc;
-      if (++c < g.c1) continue;
-      u += gridDim.x;
-      if (u >= U) break;
-      gram_unit(g, u, uoff, n_items, items, ptrs, ival, splits_max);
-      c = g.c;
+      if (++rs == DR) rs = 0;
     }
     cp_async_wait(0);   // no copy may land after the kernel's shared memory is gone
   }
@@ -1029,25 +1062,59 @@ struct RecDims {
   int nkc;
 };
 
-__device__ inline void rec_dims(const ReconItem& it, void* const* ptrs, const int* ival, RecDims& D) {
+__device__ __forceinline__ void rec_dims(const ReconItem& it, void* const* ptrs, const int* ival, RecDims& D) {
+  // every array below is indexed with constants only (unrolled loops and
+  // selects), so a cursor holding RecDims stays in registers
   D.nl = it.in.nlegs;
-  for (int k = 0; k < PEPO_MAXLEG; ++k) D.d[k] = (k < D.nl) ? ival[it.in.dim[k]] : 1;
   D.cut = D.nl - 1;
-  D.n = 4 * D.d[D.cut];
   const int chin = ival[it.new_dim];
+  int od[PEPO_MAXLEG];
+#pragma unroll
+  for (int k = 0; k < PEPO_MAXLEG; ++k) {
+    D.d[k] = (k < D.nl) ? ival[it.in.dim[k]] : 1;
+    od[k] = (k == D.cut) ? chin : D.d[k];
+  }
+  int dcut = 1;
+#pragma unroll
+  for (int k = 0; k < PEPO_MAXLEG; ++k) if (k == D.cut) dcut = D.d[k];
+  D.n = 4 * dcut;
   D.np = 4 * chin;
   D.R = 1;
-  for (int i = 0; i < D.cut; ++i) D.R *= D.d[i];
-  int od[PEPO_MAXLEG];
-  for (int i = 0; i < D.nl; ++i) od[i] = (i == D.cut) ? chin : D.d[i];
-  long long st = 4;
-  for (int kk = D.nl - 1; kk >= 0; --kk) {
-    const int li = it.out_perm[kk];
-    D.ostride[li] = st;
-    st *= od[li];
+#pragma unroll
+  for (int i = 0; i < PEPO_MAXLEG; ++i) if (i < D.cut) D.R *= D.d[i];
+  // output stride of layout leg l: 4 x the product of the output extents of
+  // the legs that follow l in the output order out_perm
+  int pos[PEPO_MAXLEG], pdim[PEPO_MAXLEG];
+#pragma unroll
+  for (int kk = 0; kk < PEPO_MAXLEG; ++kk) {
+    pos[kk] = PEPO_MAXLEG;
+    pdim[kk] = 1;
   }
-  st = 1;
-  for (int i = D.cut - 1; i >= 0; --i) { D.rstride[i] = st; st *= D.d[i]; }
+#pragma unroll
+  for (int kk = 0; kk < PEPO_MAXLEG; ++kk) {
+    if (kk >= D.nl) continue;
+    const int li = it.out_perm[kk];
+#pragma unroll
+    for (int l = 0; l < PEPO_MAXLEG; ++l)
+      if (l == li) { pos[l] = kk; pdim[kk] = od[l]; }
+  }
+#pragma unroll
+  for (int l = 0; l < PEPO_MAXLEG; ++l) {
+    long long st = 4;
+#pragma unroll
+    for (int kk = 0; kk < PEPO_MAXLEG; ++kk)
+      if (kk > pos[l] && kk < D.nl) st *= pdim[kk];
+    D.ostride[l] = st;
+  }
+  // row stride of layout leg i < cut in the input (cut leg last, row-major)
+#pragma unroll
+  for (int i = 0; i < PEPO_MAXLEG; ++i) {
+    long long st = 1;
+#pragma unroll
+    for (int j = 0; j < PEPO_MAXLEG; ++j)
+      if (j > i && j < D.cut) st *= D.d[j];
+    D.rstride[i] = st;
+  }
   D.K8 = round_up(D.n, 8);
   D.nnb = (D.np + 127) / 128;
   D.NB = round_up((D.np + D.nnb - 1) / D.nnb, 8);
@@ -1080,7 +1147,7 @@ struct RecCursor {
   long long tile, left;
   RecDims D;
 };
-__device__ inline bool rec_start(RecCursor& c, const long long* toff, int n, long long t0, long long t1,
+__device__ __forceinline__ bool rec_start(RecCursor& c, const long long* toff, int n, long long t0, long long t1,
                                  const ReconItem* items, void* const* ptrs, const int* ival) {
   c.left = t1 - t0;
   if (c.left <= 0) return false;
@@ -1091,7 +1158,7 @@ __device__ inline bool rec_start(RecCursor& c, const long long* toff, int n, lon
   rec_dims(items[i], ptrs, ival, c.D);
   return true;
 }
-__device__ inline void rec_next(RecCursor& c, const long long* toff, int n, const ReconItem* items,
+__device__ __forceinline__ void rec_next(RecCursor& c, const long long* toff, int n, const ReconItem* items,
                                 void* const* ptrs, const int* ival) {
   --c.left;
   ++c.tile;
@@ -1147,7 +1214,9 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
     if (lane == 0) {
       RecCursor c;
       bool live = rec_start(c, toff, n_items, t0, t1, items, ptrs, ival);
-      long long cc = 0, tc = 0;
+      long long tc = 0;
+      int st_i = 0;            // operand stage and its phase parity (advanced per chunk)
+      uint32_t st_ph = 0;
       bool ok = true;
       while (live && ok) {
         const int b = (int)(tc & 1);
@@ -1157,9 +1226,10 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
         const int NB = c.D.NB, K8 = c.D.K8;
         const uint32_t id_wide = idesc_tf32(kM, 2 * NB), id_half = idesc_tf32(kM, NB);
         const int nkc = (K8 + kKC - 1) / kKC;
-        for (int kc = 0; kc < nkc; ++kc, ++cc) {
-          const int s = (int)(cc % NS);
-          if (!mbar_wait(&bars->full[s], (uint32_t)((cc / NS) & 1), abort_flag, err)) { ok = false; break; }
+        for (int kc = 0; kc < nkc; ++kc) {
+          const int s = st_i;
+          if (!mbar_wait(&bars->full[s], st_ph, abort_flag, err)) { ok = false; break; }
+          if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
           tc_after();
           const uint32_t a_hi = su32(smem + (size_t)s * P.stage_bytes);
           const uint32_t a_lo = a_hi + (uint32_t)P.a_bytes;
@@ -1201,15 +1271,20 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
       const long long rg = rb * kM + row;
       const bool valid = rg < D.R;
       long long base = 0;
+      long long ocut = 0;
+#pragma unroll
+      for (int i = 0; i < PEPO_MAXLEG; ++i) if (i == D.cut) ocut = D.ostride[i];
       if (valid) {
         long long rem = rg;
-        for (int i = 0; i < D.cut; ++i) {
-          const long long idx = rem / D.rstride[i];
-          rem -= idx * D.rstride[i];
-          base += idx * D.ostride[i];
+#pragma unroll
+        for (int i = 0; i < PEPO_MAXLEG; ++i) {
+          if (i < D.cut) {
+            const long long idx = rem / D.rstride[i];
+            rem -= idx * D.rstride[i];
+            base += idx * D.ostride[i];
+          }
         }
       }
-      const long long ocut = D.ostride[D.cut];
       const uint32_t tbase = tmem + lane_base + (uint32_t)(b * 256);
       // 16-column blocks, loads of block i+1 in flight while block i is stored
       uint32_t a1[16], a2[16], b1[16], b2[16];
@@ -1258,36 +1333,65 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
     const bool issuer = (tid == 256);               // issues the bulk copy of the B block
     RecCursor c;
     bool live = rec_start(c, toff, n_items, t0, t1, items, ptrs, ival);
-    long long cc = 0;
+    int st_i = 0;              // operand stage and its phase parity
+    uint32_t st_ph = 0;
     int kc = 0;
-    // loads of the next chunk run one chunk ahead (ring rotated by unrolling)
+    // row block rb and N block nb of the store cursor's tile, advanced per
+    // tile (tiles run nb fastest; an item change restarts at tile 0)
+    long long s_rb = 0;
+    int s_nb = 0;
+    if (live) { s_rb = c.tile / c.D.nnb; s_nb = (int)(c.tile - s_rb * c.D.nnb); }
+    auto advance = [&](RecCursor& cur, long long& rb, int& nb) {
+      const int it0 = cur.item;
+      rec_next(cur, toff, n_items, items, ptrs, ival);
+      if (cur.item != it0) { rb = 0; nb = 0; }
+      else if (++nb == cur.D.nnb) { nb = 0; ++rb; }
+    };
+    // loads of the next chunk run one chunk ahead (ring rotated by unrolling);
+    // the four source rows of this thread are set up once per tile
     RecCursor lcur = c;
     int lkc = 0;
     bool l_live = live;
+    long long l_rb = s_rb;
+    int l_nb = s_nb;
+    const float* lrow[4];
+    bool lrv[4];
+    auto l_rows = [&]() {
+      const RecDims& D = lcur.D;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long r = l_rb * kM + 8 * (i8_0 + 4 * u) + il;
+        lrv[u] = r < D.R;
+        lrow[u] = D.in + (lrv[u] ? r * D.n : 0);
+      }
+    };
+    if (l_live) l_rows();
     auto load_next = [&](float4 (&v)[4]) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (!l_live) return;
       const RecDims& D = lcur.D;
-      const long long rb = lcur.tile / D.nnb;
       const int k = lkc * kKC + 4 * kq;
+      if (k < D.n) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const long long r = rb * kM + 8 * (i8_0 + 4 * u) + il;
-        if (r < D.R && k < D.n) v[u] = __ldg(reinterpret_cast<const float4*>(D.in + r * D.n + k));
+        for (int u = 0; u < 4; ++u)
+          if (lrv[u]) v[u] = __ldg(reinterpret_cast<const float4*>(lrow[u] + k));
       }
       if (++lkc < D.nkc) return;
       lkc = 0;
       if (lcur.left == 1) { l_live = false; return; }
-      rec_next(lcur, toff, n_items, items, ptrs, ival);
+      const long long rb0 = l_rb;
+      const int item0 = lcur.item;
+      advance(lcur, l_rb, l_nb);
+      if (l_rb != rb0 || lcur.item != item0) l_rows();
     };
     auto step = [&](float4 (&vl)[4], float4 (&vs)[4]) -> bool {
       load_next(vl);
       const RecDims& D = c.D;
-      const long long rb = c.tile / D.nnb;
-      const int nb = (int)(c.tile - rb * D.nnb);
-      const int s = (int)(cc % NS);
-      if (!warp_wait(&bars->empty[s], (uint32_t)(((cc / NS) & 1) ^ 1), abort_flag, err)) return false;
+      const int nb = s_nb;
+      const int s = st_i;
+      if (!warp_wait(&bars->empty[s], st_ph ^ 1u, abort_flag, err)) return false;
+      if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
       unsigned char* hi = smem + (size_t)s * P.stage_bytes;
       unsigned char* lo = hi + P.a_bytes;
       unsigned char* bs = hi + 2 * P.a_bytes;
@@ -1312,11 +1416,10 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
       }
       fence_async_smem();
       warp_arrive(&bars->full[s]);
-      ++cc;
       if (++kc < D.nkc) return true;
       kc = 0;
       if (c.left == 1) return false;
-      rec_next(c, toff, n_items, items, ptrs, ival);
+      advance(c, s_rb, s_nb);
       return true;
     };
     float4 v0[4], v1[4];
