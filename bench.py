@@ -36,6 +36,8 @@ def parse():
     ap.add_argument("--grid", type=int, default=None, help="override the grid side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default=None, help="tf32x3 | fp32 | fp64 (default tf32x3)")
+    ap.add_argument("--tuning", default="cache", choices=["cache", "none"],
+                    help="Gram launch shapes: the autotuner's cached class (default) or the built-in ones")
     ap.add_argument("--workload", default="c5", choices=["c5", "c3"],
                     help="c5: 10x10 chi=100 saturated step (default); c3: 64 batched instances "
                          "from the initial state (instance-steps/s)")
@@ -112,6 +114,10 @@ class Clocks:
 
 
 TF32_PER_BF16 = 1.1 / 2.25     # nominal dense TF32 / BF16 tensor rate of the part
+# measured DRAM bytes (read + write) per algorithmic byte, per kernel class,
+# with the profile summary it comes from; an entry is removed when its kernel
+# changes (traffic is then reported as null until it is measured again)
+TRAFFIC_RATIO = {"leg_contract": (0.986, "profiles/k_leg_umma_3x3_chi100_dram.md")}
 
 
 def fp32_alu_peak_tflops():
@@ -207,7 +213,7 @@ def run_gpu(args, rank, world, local):
     torch.cuda.set_device(local)
     w = workload(args)
     cfg = pkg.Config(**{k: v for k, v in w.items()})
-    eng = pkg.Engine(cfg, device="cuda:%d" % local)
+    eng = pkg.Engine(cfg, device="cuda:%d" % local, tuning="cache" if args.tuning == "cache" else None)
     t_up = time.perf_counter()
     state_bytes, h2d_s = upload_state(eng, w, SEED + rank)
     torch.cuda.synchronize()
@@ -287,7 +293,13 @@ def run_gpu(args, rank, world, local):
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "peak_source": src, "unit": "GB/s",
                 "frac": gbs / hbm}
-    roof.update({"kernel": name, "traffic": None, "avg_launch_ms": avg_ms,
+    # DRAM traffic per launch: measured DRAM bytes per algorithmic byte of this
+    # kernel class (one ncu capture of the current kernel version, summarised
+    # under profiles/) times this run's algorithmic bytes per launch
+    ratio = TRAFFIC_RATIO.get(name)
+    traffic = ratio[0] * tk["bytes"] / nl if ratio else None
+    roof.update({"kernel": name, "traffic": traffic, "traffic_source": ratio[1] if ratio else None,
+                 "avg_launch_ms": avg_ms,
                  "algorithmic_bytes_per_launch": tk["bytes"] / nl,
                  "algorithmic_flops_per_launch": tk["flops"] / nl,
                  "achieved_gbs": gbs, "achieved_tflops": tfs})
@@ -314,11 +326,12 @@ def run_gpu(args, rank, world, local):
                    "bp_tol": w["bp_tol"], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.1f GB of site tensors)" % (state_bytes / 1e9),
                    "state": "each step restarts from the same resident synthetic state (device restore timed)",
-                   "bp_sweeps": sweeps},
+                   "bp_sweeps": sweeps, "tuning": eng.get_tuning()},
         "roofline": roof,
         "bond_update_tflops": (sum(timing[k]["flops"] for k in bond_classes if k in timing) / 1e12
                                / (bu_ms / 1e3)) if bu_ms > 0 else None,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in timing.items() if v["launches"]},
+        "kernel_bytes_per_step": {k: v["bytes"] / args.steps for k, v in timing.items() if v["launches"]},
         "clocks": clk,
         # end to end through the public API: the timed steps (results read back
         # to the host every step) plus the host -> device upload of the state
@@ -381,7 +394,7 @@ def run_batched(args, rank, world, local):
     insts = c3_instances(seed=SEED + rank)
     cfgs = [pkg.Config(**{k: v for k, v in c.items() if k not in ("nsteps", "precision")}, precision=prec)
             for c in insts]
-    eng = pkg.Engine(cfgs, device="cuda:%d" % local)
+    eng = pkg.Engine(cfgs, device="cuda:%d" % local, tuning="cache" if args.tuning == "cache" else None)
 
     def one_step():
         eng.trotter_step(1)

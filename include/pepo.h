@@ -278,6 +278,24 @@ int pepo_num_bonds(const pepo_ctx* ctx, int inst);
  * the start of each call (exact whenever chi does not change inside the call,
  * e.g. in the saturated regime).  Classes are numbered 0 .. pepo_timing_classes()-1. */
 pepo_status pepo_set_timing(pepo_ctx* ctx, int enable);
+
+/* Launch shapes of a context (batching and autotuning; the paper has no
+ * counterpart).  The K range of a Gram is cut into splits reduced in FP64
+ * afterwards: more splits fill more SMs when few Grams run at once, fewer
+ * splits mean less partial traffic.  Results differ only in the rounding of
+ * the split sums.  A field of 0 selects the default (free-leg Gram 64, row
+ * Gram 32).  May be called at any time: a change synchronises the context's
+ * stream and drops its captured CUDA graphs (captured again at their next
+ * use).  PEPO_E_INVALID for a value outside 1..128 (gram_leg_splits) or
+ * 1..64 (gram_rows_splits), PEPO_E_CUDA if the synchronisation fails; the
+ * context is unchanged on error.  The tuning belongs to the caller-owned
+ * struct only for the duration of the call. */
+typedef struct {
+  int gram_leg_splits;    /* free-leg Gram of a BP message (Eq. 13) / the absorb step */
+  int gram_rows_splits;   /* Cholesky-QR Gram cv^T cv of the bond update (Eq. 10) */
+} pepo_tuning;
+pepo_status pepo_set_tuning(pepo_ctx* ctx, const pepo_tuning* tuning);
+pepo_status pepo_get_tuning(const pepo_ctx* ctx, pepo_tuning* tuning);
 int pepo_timing_classes(void);
 const char* pepo_timing_class_name(int kclass);
 /* Totals since the last reset: launches, milliseconds, algorithmic bytes and

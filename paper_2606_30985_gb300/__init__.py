@@ -50,10 +50,14 @@ class _Diag(ctypes.Structure):
                 ("core_sweeps32_max", ctypes.c_int), ("core_sweeps64_max", ctypes.c_int)]
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("gram_leg_splits", ctypes.c_int), ("gram_rows_splits", ctypes.c_int)]
+
+
 EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trotter_step",
            "pepo_bp_converge", "pepo_correlator", "pepo_get_spectrum", "pepo_get_site",
            "pepo_set_state", "pepo_set_bonds", "pepo_set_site", "pepo_set_site_static", "pepo_state_bytes", "pepo_save_state", "pepo_load_state",
-           "pepo_get_message", "pepo_num_bonds", "pepo_set_timing",
+           "pepo_get_message", "pepo_num_bonds", "pepo_set_timing", "pepo_set_tuning", "pepo_get_tuning",
            "pepo_timing_classes", "pepo_timing_class_name", "pepo_get_timing", "pepo_reset_timing",
            "pepo_launch_count", "pepo_last_error", "pepo_destroy",
            "pepo_mlp_num_params", "pepo_mlp_required_bytes", "pepo_mlp_init", "pepo_mlp_get_params",
@@ -142,6 +146,10 @@ def load_library(path=LIB_PATH):
     lib.pepo_num_bonds.restype = I
     lib.pepo_set_timing.argtypes = [P, I]
     lib.pepo_set_timing.restype = I
+    lib.pepo_set_tuning.argtypes = [P, ctypes.POINTER(_Tuning)]
+    lib.pepo_set_tuning.restype = I
+    lib.pepo_get_tuning.argtypes = [P, ctypes.POINTER(_Tuning)]
+    lib.pepo_get_tuning.restype = I
     lib.pepo_timing_classes.argtypes = []
     lib.pepo_timing_classes.restype = I
     lib.pepo_timing_class_name.argtypes = [I]
@@ -226,7 +234,10 @@ def diag_to_dict(d):
 class Engine:
     """A context of one or more instances living in one device arena."""
 
-    def __init__(self, cfgs, device="cuda:0"):
+    def __init__(self, cfgs, device="cuda:0", tuning="cache"):
+        """tuning: "cache" applies the launch shapes that the autotuner cached
+        for the nearest class of (chi_max, precision) (autotune.lookup), None
+        keeps the built-in shapes, a dict sets them (Engine.set_tuning)."""
         import torch
         if isinstance(cfgs, Config):
             cfgs = [cfgs]
@@ -249,6 +260,11 @@ class Engine:
         if st != 0:
             raise PepoError("pepo_init failed: %s" % STATUS.get(st, st))
         self.ctx = ctx
+        if tuning == "cache":
+            from . import autotune
+            tuning = autotune.lookup(max(c.chi_max for c in self.cfgs), self.cfgs[0].precision)
+        if tuning:
+            self.set_tuning(**tuning)
 
     # -- helpers
     def _check(self, st, what):
@@ -273,6 +289,17 @@ class Engine:
 
     def launches(self):
         return int(self.lib.pepo_launch_count(self.ctx))
+
+    def set_tuning(self, gram_leg_splits=0, gram_rows_splits=0):
+        """Launch shapes (pepo_set_tuning): K splits of the free-leg and the
+        Cholesky-QR Grams, 0 = default."""
+        t = _Tuning(int(gram_leg_splits), int(gram_rows_splits))
+        self._check(self.lib.pepo_set_tuning(self.ctx, ctypes.byref(t)), "pepo_set_tuning")
+
+    def get_tuning(self):
+        t = _Tuning()
+        self._check(self.lib.pepo_get_tuning(self.ctx, ctypes.byref(t)), "pepo_get_tuning")
+        return {"gram_leg_splits": t.gram_leg_splits, "gram_rows_splits": t.gram_rows_splits}
 
     def set_timing(self, on=True):
         self._check(self.lib.pepo_set_timing(self.ctx, 1 if on else 0), "pepo_set_timing")

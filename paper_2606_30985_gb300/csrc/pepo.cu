@@ -29,8 +29,13 @@ using namespace pepo;
 namespace {
 
 constexpr int kChiMaxLimit = 128;
+// K splits of the Cholesky-QR Gram and of the free-leg (BP message) Gram:
+// defaults and the bounds the partial-sum workspaces are sized for (the
+// launch shapes are tunable per context, pepo_set_tuning)
 constexpr int kGramSplits = 32;
 constexpr int kLegSplits = 64;
+constexpr int kGramSplitsMax = 64;
+constexpr int kLegSplitsMax = 128;
 constexpr size_t kAlign = 256;
 
 enum { LEG_U = 0, LEG_D = 1, LEG_L = 2, LEG_R = 3 };
@@ -167,6 +172,7 @@ struct pepo_ctx {
   long long launches = 0;
   std::string err;
   bool stepped = false;
+  pepo_tuning tune = {kLegSplits, kGramSplits};
   // kernel-class timing
   bool timing = false;
   std::vector<char> host_items;          // host copy of the item arrays
@@ -414,8 +420,8 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
     w.C = cv.take<double>((size_t)nmax * nmax);
     w.T = cv.take<double>((size_t)4 * nmax * rmax);
     w.perm = cv.take<int>(rmax);
-    size_t pg = (size_t)kGramSplits * nmax * nmax;
-    size_t pl = (size_t)kLegSplits * cm2;
+    size_t pg = (size_t)kGramSplitsMax * nmax * nmax;
+    size_t pl = (size_t)PEPO_MAXLEG * kLegSplitsMax * cm2;
     w.partial = cv.take<double>(std::max(pg, pl));
     w.W = cv.take<double>((size_t)nmax * nmax);
   }
@@ -743,7 +749,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
           g.x.ref = cur;
           g.y_ref = cur;
           g.leg = w;
-          g.partial = W.partial + (size_t)w * kLegSplits * cm2;
+          g.partial = W.partial + (size_t)w * kLegSplitsMax * cm2;
           g.out = W.C + (size_t)w * cm2;
           g.ldo = chimax;
           for (int u = 0; u < PEPO_MAXLEG; ++u) g.sw[u] = (u < d && u != w) ? W.sqrtD[u] : nullptr;
@@ -1208,8 +1214,8 @@ cudaError_t leg_dispatch(pepo_ctx* c, const LegItem* items, int n, int gx, int c
 template <typename T>
 cudaError_t gram_leg_dispatch(pepo_ctx* c, const GramLegItem* items, int n, int chimax) {
   if (use_umma<T>(c, chimax))
-    return launch_gram_umma(items, n, kLegSplits, chimax, c->d_ptrs, c->d_ival, c->d_kerr, c->stream);
-  return launch_gram_leg<T>(items, n, kLegSplits, chimax, c->d_ptrs, c->d_ival, c->stream);
+    return launch_gram_umma(items, n, c->tune.gram_leg_splits, chimax, c->d_ptrs, c->d_ival, c->d_kerr, c->stream);
+  return launch_gram_leg<T>(items, n, c->tune.gram_leg_splits, chimax, c->d_ptrs, c->d_ival, c->stream);
 }
 
 template <typename T>
@@ -1228,9 +1234,9 @@ pepo_status run_gate_wave(pepo_ctx* c, Inst& I, GateWave& w) {
   LAUNCH_N(w.fac.n, launch_branch(w.fac.d, w.fac.n, c->d_ival, s));
   {
     int nt = ceil_div(nmax, 64);
-    LAUNCH_T(K_GRAM_ROWS, hitems(c, w.gram), w.gram.n, launch_gram_rows<T>(w.gram.d, w.gram.n, nt * (nt + 1) / 2, kGramSplits, 1, c->d_ptrs,
+    LAUNCH_T(K_GRAM_ROWS, hitems(c, w.gram), w.gram.n, launch_gram_rows<T>(w.gram.d, w.gram.n, nt * (nt + 1) / 2, c->tune.gram_rows_splits, 1, c->d_ptrs,
                                c->d_ival, s));
-    LAUNCH_T(K_GRAM_ROWS_RED, nullptr, w.gram.n, launch_gram_rows_reduce(w.gram.d, w.gram.n, nmax, kGramSplits, 1, c->d_ival, s));
+    LAUNCH_T(K_GRAM_ROWS_RED, nullptr, w.gram.n, launch_gram_rows_reduce(w.gram.d, w.gram.n, nmax, c->tune.gram_rows_splits, 1, c->d_ival, s));
   }
   {
     const long long mmax = (long long)pow_sz(chimax, 3);
@@ -1288,7 +1294,7 @@ pepo_status run_bp_waves(pepo_ctx* c, Inst& I, std::vector<BpWave>& waves) {
     LAUNCH_T(K_GRAM_LEG, hitems(c, w.gram), w.gram.n,
              gram_leg_dispatch<T>(c, w.gram.d, w.gram.n, chimax));
     LAUNCH_T(K_GRAM_LEG_RED, nullptr, w.gram.n,
-             launch_gram_leg_reduce(w.gram.d, w.gram.n, chimax, kLegSplits, use_umma<T>(c, chimax) ? 1 : 0,
+             launch_gram_leg_reduce(w.gram.d, w.gram.n, chimax, c->tune.gram_leg_splits, use_umma<T>(c, chimax) ? 1 : 0,
                                     c->d_ival, s));
     LAUNCH_T(K_MSG, nullptr, w.rot.n, launch_rotate_back(w.rot.d, w.rot.n, chimax, c->d_ival, s));
   }
@@ -2223,6 +2229,32 @@ void pepo_destroy(pepo_ctx* c) {
   if (!c) return;
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   delete c;
+}
+
+pepo_status pepo_set_tuning(pepo_ctx* c, const pepo_tuning* t) {
+  if (!c || !t) return PEPO_E_INVALID;
+  const int gl = t->gram_leg_splits ? t->gram_leg_splits : kLegSplits;
+  const int gr = t->gram_rows_splits ? t->gram_rows_splits : kGramSplits;
+  if (gl < 1 || gl > kLegSplitsMax) return fail(c, PEPO_E_INVALID, "gram_leg_splits out of 1..128");
+  if (gr < 1 || gr > kGramSplitsMax) return fail(c, PEPO_E_INVALID, "gram_rows_splits out of 1..64");
+  if (gl == c->tune.gram_leg_splits && gr == c->tune.gram_rows_splits) return PEPO_OK;
+  // captured graphs hold the old launch shapes: finish the stream's work and
+  // drop them (they are captured again at their next use)
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, PEPO_E_CUDA, "pepo_set_tuning: %s", cudaGetErrorString(e));
+  for (cudaGraphExec_t* x : {&c->step_exec, &c->bp_exec, &c->sl_exec}) {
+    if (*x) cudaGraphExecDestroy(*x);
+    *x = nullptr;
+  }
+  c->tune.gram_leg_splits = gl;
+  c->tune.gram_rows_splits = gr;
+  return PEPO_OK;
+}
+
+pepo_status pepo_get_tuning(const pepo_ctx* c, pepo_tuning* t) {
+  if (!c || !t) return PEPO_E_INVALID;
+  *t = c->tune;
+  return PEPO_OK;
 }
 
 pepo_status pepo_set_timing(pepo_ctx* c, int enable) {
