@@ -496,12 +496,6 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
       lkc = 0;
     };
     if (lc_live) enter_tile();
-    // The per-chunk work (issue loads, convert, hand over) is kept apart from
-    // the rare tile / item transitions, which run in one place after each
-    // chunk: the ring below is unrolled three ways, and repeating the
-    // transition code (cursor, dims, B staging) in every copy made the loop
-    // outgrow the SM instruction cache.
-    bool l_adv = false, s_adv = false;
     auto load_next = [&](float4* v) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -519,21 +513,14 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
           if (j + 3 < J) v[u].w = __ldg(p0 + 3 * Q);
         }
       }
-      if (++lkc == (lc.L.K8 + kKC - 1) / kKC) l_adv = true;
-    };
-    // load cursor to the next tile (after the tile's last chunk was issued)
-    auto load_adv = [&]() {
-      if (!l_adv) return;
-      l_adv = false;
+      if (++lkc < (lc.L.K8 + kKC - 1) / kKC) return;
       if (lc.left == 1) { lc_live = false; return; }
       cursor_next(lc, toff, n_items, items, ptrs, ival);
       enter_tile();
     };
     float4 v0[4], v1[4], v2[4];
     load_next(v0);
-    load_adv();
     load_next(v1);
-    load_adv();
     // store cursor
     LegCursor c;
     bool live = cursor_start(c, toff, n_items, t0, t1, items, ptrs, ival);
@@ -543,39 +530,11 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
     bool need_b = true;
     // one chunk: issue the loads two chunks ahead into vl, convert and store
     // vs (the ring is rotated by unrolling, never by copying registers, so
-    // no load is waited on before its turn); returns false on a failed wait
+    // no load is waited on before its turn); returns false at the end
     auto step = [&](float4 (&vl)[4], float4 (&vs)[4]) -> bool {
+      const LegDims& L = c.L;
       load_next(vl);
-      const int s = st_i;
-      if (!warp_wait(&bars->empty[s], st_ph ^ 1u, abort_flag, err)) return false;
-      if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
-      unsigned char* hi = As + (size_t)s * P.stage_bytes;
-      unsigned char* lo = hi + P.stage_bytes / 2;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const size_t off = swz(r, jq0 + 2 * u);
-        const float4 x = vs[u];
-        const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-        *reinterpret_cast<float4*>(hi + off) = h;
-        *reinterpret_cast<float4*>(lo + off) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-      }
-      fence_async_smem();
-      warp_arrive(&bars->full[s]);
-      if (++kc == (c.L.K8 + kKC - 1) / kKC) s_adv = true;
-      return true;
-    };
-    // transitions after a chunk (one copy): load cursor, store cursor, and the
-    // B operand of a new item; returns false when the CTA's work is done
-    auto transitions = [&]() -> bool {
-      load_adv();
-      if (s_adv) {
-        s_adv = false;
-        kc = 0;
-        if (c.left == 1) return false;
-        if (cursor_next(c, toff, n_items, items, ptrs, ival)) { ++item_n; need_b = true; }
-      }
       if (need_b) {
-        const LegDims& L = c.L;
         if (item_n > 0 && !warp_wait(&bars->bfree, (uint32_t)((item_n - 1) & 1), abort_flag, err)) return false;
         // [Ah; Al]: rows n < N16 hold hi(A[n, :]), rows N16 + n hold lo(A[n, :]);
         // one block of 2 N16 rows per 32-wide K chunk
@@ -596,18 +555,31 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
         warp_arrive(&bars->bfull);
         need_b = false;
       }
+      const int s = st_i;
+      if (!warp_wait(&bars->empty[s], st_ph ^ 1u, abort_flag, err)) return false;
+      if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
+      unsigned char* hi = As + (size_t)s * P.stage_bytes;
+      unsigned char* lo = hi + P.stage_bytes / 2;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const size_t off = swz(r, jq0 + 2 * u);
+        const float4 x = vs[u];
+        const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+        *reinterpret_cast<float4*>(hi + off) = h;
+        *reinterpret_cast<float4*>(lo + off) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+      fence_async_smem();
+      warp_arrive(&bars->full[s]);
+      if (++kc < (L.K8 + kKC - 1) / kKC) return true;
+      kc = 0;
+      if (c.left == 1) return false;
+      if (cursor_next(c, toff, n_items, items, ptrs, ival)) { ++item_n; need_b = true; }
       return true;
     };
-    if (live) live = transitions();
-    int k3 = 0;
     while (live) {
-      bool ok;
-      if (k3 == 0) ok = step(v2, v0);
-      else if (k3 == 1) ok = step(v0, v1);
-      else ok = step(v1, v2);
-      if (!ok) break;
-      k3 = (k3 == 2) ? 0 : k3 + 1;
-      if (!transitions()) break;
+      if (!step(v2, v0)) break;
+      if (!step(v0, v1)) break;
+      if (!step(v1, v2)) break;
     }
   }
   tc_before();
@@ -713,11 +685,6 @@ struct GramBars {
   int abort_flag;
 };
 
-// odometer over the legs other than the free leg, used to form the weight
-// prod_{u != k} sw[u][j_u] of one 4-wide (Pauli) column group
-struct Odo {
-  int dig[PEPO_MAXLEG];
-};
 
 // Load side of the Gram converters: the cursor of one converter thread over
 // the chunks of its CTA's units (items x splits), kept in registers.  Per
