@@ -69,6 +69,16 @@ def workload_name(w):
 
 
 # ------------------------------------------------------------------ clocks
+def clocks_dir():
+    """Where the raw nvidia-smi samples of the timed region are written
+    (BENCH_CLOCKS_DIR if set, else the system temporary directory); the JSON
+    line carries their summary."""
+    import tempfile
+    d = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
 class Clocks:
     def __init__(self, index, path):
         self.path = path
@@ -243,8 +253,7 @@ def run_gpu(args, rank, world, local):
     if dist:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % rank)
-                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks.csv")
+    clocks = Clocks(local, os.path.join(clocks_dir(), "clocks_rank%d.csv" % rank))
     eng.reset_timing()
     eng.set_timing(True)
     l0 = eng.launches()
@@ -408,8 +417,7 @@ def run_batched(args, rank, world, local):
     if dist:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", "clocks_c3_rank%d.csv" % rank)
-                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks.csv")
+    clocks = Clocks(local, os.path.join(clocks_dir(), "clocks_c3_rank%d.csv" % rank))
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
