@@ -57,8 +57,8 @@ typedef enum {
   PEPO_E_INVALID = 1,   /* bad argument or configuration */
   PEPO_E_OOM = 2,       /* arena smaller than pepo_required_bytes */
   PEPO_E_CUDA = 3,      /* a CUDA runtime call failed */
-  PEPO_E_NUMERIC = 4,   /* NaN / Inf or a vanished bond matrix */
-  PEPO_E_STATE = 5      /* call out of order (e.g. spectrum before any step) */
+  PEPO_E_NUMERIC = 4,   /* reserved: numerical trouble is reported in pepo_diag.flags */
+  PEPO_E_STATE = 5      /* reserved: no call currently depends on call order */
 } pepo_status;
 
 typedef enum {
@@ -137,18 +137,26 @@ pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena,
                       size_t arena_bytes, void* cuda_stream, pepo_ctx** out);
 
 /* Enqueue n_steps Trotter steps (Eq. 6 schedule, Alg. 1 per bond) on every
- * instance.  Asynchronous. */
+ * instance.  Asynchronous.  Errors: PEPO_E_INVALID (NULL context,
+ * n_steps < 0), PEPO_E_CUDA (a launch or a graph capture failed; message in
+ * pepo_last_error).  Numerical trouble (a rank-deficient environment, a
+ * non-finite value, a Jacobi sweep cap) does not fail the call: it is
+ * reported in pepo_diag.flags by pepo_correlator. */
 pepo_status pepo_trotter_step(pepo_ctx* ctx, int n_steps);
 
 /* Run damped double-layer BP (Eq. 13-19) to tolerance or the sweep budget.
  * sweeps_out / delta_out: host arrays of n_inst entries (may be NULL).
- * Synchronises the stream. */
+ * Synchronises the stream.  Errors: PEPO_E_INVALID (NULL context),
+ * PEPO_E_CUDA (a launch or read-back failed, or a tensor-core pipeline wait
+ * ran out of time: the kernels return instead of hanging and the call fails
+ * with that message). */
 pepo_status pepo_bp_converge(pepo_ctx* ctx, int* sweeps_out, double* delta_out);
 
 /* Single-layer BP on the pinned network and the Bethe value of C(t)
  * (Eq. 7-9).  Uses the current double-layer messages (call
  * pepo_bp_converge first).  C_out: n_inst doubles; diag_out: n_inst records
- * (either may be NULL).  Synchronises the stream. */
+ * (either may be NULL).  Synchronises the stream.  Errors as
+ * pepo_bp_converge. */
 pepo_status pepo_correlator(pepo_ctx* ctx, double* C_out, pepo_diag* diag_out);
 
 /* Vidal-normalised singular values of a bond (Eq. 12) from its last update.
@@ -279,6 +287,14 @@ int pepo_num_bonds(const pepo_ctx* ctx, int inst);
  * e.g. in the saturated regime).  Classes are numbered 0 .. pepo_timing_classes()-1. */
 pepo_status pepo_set_timing(pepo_ctx* ctx, int enable);
 
+int pepo_timing_classes(void);
+const char* pepo_timing_class_name(int kclass);
+/* Totals since the last reset: launches, milliseconds, algorithmic bytes and
+ * FLOPs of one class.  Synchronises the stream. */
+pepo_status pepo_get_timing(pepo_ctx* ctx, int kclass, long long* launches, double* ms,
+                            double* bytes, double* flops);
+pepo_status pepo_reset_timing(pepo_ctx* ctx);
+
 /* Launch shapes of a context (batching and autotuning; the paper has no
  * counterpart).  The K range of a Gram is cut into splits reduced in FP64
  * afterwards: more splits fill more SMs when few Grams run at once, fewer
@@ -296,13 +312,6 @@ typedef struct {
 } pepo_tuning;
 pepo_status pepo_set_tuning(pepo_ctx* ctx, const pepo_tuning* tuning);
 pepo_status pepo_get_tuning(const pepo_ctx* ctx, pepo_tuning* tuning);
-int pepo_timing_classes(void);
-const char* pepo_timing_class_name(int kclass);
-/* Totals since the last reset: launches, milliseconds, algorithmic bytes and
- * FLOPs of one class.  Synchronises the stream. */
-pepo_status pepo_get_timing(pepo_ctx* ctx, int kclass, long long* launches, double* ms,
-                            double* bytes, double* flops);
-pepo_status pepo_reset_timing(pepo_ctx* ctx);
 
 /* Number of kernel launches enqueued by this context so far. */
 long long pepo_launch_count(const pepo_ctx* ctx);
