@@ -122,3 +122,20 @@ def test_dropped_pinv_of_deabsorb_is_caught(monkeypatch):
     orig = pepo.env_sqrt
     monkeypatch.setattr(pepo, "env_sqrt", lambda M, rel: (orig(M, rel)[0], orig(M, rel)[0]))
     assert chain_error() > 1e-6 or loop_error() > 1e-6
+
+
+def test_dropped_first_site_gates_are_caught(monkeypatch):
+    # the first layer of site gates skipped: the operator cannot leave its
+    # site in the first step, so the light-cone pin must fail
+    from tests import test_oracle_structure as ts
+    orig = run.apply_site_gates
+    calls = {"n": 0}
+
+    def skip_first(net, g):
+        calls["n"] += 1
+        if calls["n"] > 1:
+            orig(net, g)
+
+    monkeypatch.setattr(run, "apply_site_gates", skip_first)
+    with pytest.raises(AssertionError):
+        ts.test_bond_dimension_grows_exactly_inside_the_light_cone((2, 1), 2, 1, "ZZ_X")
