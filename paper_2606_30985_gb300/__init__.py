@@ -73,6 +73,23 @@ WS_WIDTH = 256
 WS_GAMMA = 0.25
 
 
+def _device_tensor(t, dtype, min_numel, what):
+    """Raise PepoError unless t is a contiguous CUDA tensor of `dtype` with at
+    least min_numel elements (the library receives only its raw pointer)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise PepoError("%s: expected a torch tensor, got %s" % (what, type(t).__name__))
+    if not t.is_cuda:
+        raise PepoError("%s: the tensor must live on the GPU" % what)
+    if t.dtype != dtype:
+        raise PepoError("%s: expected dtype %s, got %s" % (what, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise PepoError("%s: the tensor must be contiguous" % what)
+    if t.numel() < min_numel:
+        raise PepoError("%s: %d elements, at least %d needed" % (what, t.numel(), min_numel))
+    return t
+
+
 def load_library(path=LIB_PATH):
     """Load libpepo.so (raises if it has not been built)."""
     global _lib
@@ -405,6 +422,8 @@ class Engine:
         """As set_site, through the library's fixed device staging buffer (no
         allocation); tensor must already have the storage dtype."""
         t = np.ascontiguousarray(tensor)
+        if t.dtype not in (np.float32, np.float64):
+            raise PepoError("set_site_static: float32 or float64 data required, got %s" % t.dtype)
         dt = 0 if t.dtype == np.float32 else 1
         self._check(self.lib.pepo_set_site_static(self.ctx, inst, v, ctypes.c_void_p(t.ctypes.data), dt,
                                                   t.size), "pepo_set_site_static")
@@ -415,10 +434,14 @@ class Engine:
 
     def save_state(self, buf, inst=0):
         """Copy the instance's state into the device tensor `buf` (uint8)."""
+        import torch
+        _device_tensor(buf, torch.uint8, self.state_bytes(inst), "save_state")
         self._check(self.lib.pepo_save_state(self.ctx, inst, ctypes.c_void_p(buf.data_ptr()), buf.numel()),
                     "pepo_save_state")
 
     def load_state(self, buf, inst=0):
+        import torch
+        _device_tensor(buf, torch.uint8, self.state_bytes(inst), "load_state")
         self._check(self.lib.pepo_load_state(self.ctx, inst, ctypes.c_void_p(buf.data_ptr()), buf.numel()),
                     "pepo_load_state")
 
@@ -434,6 +457,9 @@ class Engine:
         import torch
         r = self.ws_rows(inst)
         X = out if out is not None else torch.empty((r, WS_FEATURES), dtype=torch.float32, device=self.device)
+        _device_tensor(X, torch.float32, 0, "ws_features")
+        if X.dim() != 2 or X.shape[1] != WS_FEATURES:
+            raise PepoError("ws_features: out must be [rows, %d]" % WS_FEATURES)
         self._check(self.lib.pepo_ws_features(self.ctx, inst, ctypes.c_void_p(X.data_ptr()), X.shape[0]),
                     "pepo_ws_features")
         return X
@@ -443,12 +469,17 @@ class Engine:
         import torch
         r = self.ws_rows(inst)
         t = out if out is not None else torch.empty((r,), dtype=torch.float32, device=self.device)
+        _device_tensor(t, torch.float32, 0, "ws_targets")
         self._check(self.lib.pepo_ws_targets(self.ctx, inst, ctypes.c_void_p(t.data_ptr()), t.shape[0]),
                     "pepo_ws_targets")
         return t
 
     def ws_apply(self, y, inst=0, gamma=1.0):
         """Messages <- diag((1-gamma) d/sum d + gamma exp(y)/sum exp(y)) per directed bond."""
+        import torch
+        _device_tensor(y, torch.float32, self.ws_rows(inst), "ws_apply")
+        if not 0.0 <= gamma <= 1.0:
+            raise PepoError("ws_apply: gamma must lie in [0, 1]")
         self._check(self.lib.pepo_ws_apply(self.ctx, inst, ctypes.c_void_p(y.data_ptr()), ctypes.c_float(gamma)),
                     "pepo_ws_apply")
 
