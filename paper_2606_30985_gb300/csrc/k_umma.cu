@@ -25,9 +25,12 @@
 //   warps 4-7     epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
 //                 lanes 32 (w % 4) .. +31), store to global memory (leg) or
 //                 add into compensated FP32 sums in shared memory (Gram)
-//   warps 8-15    converters: coalesced global loads, weight, split, and
-//                 16-byte conflict-free stores into the swizzled K-major
-//                 layout the MMA descriptors describe (below)
+//   warps 8-15    converters: coalesced global loads (leg, reconstruct:
+//                 a register ring two or one chunks ahead; Gram: per-thread
+//                 cp.async into a ring of raw shared-memory stages four chunks
+//                 ahead), weight, split, and 16-byte conflict-free stores into
+//                 the swizzled K-major layout the MMA descriptors describe
+//                 (below); the reconstruct's W block arrives by bulk copy
 // Stages and accumulators are handed over with mbarriers.  Every wait is
 // bounded (a few seconds of %globaltimer); on expiry the kernel records bit 0
 // in *err (bit 1 marks a reconstruct item without its packed-W workspace),
