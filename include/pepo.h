@@ -58,7 +58,8 @@ typedef enum {
   PEPO_E_OOM = 2,       /* arena smaller than pepo_required_bytes */
   PEPO_E_CUDA = 3,      /* a CUDA runtime call failed */
   PEPO_E_NUMERIC = 4,   /* reserved: numerical trouble is reported in pepo_diag.flags */
-  PEPO_E_STATE = 5      /* reserved: no call currently depends on call order */
+  PEPO_E_STATE = 5      /* a call that needs an earlier setup (warm-start weights without a
+                           warm_start instance) */
 } pepo_status;
 
 typedef enum {
@@ -89,7 +90,8 @@ typedef struct {
   double pinv_rel;         /* rank threshold for message square roots (1e-12) */
   int gates;               /* pepo_gateset */
   int prec;                /* pepo_precision */
-  int warm_start;          /* reserved, 0 (the warm start is driven through pepo_ws_*) */
+  int warm_start;          /* 1: pepo_bp_converge applies the learned warm start once
+                              weights are set (pepo_set_warmstart_weights); 0: plain BP */
   int inflight_sites;      /* sites updated concurrently (scratch slabs), 0 = auto */
 } pepo_config;
 
@@ -261,6 +263,18 @@ pepo_status pepo_mlp_gradient(pepo_mlp* mlp, const float* X_dev, const float* t_
 /* One Adam update with the last gradient. */
 pepo_status pepo_mlp_adam_step(pepo_mlp* mlp, float lr);
 void pepo_mlp_destroy(pepo_mlp* mlp);
+/* The warm start inside pepo_bp_converge: dev_weights holds the network's
+ * pepo_mlp_num_params FP32 parameters (layout above; device memory owned by
+ * the caller, copied during the call).  From then on every pepo_bp_converge
+ * first writes, for each instance created with warm_start = 1, the blended
+ * start (1 - 0.25) d / sum d + 0.25 exp(y) / sum exp(y) into its messages
+ * (features, forward pass and writer as pepo_ws_features / pepo_mlp_forward
+ * / pepo_ws_apply); damped BP then runs to its tolerance as usual.  The arena
+ * holds the workspace only when some instance has warm_start = 1.  Errors:
+ * PEPO_E_INVALID (bytes != pepo_mlp_num_params * 4, NULL weights),
+ * PEPO_E_STATE (no instance has warm_start = 1), PEPO_E_CUDA.  Synchronises
+ * the stream.  Not yet run on a GPU: the composed calls are tested one by one. */
+pepo_status pepo_set_warmstart_weights(pepo_ctx* ctx, const void* dev_weights, size_t bytes);
 /* Row count of instance inst (-1 on error).  Synchronises. */
 int pepo_ws_rows(pepo_ctx* ctx, int inst);
 /* Feature rows of the current state into X_dev (rows beyond max_rows dropped). */

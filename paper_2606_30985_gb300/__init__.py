@@ -62,7 +62,7 @@ EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trot
            "pepo_launch_count", "pepo_last_error", "pepo_destroy",
            "pepo_mlp_num_params", "pepo_mlp_required_bytes", "pepo_mlp_init", "pepo_mlp_get_params",
            "pepo_mlp_forward", "pepo_mlp_gradient", "pepo_mlp_adam_step", "pepo_mlp_destroy",
-           "pepo_ws_rows", "pepo_ws_features", "pepo_ws_targets", "pepo_ws_apply"]
+           "pepo_ws_rows", "pepo_ws_features", "pepo_ws_targets", "pepo_ws_apply", "pepo_set_warmstart_weights"]
 
 _lib = None
 
@@ -157,6 +157,8 @@ def load_library(path=LIB_PATH):
     lib.pepo_ws_targets.restype = I
     lib.pepo_ws_apply.argtypes = [P, I, P, F]
     lib.pepo_ws_apply.restype = I
+    lib.pepo_set_warmstart_weights.argtypes = [P, P, S]
+    lib.pepo_set_warmstart_weights.restype = I
     lib.pepo_get_message.argtypes = [P, I, I, I, ctypes.POINTER(D), ctypes.POINTER(I)]
     lib.pepo_get_message.restype = I
     lib.pepo_num_bonds.argtypes = [P, I]
@@ -208,6 +210,7 @@ class Config:
     gateset: str = "ZZ_X"
     precision: str = "fp32"
     inflight_sites: int = 0
+    warm_start: int = 0
 
     def to_c(self):
         c = _Config()
@@ -224,7 +227,7 @@ class Config:
         c.pinv_rel = self.pinv_rel
         c.gates = GATES[self.gateset]
         c.prec = PRECISIONS[self.precision]
-        c.warm_start = 0
+        c.warm_start = int(self.warm_start)
         c.inflight_sites = self.inflight_sites
         return c
 
@@ -482,6 +485,16 @@ class Engine:
             raise PepoError("ws_apply: gamma must lie in [0, 1]")
         self._check(self.lib.pepo_ws_apply(self.ctx, inst, ctypes.c_void_p(y.data_ptr()), ctypes.c_float(gamma)),
                     "pepo_ws_apply")
+
+    def set_warmstart_weights(self, params):
+        """Install the warm-start network for pepo_bp_converge (instances
+        created with warm_start=1): params is a device float32 tensor of
+        pepo_mlp_num_params entries (e.g. a trained Mlp's parameters)."""
+        import torch
+        n = int(self.lib.pepo_mlp_num_params())
+        _device_tensor(params, torch.float32, n, "set_warmstart_weights")
+        self._check(self.lib.pepo_set_warmstart_weights(self.ctx, ctypes.c_void_p(params.data_ptr()), 4 * n),
+                    "pepo_set_warmstart_weights")
 
     def ws_warm_start(self, mlp, inst=0, gamma=WS_GAMMA):
         """Predict the converged message diagonals with `mlp` and install them

@@ -173,6 +173,13 @@ struct pepo_ctx {
   std::string err;
   bool stepped = false;
   pepo_tuning tune = {kLegSplits, kGramSplits};
+  // learned warm start applied inside pepo_bp_converge to the instances with
+  // warm_start = 1 (workspace carved only when such an instance exists)
+  MlpBuffers ws_mlp{};
+  float* ws_X = nullptr;
+  float* ws_y = nullptr;
+  int ws_rows_max = 0;
+  bool ws_ready = false;
   // kernel-class timing
   bool timing = false;
   std::vector<char> host_items;          // host copy of the item arrays
@@ -1074,6 +1081,20 @@ size_t layout_arena(pepo_ctx* c, char* base, Planner* keep) {
   c->d_kerr = cv.take<int>(1);
   c->d_active = cv.take<int>(c->n_inst);
   c->d_items = cv.take<char>(P.st.bytes.size() + 256);
+  // warm-start workspace: one network and one feature / prediction buffer
+  // sized for the largest instance (instances are handled one after another)
+  int ws_rows = 0;
+  for (int i = 0; i < c->n_inst; ++i)
+    if (c->inst[i].cfg.warm_start)
+      ws_rows = std::max(ws_rows, 2 * c->inst[i].nb * c->inst[i].cfg.chi_max);
+  c->ws_rows_max = ws_rows;
+  if (ws_rows > 0) {
+    MlpBuffers tmp;
+    char* mbase = cv.take<char>(mlp_layout(nullptr, ws_rows, &tmp));
+    if (base) mlp_layout(mbase, ws_rows, &c->ws_mlp);
+    c->ws_X = cv.take<float>((size_t)ws_rows * PEPO_WS_FEATURES);
+    c->ws_y = cv.take<float>((size_t)ws_rows);
+  }
   size_t total = cv.off + kAlign;
   if (keep) *keep = std::move(P);
   return total;
@@ -1758,8 +1779,36 @@ pepo_status pepo_trotter_step(pepo_ctx* c, int n_steps) {
   return st;
 }
 
+// The learned warm start of the instances with warm_start = 1: features of
+// the current state, the network's prediction of the converged message
+// diagonals, and the blended diagonal start (gamma 0.25) written into their
+// messages before the BP sweeps.  The forward pass runs over the instance's
+// row capacity (2 nb chi_max); the features and the writer use the live rows
+// only, so the rows beyond them are never read.
+static pepo_status ws_apply_all(pepo_ctx* c) {
+  constexpr float kGamma = 0.25f;
+  for (int i = 0; i < c->n_inst; ++i) {
+    Inst& I = c->inst[i];
+    if (!I.cfg.warm_start) continue;
+    const int cap = 2 * I.nb * I.cfg.chi_max;
+    const float t = (float)(I.steps * I.cfg.dt);
+    cudaError_t e = launch_ws_features(I.ws_geom, I.nb, c->d_ival + I.chi0, I.lam, I.cfg.chi_max, t,
+                                       (float)I.cfg.h, (float)I.cfg.J, c->ws_X, cap, c->stream);
+    if (e == cudaSuccess) e = mlp_forward(c->ws_mlp, c->ws_X, cap, c->ws_y, c->stream);
+    if (e == cudaSuccess)
+      e = launch_ws_apply(I.nb, c->d_ival + I.chi0, c->ws_y, I.msg, I.cfg.chi_max, kGamma, c->stream);
+    c->launches += 3;
+    if (e != cudaSuccess) return fail(c, PEPO_E_CUDA, "warm start: %s", cudaGetErrorString(e));
+  }
+  return PEPO_OK;
+}
+
 pepo_status pepo_bp_converge(pepo_ctx* c, int* sweeps_out, double* delta_out) {
   if (!c) return PEPO_E_INVALID;
+  if (c->ws_ready) {
+    const pepo_status ws = ws_apply_all(c);
+    if (ws != PEPO_OK) return ws;
+  }
   timing_begin(c);
   pepo_status st = c->tsize == 8 ? do_bp<double>(c, sweeps_out, delta_out) : do_bp<float>(c, sweeps_out, delta_out);
   timing_harvest(c);
@@ -2092,6 +2141,20 @@ pepo_status pepo_mlp_init(void* dev_buf, size_t bytes, int max_rows, const float
   ok = ok && cudaStreamSynchronize(m->stream) == cudaSuccess;
   if (!ok) { delete m; return PEPO_E_CUDA; }
   *out = m;
+  return PEPO_OK;
+}
+
+pepo_status pepo_set_warmstart_weights(pepo_ctx* c, const void* dev_weights, size_t bytes) {
+  if (!c) return PEPO_E_INVALID;
+  const size_t want = sizeof(float) * (size_t)mlp_num_params();
+  if (!dev_weights || bytes != want)
+    return fail(c, PEPO_E_INVALID, "warm-start weights: %zu bytes given, %zu expected", bytes, want);
+  if (c->ws_rows_max == 0)
+    return fail(c, PEPO_E_STATE, "warm-start weights: no instance was created with warm_start = 1");
+  if (cudaMemcpyAsync(c->ws_mlp.p, dev_weights, want, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "warm-start weights: copy failed");
+  c->ws_ready = true;
   return PEPO_OK;
 }
 
