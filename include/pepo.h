@@ -273,7 +273,7 @@ void pepo_mlp_destroy(pepo_mlp* mlp);
  * holds the workspace only when some instance has warm_start = 1.  Errors:
  * PEPO_E_INVALID (bytes != pepo_mlp_num_params * 4, NULL weights),
  * PEPO_E_STATE (no instance has warm_start = 1), PEPO_E_CUDA.  Synchronises
- * the stream.  Not yet run on a GPU: the composed calls are tested one by one. */
+ * the stream. */
 pepo_status pepo_set_warmstart_weights(pepo_ctx* ctx, const void* dev_weights, size_t bytes);
 /* Row count of instance inst (-1 on error).  Synchronises. */
 int pepo_ws_rows(pepo_ctx* ctx, int inst);
