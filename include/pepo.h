@@ -70,8 +70,11 @@ typedef enum {
 typedef enum {
   PEPO_FP64 = 0,        /* site tensors and all arithmetic in double */
   PEPO_FP32 = 1,        /* site tensors float; small linear algebra double */
-  PEPO_TF32X3 = 2,      /* reserved: split-precision tensor-core GEMMs */
-  PEPO_BF16X3 = 3       /* reserved */
+  PEPO_TF32X3 = 2,      /* site tensors float; absorb, BP and reconstruct contractions on
+                           tcgen05 as three TF32 products (hi*hi + hi*lo + lo*hi, FP32
+                           accumulation); factorisations in double.  chi_max > 128
+                           runs the FP32 (CUDA-core) kernels instead */
+  PEPO_BF16X3 = 3       /* accepted; runs the PEPO_TF32X3 kernels (no BF16 split is built) */
 } pepo_precision;
 
 typedef struct {
