@@ -51,6 +51,26 @@ def dist_env():
     return rank, world, local
 
 
+def init_dist(world):
+    """Process group for N > 1 ranks (one process per GPU): NCCL between GPUs,
+    gloo where no GPU is visible (host-side tests).  Nothing for one rank."""
+    if world <= 1:
+        return
+    import torch
+    torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum of a list of floats over all ranks, returned on
+    every rank; the list itself when no process group is running."""
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def workload(args):
     w = dict(WORKLOAD)
     if args.chi:
@@ -279,11 +299,7 @@ def run_gpu(args, rank, world, local):
     launches = eng.launches() - l0
     ms = e0.elapsed_time(e1)
     timing = eng.timing()
-    # max over ranks
-    if dist:
-        t = torch.tensor([ms, wall], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, wall = float(t[0]), float(t[1])
+    ms, wall = max_over_ranks([ms, wall], "cuda:%d" % local)
     steps_total = args.steps * world
     value = steps_total / (ms / 1e3)
     hbm, bf16, src = peaks()
@@ -440,10 +456,7 @@ def run_batched(args, rank, world, local):
     wall = time.perf_counter() - h0
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms, wall], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, wall = float(t[0]), float(t[1])
+    ms, wall = max_over_ranks([ms, wall], "cuda:%d" % local)
     n_units = len(cfgs) * args.steps * world
     out = {
         "metric": "instance-steps/s, 64 batched TFIM instances (gates + BP + Bethe C(t))",
@@ -469,9 +482,7 @@ def main():
     args = parse()
     rank, world, local = dist_env()
     if args.workload == "c3" and args.impl != "reference":
-        if world > 1:
-            import torch
-            torch.distributed.init_process_group("nccl")
+        init_dist(world)
         out = run_batched(args, rank, world, local)
         if rank == 0:
             print(json.dumps(out))
@@ -484,9 +495,7 @@ def main():
             return
         print(json.dumps(run_reference(args, rank, world)))
         return
-    if world > 1:
-        import torch
-        torch.distributed.init_process_group("nccl")
+    init_dist(world)
     out = run_gpu(args, rank, world, local)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
