@@ -64,3 +64,28 @@ def test_required_bytes_follow_the_memory_model(lib):
     m_psi = (4 * chi ** 2 + 2 * (k + l - 4) * chi ** 3 + (k - 2) * (l - 2) * chi ** 4) * 4 * 4
     need = pkg.required_bytes(pkg.Config(Lx=k, Ly=l, chi_max=chi))
     assert m_psi < need < 180e9
+
+
+@pytest.mark.parametrize("field,value", [
+    ("bp_alpha", 0.0), ("bp_alpha", 1.5), ("bp_tol", 0.0), ("bp_max_sweeps", 0),
+    ("eps_cut", -1e-3), ("chi_max", 0), ("h", float("nan")), ("dt", float("inf")),
+    ("inflight_sites", -1)])
+def test_required_bytes_rejects_each_invalid_field(lib, field, value):
+    assert pkg.required_bytes(pkg.Config(Lx=3, Ly=3, chi_max=8)) > 0
+    cfg = pkg.Config(Lx=3, Ly=3, chi_max=8)
+    setattr(cfg, field, value)
+    assert pkg.required_bytes(cfg) == 0
+
+
+def test_required_bytes_rejects_invalid_raw_fields(lib):
+    def raw(**kw):
+        c = pkg.Config(Lx=3, Ly=3, chi_max=8).to_c()
+        for k, v in kw.items():
+            setattr(c, k, v)
+        arr = (pkg._Config * 1)(c)
+        return int(lib.pepo_required_bytes(arr, 1))
+    assert raw() > 0
+    assert raw(obs_pauli=0) == 0 and raw(obs_pauli=4) == 0
+    assert raw(gates=2) == 0 and raw(prec=4) == 0 and raw(prec=-1) == 0
+    assert raw(Lx=65, Ly=65) == 0                      # more than 4096 sites
+    assert raw(Lx=2, Ly=1, obs_x=1, obs_y=0) > 0       # a two-site chain is a valid grid
