@@ -119,7 +119,16 @@ typedef struct {
   int steps;               /* Trotter steps taken so far */
   int core_sweeps32_max;   /* max FP32 (preconditioning) Jacobi sweeps of a bond core, last step */
   int core_sweeps64_max;   /* max FP64 Jacobi sweeps of a bond core, last step */
+  int c_drop;              /* Sec. 6.3 remediation check: |C| fell below half of the previous
+                              layer's with no jump of gate_err (pepo_c_drop); with trap_type1
+                              it marks a trapped layer.  0 without a previous layer measured
+                              since the last state upload or restore */
 } pepo_diag;
+
+/* Sec. 6.3 (trap remediation, second check): 1 if |C| < |C_prev| / 2 while
+ * the discarded weight did not jump, gate_err <= 2 max(gate_err_prev, 1e-12);
+ * 0 otherwise or when an argument is not finite.  Pure host function. */
+int pepo_c_drop(double C_prev, double gate_err_prev, double C, double gate_err);
 
 /* Fill *cfg with the paper's defaults (Sec. 6: eps_cut 1e-11, tol 1e-5,
  * 100 sweeps, thresholds 150/150) and the ZZ_X gate set, 3x3 grid. */

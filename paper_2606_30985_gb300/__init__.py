@@ -47,7 +47,8 @@ class _Diag(ctypes.Structure):
                 ("bp1_delta", ctypes.c_double), ("entropy_frac_max", ctypes.c_double),
                 ("trap_type1", ctypes.c_int), ("trap_type2", ctypes.c_int),
                 ("norm_exploded", ctypes.c_int), ("flags", ctypes.c_int), ("steps", ctypes.c_int),
-                ("core_sweeps32_max", ctypes.c_int), ("core_sweeps64_max", ctypes.c_int)]
+                ("core_sweeps32_max", ctypes.c_int), ("core_sweeps64_max", ctypes.c_int),
+                ("c_drop", ctypes.c_int)]
 
 
 class _Tuning(ctypes.Structure):
@@ -62,7 +63,8 @@ EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trot
            "pepo_launch_count", "pepo_last_error", "pepo_destroy",
            "pepo_mlp_num_params", "pepo_mlp_required_bytes", "pepo_mlp_init", "pepo_mlp_get_params",
            "pepo_mlp_forward", "pepo_mlp_gradient", "pepo_mlp_adam_step", "pepo_mlp_destroy",
-           "pepo_ws_rows", "pepo_ws_features", "pepo_ws_targets", "pepo_ws_apply", "pepo_set_warmstart_weights"]
+           "pepo_ws_rows", "pepo_ws_features", "pepo_ws_targets", "pepo_ws_apply", "pepo_set_warmstart_weights",
+           "pepo_c_drop"]
 
 _lib = None
 
@@ -102,6 +104,8 @@ def load_library(path=LIB_PATH):
     CP = ctypes.POINTER(_Config)
     lib.pepo_config_default.argtypes = [CP]
     lib.pepo_config_default.restype = None
+    lib.pepo_c_drop.argtypes = [ctypes.c_double] * 4
+    lib.pepo_c_drop.restype = ctypes.c_int
     lib.pepo_required_bytes.argtypes = [CP, I]
     lib.pepo_required_bytes.restype = S
     lib.pepo_init.argtypes = [CP, I, P, S, P, ctypes.POINTER(P)]

@@ -146,6 +146,10 @@ struct Inst {
   int saved_steps = 0;       // step count stored with the last pepo_save_state
   int last_sweeps = 0, last_sweeps1 = 0;
   double last_delta = 0, last_delta1 = 0;
+  // the last measurement (pepo_correlator) and the one of the layer before
+  // it, both since the last change of state from the host (c_drop signal)
+  int meas_valid = 0, meas_steps = 0, prev_valid = 0;
+  double meas_C = 0, meas_ge = 0, prev_C = 0, prev_ge = 0;
   int cap[5] = {0, 0, 0, 0, 0};   // in-flight sites per degree class
   int scratch_ref[5] = {-1, -1, -1, -1, -1};   // one scratch slab per class (uploads)
 };
@@ -1571,15 +1575,28 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
     I.last_sweeps1 = sweeps[i];
     I.last_delta1 = delta[i];
     if (C_out) C_out[i] = out[0];
+    double ge = 0.0;
+    if (I.steps > 0) for (double x : disc) ge += x;
+    // previous layer: the last measurement at a smaller step count (a repeated
+    // measurement of the same layer keeps the layer before it)
+    if (I.meas_valid && I.meas_steps < I.steps) {
+      I.prev_valid = 1;
+      I.prev_C = I.meas_C;
+      I.prev_ge = I.meas_ge;
+    }
+    const int drop = I.prev_valid ? pepo_c_drop(I.prev_C, I.prev_ge, out[0], ge) : 0;
+    I.meas_valid = 1;
+    I.meas_steps = I.steps;
+    I.meas_C = out[0];
+    I.meas_ge = ge;
     if (diag_out) {
       pepo_diag& d = diag_out[i];
       std::memset(&d, 0, sizeof d);
       d.C = out[0];
       d.C_proj = out[1];
       d.log_norm = out[4];
-      double ge = 0.0;
-      if (I.steps > 0) for (double x : disc) ge += x;
       d.gate_err = ge;
+      d.c_drop = drop;
       d.bp_sweeps = I.last_sweeps;
       d.bp_delta = I.last_delta;
       d.bp1_sweeps = sweeps[i];
@@ -1617,6 +1634,14 @@ std::vector<int> boundary_layout(const SiteG& S) { return layout_for(S, S.upd[0]
 
 // =================================================================== C ABI
 extern "C" {
+
+int pepo_c_drop(double C_prev, double gate_err_prev, double C, double gate_err) {
+  if (!std::isfinite(C_prev) || !std::isfinite(C) || !std::isfinite(gate_err_prev) || !std::isfinite(gate_err))
+    return 0;
+  const bool dropped = std::fabs(C) < 0.5 * std::fabs(C_prev);
+  const bool jump = gate_err > 2.0 * std::max(gate_err_prev, 1e-12);
+  return (dropped && !jump) ? 1 : 0;
+}
 
 void pepo_config_default(pepo_config* cfg) {
   if (!cfg) return;
@@ -1905,6 +1930,7 @@ pepo_status pepo_set_bonds(pepo_ctx* c, int inst, const int* chi, const double* 
   for (int b = 0; b < I.nb; ++b)
     if (chi[b] < 1 || chi[b] > chimax) return fail(c, PEPO_E_INVALID, "chi of bond %d out of range", b);
   std::vector<int> chiv(chi, chi + I.nb);
+  I.meas_valid = I.prev_valid = 0;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
       cudaMemcpy(c->d_ival + I.chi0, chiv.data(), sizeof(int) * I.nb, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->d_ival + I.pend0, chiv.data(), sizeof(int) * I.nb, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1920,6 +1946,7 @@ pepo_status pepo_set_site(pepo_ctx* c, int inst, int site, const void* data, int
   Inst& I = c->inst[inst];
   if (site < 0 || site >= I.N || !data || (dtype != 0 && dtype != 1))
     return fail(c, PEPO_E_INVALID, "bad site upload arguments");
+  I.meas_valid = I.prev_valid = 0;
   const SiteG& S = I.sites[site];
   std::vector<int> chi(I.nb);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
@@ -1997,6 +2024,7 @@ pepo_status pepo_set_site_static(pepo_ctx* c, int inst, int site, const void* da
   const size_t ts = c->tsize;
   if ((dtype == 0) != (ts == 4))
     return fail(c, PEPO_E_INVALID, "static upload needs the storage type (%s)", ts == 4 ? "float" : "double");
+  I.meas_valid = I.prev_valid = 0;
   const SiteG& S = I.sites[site];
   void* stage = nullptr;
   pepo_status st = static_stage(c, &stage);
@@ -2103,7 +2131,10 @@ pepo_status pepo_save_state(pepo_ctx* c, int inst, void* dev_buf, size_t bytes) 
 
 pepo_status pepo_load_state(pepo_ctx* c, int inst, const void* dev_buf, size_t bytes) {
   pepo_status st = state_copy(c, inst, const_cast<char*>(static_cast<const char*>(dev_buf)), bytes, false);
-  if (st == PEPO_OK) c->inst[inst].steps = c->inst[inst].saved_steps;
+  if (st == PEPO_OK) {
+    c->inst[inst].steps = c->inst[inst].saved_steps;
+    c->inst[inst].meas_valid = c->inst[inst].prev_valid = 0;
+  }
   return st;
 }
 
