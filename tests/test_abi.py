@@ -89,3 +89,44 @@ def test_required_bytes_rejects_invalid_raw_fields(lib):
     assert raw(gates=2) == 0 and raw(prec=4) == 0 and raw(prec=-1) == 0
     assert raw(Lx=65, Ly=65) == 0                      # more than 4096 sites
     assert raw(Lx=2, Ly=1, obs_x=1, obs_y=0) > 0       # a two-site chain is a valid grid
+
+
+def test_every_context_call_refuses_a_null_context(lib):
+    # host-side guards: no CUDA call is reached
+    null = None
+    I, D = ctypes.c_int, ctypes.c_double
+    assert lib.pepo_trotter_step(null, 1) == 1
+    assert lib.pepo_bp_converge(null, None, None) == 1
+    assert lib.pepo_correlator(null, None, None) == 1
+    assert lib.pepo_get_spectrum(null, 0, 0, (D * 4)(), ctypes.byref(I())) == 1
+    assert lib.pepo_set_site(null, 0, 0, None, 0, 0) == 1
+    assert lib.pepo_save_state(null, 0, None, 0) == 1
+    assert lib.pepo_load_state(null, 0, None, 0) == 1
+    assert lib.pepo_set_timing(null, 1) == 1 and lib.pepo_reset_timing(null) == 1
+    assert lib.pepo_set_tuning(null, ctypes.byref(pkg._Tuning())) == 1
+    assert lib.pepo_get_tuning(null, ctypes.byref(pkg._Tuning())) == 1
+    assert lib.pepo_set_warmstart_weights(null, None, 0) == 1
+    assert lib.pepo_state_bytes(null, 0) == 0 and lib.pepo_num_bonds(null, 0) == 0
+    assert lib.pepo_launch_count(null) == 0
+    assert lib.pepo_last_error(null)          # a message, not a null pointer
+    lib.pepo_destroy(null)                    # a no-op
+
+
+def test_init_refusals_happen_before_any_device_access(lib):
+    cfg = pkg.Config(Lx=3, Ly=3, chi_max=8).to_c()
+    arr = (pkg._Config * 1)(cfg)
+    need = int(lib.pepo_required_bytes(arr, 1))
+    fake = ctypes.c_void_p(1 << 20)              # aligned, never dereferenced on these paths
+    out = ctypes.c_void_p(123)
+
+    def init(cfgs=arr, n=1, arena=fake, nbytes=need, outp=True):
+        out.value = 123
+        return lib.pepo_init(cfgs, n, arena, nbytes, None, ctypes.byref(out) if outp else None)
+
+    assert init(nbytes=need - 1) == 2 and not out.value          # PEPO_E_OOM, *out = NULL
+    assert init(nbytes=0) == 2 and not out.value
+    assert init(arena=ctypes.c_void_p((1 << 20) + 8)) == 1 and not out.value   # misaligned
+    assert init(arena=None) == 1 and init(n=0) == 1 and init(cfgs=None) == 1
+    assert init(outp=False) == 1
+    bad = pkg.Config(Lx=3, Ly=3, chi_max=8, bp_alpha=0.0).to_c()
+    assert init(cfgs=(pkg._Config * 1)(bad)) == 1 and not out.value
