@@ -130,3 +130,23 @@ def test_init_refusals_happen_before_any_device_access(lib):
     assert init(outp=False) == 1
     bad = pkg.Config(Lx=3, Ly=3, chi_max=8, bp_alpha=0.0).to_c()
     assert init(cfgs=(pkg._Config * 1)(bad)) == 1 and not out.value
+
+
+def test_mlp_entry_points_refuse_bad_arguments_on_the_host(lib):
+    n = int(lib.pepo_mlp_num_params())
+    assert n > 0
+    assert lib.pepo_mlp_required_bytes(0) == 0
+    need = int(lib.pepo_mlp_required_bytes(64))
+    assert need > 4 * n
+    params = (ctypes.c_float * n)()
+    out = ctypes.c_void_p(123)
+    fake = ctypes.c_void_p(1 << 20)
+    assert lib.pepo_mlp_init(fake, need - 1, 64, params, None, ctypes.byref(out)) == 2 and not out.value
+    assert lib.pepo_mlp_init(ctypes.c_void_p((1 << 20) + 4), need, 64, params, None, ctypes.byref(out)) == 1
+    assert lib.pepo_mlp_init(fake, need, 0, params, None, ctypes.byref(out)) == 1
+    assert lib.pepo_mlp_init(fake, need, 64, None, None, ctypes.byref(out)) == 1
+    assert lib.pepo_mlp_forward(None, fake, 1, fake) == 1
+    assert lib.pepo_mlp_gradient(None, fake, fake, 1, None, None) == 1
+    assert lib.pepo_mlp_adam_step(None, 1e-3) == 1
+    assert lib.pepo_ws_rows(None, 0) == -1
+    lib.pepo_mlp_destroy(None)
