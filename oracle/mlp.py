@@ -1,9 +1,9 @@
 """Learned BP warm start: features, MLP, loss and Adam (oracle, NumPy).
 
 Test infrastructure (like the rest of oracle/): a plain CPU statement of what
-the GPU kernels of the warm start compute.  The paper has no learned part; the
-method is specified by the task's scope (a proposal): per directed bond e and
-Schmidt index k, a small MLP predicts the log of the diagonal of the converged
+the GPU kernels of the warm start compute.  The paper has no learned part
+(its BP starts from the gate-time messages).  The extension: per directed
+bond e and Schmidt index k, a small MLP predicts the log of the diagonal of the converged
 double-layer message in the bond's Schmidt basis, and damped BP then runs
 to its tolerance from the trace-1 diagonal that blends the prediction
 exp(y) / sum(exp(y)) with the diag(lambda) start by a weight gamma.
