@@ -237,8 +237,7 @@ pepo_status pepo_set_site_static(pepo_ctx* ctx, int inst, int site, const void* 
 
 /* ---- Learned BP warm start ------------------------------------------------
  * The paper has no learned part (it motivates one by BP's sweep counts and
- * fixed-point traps, Sec. 6.3); this is the warm-start proposal of the
- * hot-path scope.  Rows are (bond b, direction dir, Schmidt index k < chi_b)
+ * fixed-point traps, Sec. 6.3); this is an extension of the method.  Rows are (bond b, direction dir, Schmidt index k < chi_b)
  * in bond order, dir 0 = first site -> second site; pepo_ws_rows gives their
  * number (sum of 2 chi_b).  A row has PEPO_WS_FEATURES floats:
  *   log lam_k, k / chi_b, S_b / log chi_b, deg(src) / 4, deg(dst) / 4,

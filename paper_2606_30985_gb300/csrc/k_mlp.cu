@@ -1,6 +1,6 @@
 // Learned BP warm start: feature rows, a 3-layer MLP (forward, backward,
-// Adam) and the message writer.  The paper has no learned part; this is the
-// warm-start proposal of the hot-path scope: per directed bond e and Schmidt
+// Adam) and the message writer.  The paper has no learned part; in this
+// extension of the method, per directed bond e and Schmidt
 // index k the MLP predicts y = log diag(M_e)[k] of the converged double-layer
 // message (Eq. 13 fixed point) in the bond's Schmidt basis, and damped BP then
 // starts from M_e = diag(exp(y)) / sum exp(y).

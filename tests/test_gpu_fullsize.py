@@ -1,4 +1,4 @@
-"""Parity at the benchmark's full size on sampled outputs.
+"""Parity at the full 10x10, chi_max = 100 size on sampled outputs.
 
 The 10x10, chi_max = 100 FP32 workload of bench.py is started from its seeded
 synthetic saturated state and advanced one Trotter step on the GPU.  The
