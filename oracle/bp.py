@@ -28,8 +28,10 @@ N = 1 it is the paper's Eq. 9.
 Pinned by: tests/test_oracle_pepo.py -- on trees (1 x N chains and the star
 around an edge site) BP is exact, so the Bethe value must equal the dense
 C(t), including the negative values of cos(2 J t)^3.  On loops the Bethe
-value itself has no closed form: parity unpinned for the loopy Bethe number
-(only the tree pins cover this code).
+value has no closed form; it is pinned by the values the paper prints for
+the 4x4 grid at chi = 40 (tests/test_oracle_paper_4x4.py, a long test run
+with pytest --runslow): C(1.4) = 0.085 and C(2.0) = 0.0572, where the exact
+dynamics gives 0.0908 and 0.0645.
 """
 import numpy as np
 
