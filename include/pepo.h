@@ -298,6 +298,24 @@ pepo_status pepo_ws_targets(pepo_ctx* ctx, int inst, float* t_dev, int max_rows)
  * prediction alone).  y_dev has pepo_ws_rows entries. */
 pepo_status pepo_ws_apply(pepo_ctx* ctx, int inst, const float* y_dev, float gamma);
 
+/* Change the BP settings of instance inst (-1: every instance) between
+ * calls: damping alpha of Eq. 19 in (0, 1], tolerance tol > 0 of Eq. 14 and
+ * the sweep budget (>= 1), for the following pepo_bp_converge and
+ * pepo_correlator calls.  Used by the Sec. 6.3 trap remediation (retry BP
+ * with another damping).  Synchronises the stream.  Errors: PEPO_E_INVALID
+ * (a value out of range, a bad instance), PEPO_E_CUDA. */
+pepo_status pepo_set_bp_params(pepo_ctx* ctx, int inst, double alpha, double tol, int max_sweeps);
+
+/* All double-layer messages of instance inst as stored: 2 * num_bonds
+ * messages of chi_max x chi_max doubles (message 2 b + dir, row-major, zero
+ * outside the live chi x chi block).  pepo_get_messages copies them to the
+ * host array out; pepo_set_messages replaces them from msgs (same layout),
+ * e.g. to restart BP from the messages a snapshot holds.  Both synchronise
+ * the stream.  Errors: PEPO_E_INVALID (bad instance, NULL array),
+ * PEPO_E_CUDA. */
+pepo_status pepo_get_messages(pepo_ctx* ctx, int inst, double* out);
+pepo_status pepo_set_messages(pepo_ctx* ctx, int inst, const double* msgs);
+
 /* Copy one directed message (chi x chi, row-major) to the host. */
 pepo_status pepo_get_message(pepo_ctx* ctx, int inst, int bond, int dir, double* out,
                              int* chi_out);

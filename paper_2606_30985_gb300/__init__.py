@@ -64,7 +64,7 @@ EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trot
            "pepo_mlp_num_params", "pepo_mlp_required_bytes", "pepo_mlp_init", "pepo_mlp_get_params",
            "pepo_mlp_forward", "pepo_mlp_gradient", "pepo_mlp_adam_step", "pepo_mlp_destroy",
            "pepo_ws_rows", "pepo_ws_features", "pepo_ws_targets", "pepo_ws_apply", "pepo_set_warmstart_weights",
-           "pepo_c_drop"]
+           "pepo_c_drop", "pepo_set_bp_params", "pepo_get_messages", "pepo_set_messages"]
 
 _lib = None
 
@@ -106,6 +106,9 @@ def load_library(path=LIB_PATH):
     lib.pepo_config_default.restype = None
     lib.pepo_c_drop.argtypes = [ctypes.c_double] * 4
     lib.pepo_c_drop.restype = ctypes.c_int
+    lib.pepo_set_bp_params.argtypes = [P, I, D, D, I]
+    lib.pepo_get_messages.argtypes = [P, I, ctypes.POINTER(D)]
+    lib.pepo_set_messages.argtypes = [P, I, ctypes.POINTER(D)]
     lib.pepo_required_bytes.argtypes = [CP, I]
     lib.pepo_required_bytes.restype = S
     lib.pepo_init.argtypes = [CP, I, P, S, P, ctypes.POINTER(P)]
@@ -284,6 +287,7 @@ class Engine:
         if st != 0:
             raise PepoError("pepo_init failed: %s" % STATUS.get(st, st))
         self.ctx = ctx
+        self._bp = [(c.bp_alpha, c.bp_tol, c.bp_max_sweeps) for c in self.cfgs]
         if tuning == "cache":
             from . import autotune
             tuning = autotune.lookup(max(c.chi_max for c in self.cfgs), self.cfgs[0].precision)
@@ -358,6 +362,44 @@ class Engine:
         D = (_Diag * self.n_inst)()
         self._check(self.lib.pepo_correlator(self.ctx, C, D), "pepo_correlator")
         return list(C), [diag_to_dict(d) for d in D]
+
+    # -- BP settings and message snapshots (trap remediation)
+    def set_bp_params(self, alpha, tol=None, max_sweeps=None, inst=-1):
+        """Damping / tolerance / sweep budget of instance inst (-1: all) for the
+        following BP runs (pepo_set_bp_params); None keeps a value."""
+        targets = range(self.n_inst) if inst < 0 else [inst]
+        for i in targets:
+            a0, t0, m0 = self.bp_params(i)
+            t = t0 if tol is None else tol
+            m = m0 if max_sweeps is None else max_sweeps
+            self._check(self.lib.pepo_set_bp_params(self.ctx, i, float(alpha), float(t), int(m)),
+                        "pepo_set_bp_params")
+            self._bp[i] = (float(alpha), float(t), int(m))
+
+    def bp_params(self, inst=0):
+        """(alpha, tol, max_sweeps) in force for instance inst."""
+        return self._bp[inst]
+
+    def get_messages(self, inst=0):
+        """All double-layer messages as stored (2 * num_bonds x chi_max x chi_max)."""
+        cm = self.cfgs[inst].chi_max
+        out = np.zeros((2 * self.num_bonds(inst), cm, cm))
+        self._check(self.lib.pepo_get_messages(self.ctx, inst, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                    "pepo_get_messages")
+        return out
+
+    def set_messages(self, msgs, inst=0):
+        cm = self.cfgs[inst].chi_max
+        m = np.ascontiguousarray(np.asarray(msgs, dtype=np.float64))
+        if m.size != 2 * self.num_bonds(inst) * cm * cm:
+            raise PepoError("set_messages: expected %d values, got %d" % (2 * self.num_bonds(inst) * cm * cm, m.size))
+        self._check(self.lib.pepo_set_messages(self.ctx, inst, m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                    "pepo_set_messages")
+
+    def measure_remediated(self, alphas=None, inst=0):
+        """BP + correlator with the Sec. 6.3 trap remediation (remediation.measure)."""
+        from . import remediation
+        return remediation.measure(self, inst=inst, alphas=alphas or remediation.ALPHAS)
 
     # -- state access
     def num_bonds(self, inst=0):

@@ -2289,6 +2289,64 @@ pepo_status pepo_set_state(pepo_ctx* c, int inst, const double* sites, size_t co
   return PEPO_OK;
 }
 
+pepo_status pepo_get_messages(pepo_ctx* c, int inst, double* out) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst || !out) return fail(c, PEPO_E_INVALID, "bad arguments");
+  Inst& I = c->inst[inst];
+  const size_t n = (size_t)2 * I.nb * I.cfg.chi_max * I.cfg.chi_max;
+  if (cudaMemcpyAsync(out, I.msg, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "message readback");
+  return PEPO_OK;
+}
+
+pepo_status pepo_set_messages(pepo_ctx* c, int inst, const double* msgs) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst || !msgs) return fail(c, PEPO_E_INVALID, "bad arguments");
+  Inst& I = c->inst[inst];
+  const size_t n = (size_t)2 * I.nb * I.cfg.chi_max * I.cfg.chi_max;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+      cudaMemcpy(I.msg, msgs, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "message upload");
+  return PEPO_OK;
+}
+
+pepo_status pepo_set_bp_params(pepo_ctx* c, int inst, double alpha, double tol, int max_sweeps) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < -1 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
+  if (!(alpha > 0.0 && alpha <= 1.0)) return fail(c, PEPO_E_INVALID, "bp_alpha must be in (0, 1]");
+  if (!(tol > 0.0)) return fail(c, PEPO_E_INVALID, "bp_tol must be > 0");
+  if (max_sweeps < 1) return fail(c, PEPO_E_INVALID, "bp_max_sweeps must be >= 1");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, PEPO_E_CUDA, "pepo_set_bp_params: %s", cudaGetErrorString(e));
+  // the damping is staged in the message items (per instance, and in the
+  // grouped array of a multi-instance context): patch the host copy of the
+  // items and upload the patched range; captured graphs read the items from
+  // device memory, so they see the new value
+  auto patch = [&](const DArr<MsgItem>& a, size_t first, size_t n) -> bool {
+    if (n == 0) return true;
+    MsgItem* h = reinterpret_cast<MsgItem*>(c->host_items.data() + a.off) + first;
+    for (size_t k = 0; k < n; ++k) h[k].alpha = alpha;
+    return cudaMemcpy(const_cast<MsgItem*>(a.d) + first, h, sizeof(MsgItem) * n, cudaMemcpyHostToDevice) ==
+           cudaSuccess;
+  };
+  size_t gpos = 0;
+  for (int i = 0; i < c->n_inst; ++i) {
+    Inst& I = c->inst[i];
+    const size_t n = (size_t)I.msgs.n;
+    if (inst < 0 || inst == i) {
+      I.cfg.bp_alpha = alpha;
+      I.cfg.bp_tol = tol;
+      I.cfg.bp_max_sweeps = max_sweeps;
+      bool ok = patch(I.msgs, 0, n);
+      if (ok && c->n_inst > 1) ok = patch(c->grp.msgs, gpos, n);
+      if (!ok) return fail(c, PEPO_E_CUDA, "message item upload");
+    }
+    gpos += n;
+  }
+  return PEPO_OK;
+}
+
 pepo_status pepo_get_message(pepo_ctx* c, int inst, int bond, int dir, double* out, int* chi_out) {
   if (!c) return PEPO_E_INVALID;
   if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");

@@ -106,6 +106,8 @@ def test_every_context_call_refuses_a_null_context(lib):
     assert lib.pepo_set_tuning(null, ctypes.byref(pkg._Tuning())) == 1
     assert lib.pepo_get_tuning(null, ctypes.byref(pkg._Tuning())) == 1
     assert lib.pepo_set_warmstart_weights(null, None, 0) == 1
+    assert lib.pepo_set_bp_params(null, 0, 0.5, 1e-5, 100) == 1
+    assert lib.pepo_get_messages(null, 0, None) == 1 and lib.pepo_set_messages(null, 0, None) == 1
     assert lib.pepo_state_bytes(null, 0) == 0 and lib.pepo_num_bonds(null, 0) == 0
     assert lib.pepo_launch_count(null) == 0
     assert lib.pepo_last_error(null)          # a message, not a null pointer
