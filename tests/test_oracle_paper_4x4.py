@@ -14,7 +14,7 @@ oracle's defaults (damping 0.5, tolerance 1e-5, 100 sweeps).
 
 Measured with this test's configuration: C(1.4) = 0.08533, C(2.0) = 0.05715.
 
-About an hour and a half on a few host cores: marked slow (pytest --runslow).
+About 80 minutes on 8 host cores: marked slow (pytest --runslow).
 """
 import os
 
