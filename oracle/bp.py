@@ -52,6 +52,21 @@ def double_message(net, v, k_out, M):
     return _contract_all_but(net.O[v], Y, k_out)
 
 
+def double_update(net, v, k_out, M, alpha):
+    """One damped update of the message that site v sends out of its leg
+    k_out (Eq. 13 contraction, Hermitian part, unit trace, Eq. 19 damping
+    against the previous message M[(v, u)]).  Returns (new, old)."""
+    u = net.legs[v][k_out][1]
+    Mh = double_message(net, v, k_out, M)
+    Mh = 0.5 * (Mh + Mh.conj().T)
+    tr = np.real(np.trace(Mh))
+    if not tr > 0:
+        raise FloatingPointError("double-layer message has no weight")
+    Mh = Mh / tr
+    old = M[(v, u)]
+    return (1.0 - alpha) * old + alpha * Mh, old
+
+
 def bp_double(net, alpha, tol, max_sweeps):
     """Damped Jacobi BP on the double layer; updates net.M in place."""
     M = {k: m.copy() for k, m in net.M.items()}
@@ -61,14 +76,7 @@ def bp_double(net, alpha, tol, max_sweeps):
         delta = 0.0
         for v in range(net.N):
             for k, (_, u) in enumerate(net.legs[v]):
-                Mh = double_message(net, v, k, M)
-                Mh = 0.5 * (Mh + Mh.conj().T)
-                tr = np.real(np.trace(Mh))
-                if not tr > 0:
-                    raise FloatingPointError("double-layer message has no weight")
-                Mh = Mh / tr
-                old = M[(v, u)]
-                Mn = (1.0 - alpha) * old + alpha * Mh
+                Mn, old = double_update(net, v, k, M, alpha)
                 delta = max(delta, float(np.max(np.abs(np.diag(Mn) - np.diag(old)))))
                 newM[(v, u)] = Mn
         M = newM
