@@ -83,6 +83,16 @@ def workload(args):
     return w
 
 
+def site_degrees(w):
+    Lx, Ly = w["Lx"], w["Ly"]
+    return [(y > 0) + (y < Ly - 1) + (x > 0) + (x < Lx - 1) for y in range(Ly) for x in range(Lx)]
+
+
+def site_bytes(w):
+    """FP32 bytes of every site tensor at chi_max (4 chi^deg coefficients)."""
+    return [4 * 4 * w["chi_max"] ** d for d in site_degrees(w)]
+
+
 def workload_name(w):
     return "%dx%d TFIM chi_max=%d saturated Trotter step (gates + BP + Bethe C(t))" % (
         w["Lx"], w["Ly"], w["chi_max"])
@@ -152,7 +162,8 @@ PAPER_STEPS_PER_S_10X10_CHI100 = 1.0 / 1440.0
 # measured DRAM bytes (read + write) per algorithmic byte, per kernel class,
 # with the profile summary it comes from; an entry is removed when its kernel
 # changes (traffic is then reported as null until it is measured again)
-TRAFFIC_RATIO = {"leg_contract": (0.986, "profiles/k_leg_umma_3x3_chi100_dram.md")}
+TRAFFIC_RATIO = {"leg_contract": (0.986, "profiles/k_leg_umma_3x3_chi100_dram.md"),
+                 "bp_leg_contract": (0.986, "profiles/k_leg_umma_3x3_chi100_dram.md")}
 
 
 def fp32_alu_peak_tflops():
@@ -333,7 +344,7 @@ def run_gpu(args, rank, world, local):
     nl = max(1, tk["launches"])
     gbs = (tk["bytes"] / nl) / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
     tfs = (tk["flops"] / nl) / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
-    tensor_mode = w["precision"] in ("tf32x3", "bf16x3")
+    tensor_mode = w["precision"] == "tf32x3"
     alu_peak = fp32_alu_peak_tflops()
     cpeak = bf16 * TF32_PER_BF16 if tensor_mode else alu_peak
     if tfs / cpeak >= gbs / hbm:
@@ -353,10 +364,25 @@ def run_gpu(args, rank, world, local):
                  "algorithmic_bytes_per_launch": tk["bytes"] / nl,
                  "algorithmic_flops_per_launch": tk["flops"] / nl,
                  "achieved_gbs": gbs, "achieved_tflops": tfs})
+    # the bond layer's kernel classes (absorb legs, Cholesky-QR Gram,
+    # Householder, factors, core, reconstruct, environment factors); the BP
+    # classes (bp_leg_contract, gram_leg, bp_env_eig, msg_finish) and the
+    # single-layer contractions are reported apart
     bond_classes = ["leg_contract", "gram_rows", "gram_rows_reduce", "reconstruct", "householder_tsqr",
                     "factor", "core_svd", "env_factor"]
+    bp_classes = ["bp_leg_contract", "gram_leg", "gram_leg_reduce", "bp_env_eig", "msg_finish"]
     # bond-update FLOPs: algorithmic FLOPs of the bond-update kernels over their time
     bu_ms = sum(timing[k]["ms"] for k in bond_classes if k in timing)
+    bp_ms = sum(timing[k]["ms"] for k in bp_classes if k in timing)
+    # the method's minimum HBM bytes per step: each site update reads its
+    # tensor for the Gram and reads + writes it in the reconstruct (3 |psi|),
+    # each BP sweep reads every tensor once
+    psi_bytes = site_bytes(w)
+    deg = site_degrees(w)
+    min_bond = sum(3 * d * b for d, b in zip(deg, psi_bytes))
+    mean_sweeps = float(np.mean(sweeps)) if sweeps else 0.0
+    min_step = min_bond + mean_sweeps * sum(psi_bytes)
+    moved = sum(v["bytes"] for v in timing.values()) / args.steps
     out = {
         "metric": "Trotter steps/s at 10x10 chi=100 (gates + BP + Bethe C(t))",
         "value": value,
@@ -386,6 +412,13 @@ def run_gpu(args, rank, world, local):
         "roofline": roof,
         "bond_update_tflops": (sum(timing[k]["flops"] for k in bond_classes if k in timing) / 1e12
                                / (bu_ms / 1e3)) if bu_ms > 0 else None,
+        "bond_layer_ms_per_step": bu_ms / args.steps,
+        "bp_ms_per_step": bp_ms / args.steps,
+        "step_bytes": {"kernel_algorithmic": moved, "method_minimum": min_step,
+                       "ratio": moved / min_step if min_step > 0 else None,
+                       "method_minimum_hbm_frac": (min_step / (ms / args.steps / 1e3)) / (hbm * 1e9),
+                       "what": "bytes credited to the kernels per step vs the method's minimum (bond layer "
+                               "3 |psi| per site update, one read of every tensor per BP sweep)"},
         "kernel_ms": {k: round(v["ms"], 3) for k, v in timing.items() if v["launches"]},
         "kernel_bytes_per_step": {k: v["bytes"] / args.steps for k, v in timing.items() if v["launches"]},
         "clocks": clk,

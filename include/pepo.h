@@ -58,8 +58,9 @@ typedef enum {
   PEPO_E_OOM = 2,       /* arena smaller than pepo_required_bytes */
   PEPO_E_CUDA = 3,      /* a CUDA runtime call failed */
   PEPO_E_NUMERIC = 4,   /* reserved: numerical trouble is reported in pepo_diag.flags */
-  PEPO_E_STATE = 5      /* a call that needs an earlier setup (warm-start weights without a
-                           warm_start instance) */
+  PEPO_E_STATE = 5      /* a call out of order: warm-start weights without a warm_start
+                           instance, or a call that needs whole steps while a step is
+                           partly applied (pepo_trotter_colour) */
 } pepo_status;
 
 typedef enum {
@@ -74,7 +75,9 @@ typedef enum {
                            tcgen05 as three TF32 products (hi*hi + hi*lo + lo*hi, FP32
                            accumulation); factorisations in double.  chi_max > 128
                            runs the FP32 (CUDA-core) kernels instead */
-  PEPO_BF16X3 = 3       /* accepted; runs the PEPO_TF32X3 kernels (no BF16 split is built) */
+  PEPO_BF16X3 = 3       /* not built: refused with PEPO_E_INVALID by pepo_required_bytes and
+                           pepo_init (a BF16 split needs six BF16 products for FP32-level
+                           accuracy, twice the tensor time of the three TF32 products) */
 } pepo_precision;
 
 typedef struct {
@@ -157,6 +160,20 @@ pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena,
  * non-finite value, a Jacobi sweep cap) does not fail the call: it is
  * reported in pepo_diag.flags by pepo_correlator. */
 pepo_status pepo_trotter_step(pepo_ctx* ctx, int n_steps);
+
+/* Enqueue the bond gates of one colour class (0..3, Sec. 2.4 four-colour
+ * partition) of the current Trotter step on every instance: the colours of a
+ * step are applied in the order 0, 1, 2, 3, and the four calls together do
+ * exactly what one pepo_trotter_step does (the site gates of Eq. 6 are folded
+ * into the first and last bond gate of each site, so they travel with the
+ * colour that holds that bond).  The step counter advances after colour 3.
+ * Used to inspect the state in the middle of a step (pepo_get_site,
+ * pepo_get_spectrum, pepo_get_message): between the calls, every call that needs
+ * whole steps (pepo_trotter_step, BP, the correlator, state uploads,
+ * snapshots, the warm start) fails with PEPO_E_STATE.  Launches directly
+ * (no graph).  Asynchronous.  Errors: PEPO_E_INVALID (NULL context, colour
+ * outside 0..3), PEPO_E_STATE (colour out of order), PEPO_E_CUDA. */
+pepo_status pepo_trotter_colour(pepo_ctx* ctx, int colour);
 
 /* Run damped double-layer BP (Eq. 13-19) to tolerance or the sweep budget.
  * sweeps_out / delta_out: host arrays of n_inst entries (may be NULL).
@@ -355,6 +372,18 @@ typedef struct {
 } pepo_tuning;
 pepo_status pepo_set_tuning(pepo_ctx* ctx, const pepo_tuning* tuning);
 pepo_status pepo_get_tuning(const pepo_ctx* ctx, pepo_tuning* tuning);
+
+/* Limit of every pipeline wait inside the tensor-core (PEPO_TF32X3) kernels,
+ * in seconds, 1e-9 .. 60 (default 4).  A wait that runs longer makes its
+ * kernel leave its loops, let its own MMAs and copies in flight finish
+ * (bounded), free its tensor memory and return instead of hanging; the next
+ * call that reads results (pepo_bp_converge, pepo_correlator) fails with
+ * PEPO_E_CUDA and clears the kernel error word, so the context stays usable,
+ * but its state is undefined until restored (pepo_load_state) or uploaded
+ * again.  A change synchronises the stream and drops captured graphs.
+ * Errors: PEPO_E_INVALID (value out of range), PEPO_E_CUDA.  Not a step of
+ * the paper's method: failure handling of this implementation. */
+pepo_status pepo_set_wait_limit(pepo_ctx* ctx, double seconds);
 
 /* Number of kernel launches enqueued by this context so far. */
 long long pepo_launch_count(const pepo_ctx* ctx);

@@ -55,7 +55,7 @@ class _Tuning(ctypes.Structure):
     _fields_ = [("gram_leg_splits", ctypes.c_int), ("gram_rows_splits", ctypes.c_int)]
 
 
-EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trotter_step",
+EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trotter_step", "pepo_trotter_colour",
            "pepo_bp_converge", "pepo_correlator", "pepo_get_spectrum", "pepo_get_site",
            "pepo_set_state", "pepo_set_bonds", "pepo_set_site", "pepo_set_site_static", "pepo_state_bytes", "pepo_save_state", "pepo_load_state",
            "pepo_get_message", "pepo_num_bonds", "pepo_set_timing", "pepo_set_tuning", "pepo_get_tuning",
@@ -64,7 +64,8 @@ EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trot
            "pepo_mlp_num_params", "pepo_mlp_required_bytes", "pepo_mlp_init", "pepo_mlp_get_params",
            "pepo_mlp_forward", "pepo_mlp_gradient", "pepo_mlp_adam_step", "pepo_mlp_destroy",
            "pepo_ws_rows", "pepo_ws_features", "pepo_ws_targets", "pepo_ws_apply", "pepo_set_warmstart_weights",
-           "pepo_c_drop", "pepo_set_bp_params", "pepo_get_messages", "pepo_set_messages"]
+           "pepo_c_drop", "pepo_set_bp_params", "pepo_get_messages", "pepo_set_messages",
+           "pepo_set_wait_limit"]
 
 _lib = None
 
@@ -115,6 +116,8 @@ def load_library(path=LIB_PATH):
     lib.pepo_init.restype = I
     lib.pepo_trotter_step.argtypes = [P, I]
     lib.pepo_trotter_step.restype = I
+    lib.pepo_trotter_colour.argtypes = [P, I]
+    lib.pepo_trotter_colour.restype = I
     lib.pepo_bp_converge.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(D)]
     lib.pepo_bp_converge.restype = I
     lib.pepo_correlator.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(_Diag)]
@@ -172,6 +175,8 @@ def load_library(path=LIB_PATH):
     lib.pepo_num_bonds.restype = I
     lib.pepo_set_timing.argtypes = [P, I]
     lib.pepo_set_timing.restype = I
+    lib.pepo_set_wait_limit.argtypes = [P, D]
+    lib.pepo_set_wait_limit.restype = I
     lib.pepo_set_tuning.argtypes = [P, ctypes.POINTER(_Tuning)]
     lib.pepo_set_tuning.restype = I
     lib.pepo_get_tuning.argtypes = [P, ctypes.POINTER(_Tuning)]
@@ -324,6 +329,10 @@ class Engine:
         t = _Tuning(int(gram_leg_splits), int(gram_rows_splits))
         self._check(self.lib.pepo_set_tuning(self.ctx, ctypes.byref(t)), "pepo_set_tuning")
 
+    def set_wait_limit(self, seconds):
+        """Limit of every tensor-core pipeline wait (pepo_set_wait_limit)."""
+        self._check(self.lib.pepo_set_wait_limit(self.ctx, float(seconds)), "pepo_set_wait_limit")
+
     def get_tuning(self):
         t = _Tuning()
         self._check(self.lib.pepo_get_tuning(self.ctx, ctypes.byref(t)), "pepo_get_tuning")
@@ -350,6 +359,11 @@ class Engine:
     # -- the four entry points of the method
     def trotter_step(self, n=1):
         self._check(self.lib.pepo_trotter_step(self.ctx, n), "pepo_trotter_step")
+
+    def trotter_colour(self, colour):
+        """Bond gates of one colour class of the current step (colours in the
+        order 0..3; the four together equal trotter_step(1))."""
+        self._check(self.lib.pepo_trotter_colour(self.ctx, int(colour)), "pepo_trotter_colour")
 
     def bp_converge(self):
         sw = (ctypes.c_int * self.n_inst)()

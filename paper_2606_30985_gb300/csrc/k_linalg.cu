@@ -40,8 +40,10 @@ __device__ inline double block_sum(double v, double* red) {
   return t;
 }
 
-// Block-wide argmax over values[i] for i in [lo, hi); returns the index
-// (smallest index among ties).  `ri` needs blockDim.x / 32 ints, `rv` doubles.
+// Block-wide argmax over values[i] for i in [lo, hi) (hi > lo); returns the
+// index (smallest index among ties), always inside [lo, hi): lo when no value
+// exceeds -1 (every value NaN), where the callers' pivot test then stops.
+// `ri` needs blockDim.x / 32 ints, `rv` doubles.
 __device__ inline int block_argmax(const double* values, int lo, int hi, double* rv, int* ri) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double best = -1.0;
@@ -64,7 +66,7 @@ __device__ inline int block_argmax(const double* values, int lo, int hi, double*
   for (int i = 0; i < nw; ++i)
     if (rv[i] > b || (rv[i] == b && ri[i] < idx)) { b = rv[i]; idx = ri[i]; }
   __syncthreads();
-  return idx;
+  return idx < hi ? idx : lo;
 }
 
 // =============================================================== env factor
@@ -527,6 +529,10 @@ cudaError_t launch_factor(const SiteFacItem* items, int n_items, int rmax, int n
 }
 
 // ===================================================================== core
+// Sort key of a singular-value estimate (a norm, >= 0): NaN ranks last, so
+// the ranks of any input form a permutation (every order[] slot written once).
+__device__ inline double rank_key(double x) { return x == x ? x : -1.0; }
+
 // One-sided Jacobi (Hestenes) on the columns of A (m x n, column-major, m >= n),
 // accumulating V (n x n, column-major).  Returns the sweep count; sets
 // *capped when the sweep budget ran out.  abs_rel > 0 also skips a pair whose
@@ -709,7 +715,11 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
     __syncthreads();
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
       int rk = 0;
-      for (int i = 0; i < N; ++i) if (sv[512 + i] > sv[512 + j] || (sv[512 + i] == sv[512 + j] && i < j)) ++rk;
+      const double kj = rank_key(sv[512 + j]);
+      for (int i = 0; i < N; ++i) {
+        const double ki = rank_key(sv[512 + i]);
+        if (ki > kj || (ki == kj && i < j)) ++rk;
+      }
       order[rk] = j;
     }
     __syncthreads();
@@ -790,7 +800,11 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
     __syncthreads();
     for (int j = threadIdx.x; j < NK; j += blockDim.x) {
       int rk = 0;
-      for (int i = 0; i < NK; ++i) if (sv[i] > sv[j] || (sv[i] == sv[j] && i < j)) ++rk;
+      const double kj = rank_key(sv[j]);
+      for (int i = 0; i < NK; ++i) {
+        const double ki = rank_key(sv[i]);
+        if (ki > kj || (ki == kj && i < j)) ++rk;
+      }
       order[rk] = j;
     }
     __syncthreads();

@@ -56,7 +56,7 @@ constexpr int kM = 128;                 // accumulator rows = TMEM lanes
 constexpr int kKC = 32;                 // K values per staged chunk
 constexpr int kTmemCols = 512;          // two accumulators of 256 columns
 constexpr int kRun = 8;                 // Gram chunks per FP32 accumulator run
-constexpr unsigned long long kTimeoutNs = 4000000000ull;
+constexpr unsigned long long kDrainNs = 2000000000ull;   // bound of the exit drains
 constexpr int kMaxItems = 512;
 
 // ---------------------------------------------------------------- PTX helpers
@@ -85,13 +85,16 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 // Bounded wait for the phase of parity `parity`; false once the CTA aborts.
-__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err) {
+// `limit` (ns of %globaltimer) is the launch's wait limit; on expiry the wait
+// records bit 0 in *err and raises the CTA's abort flag.
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err,
+                          unsigned long long limit) {
   if (mbar_try(b, parity)) return true;
   const unsigned long long t0 = gtimer();
   while (true) {
     if (mbar_try(b, parity)) return true;
     if (*abort_flag) return false;
-    if (gtimer() - t0 > kTimeoutNs) {
+    if (gtimer() - t0 > limit) {
       *abort_flag = 1;
       atomicOr(err, 1);
       return false;
@@ -99,9 +102,23 @@ __device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag
   }
 }
 
+// Wait on the way out, also after an abort: the CTA's own MMAs and bulk
+// copies in flight complete before its tensor and shared memory are released.
+// Bounded by kDrainNs (they finish within microseconds); bit 2 in *err if not.
+__device__ void mbar_drain(uint64_t* b, uint32_t parity, int* err) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(b, parity)) {
+    if (gtimer() - t0 > kDrainNs) {
+      atomicOr(err, 4);
+      return;
+    }
+  }
+}
+
 // warp-uniform wait (every lane agrees, so the warp leaves a loop together)
-__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err) {
-  const bool ok = mbar_wait(b, parity, abort_flag, err);
+__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err,
+                                          unsigned long long limit) {
+  const bool ok = mbar_wait(b, parity, abort_flag, err, limit);
   return __all_sync(0xffffffffu, ok);
 }
 // one arrival per warp once every lane's shared-memory writes are ordered
@@ -322,7 +339,7 @@ struct LegBars {
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* const* ptrs,
-           const int* __restrict__ ival, int* err) {
+           const int* __restrict__ ival, int* err, unsigned long long lim) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const LegSmem P = leg_smem(chimax);
@@ -369,10 +386,10 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
       uint32_t st_ph = 0;
       int item_n = 0;
       bool ok = true;
-      if (live) ok = mbar_wait(&bars->bfull, 0, abort_flag, err);
+      if (live) ok = mbar_wait(&bars->bfull, 0, abort_flag, err, lim);
       while (live && ok) {
         const int b = (int)(tc & 1);
-        if (!mbar_wait(&bars->accempty[b], (uint32_t)(((tc >> 1) & 1) ^ 1), abort_flag, err)) break;
+        if (!mbar_wait(&bars->accempty[b], (uint32_t)(((tc >> 1) & 1) ^ 1), abort_flag, err, lim)) break;
         tc_after();
         const uint32_t d_tmem = tmem + (uint32_t)(b * 256);
         const int N16 = c.L.N16, K8 = c.L.K8;
@@ -381,7 +398,7 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
         const int nkc = (K8 + kKC - 1) / kKC;
         for (int kc = 0; kc < nkc && ok; ++kc) {
           const int s = st_i;
-          if (!mbar_wait(&bars->full[s], st_ph, abort_flag, err)) { ok = false; break; }
+          if (!mbar_wait(&bars->full[s], st_ph, abort_flag, err, lim)) { ok = false; break; }
           if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
           tc_after();
           const uint32_t a_hi = su32(As + (size_t)s * P.stage_bytes);
@@ -406,13 +423,13 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
         if (last) break;
         if (changed) {
           ++item_n;
-          if (!mbar_wait(&bars->bfull, (uint32_t)(item_n & 1), abort_flag, err)) break;
+          if (!mbar_wait(&bars->bfull, (uint32_t)(item_n & 1), abort_flag, err, lim)) break;
           tc_after();
         }
       }
       // every issued MMA completes before tensor memory is released
       mma_commit(&bars->drain);
-      mbar_wait(&bars->drain, 0, abort_flag, err);
+      mbar_drain(&bars->drain, 0, err);
     }
     __syncwarp();
   } else if (warp >= 4 && warp < 8) {
@@ -424,7 +441,7 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
     long long tc = 0;
     while (live) {
       const int b = (int)(tc & 1);
-      if (!warp_wait(&bars->accfull[b], (uint32_t)((tc >> 1) & 1), abort_flag, err)) break;
+      if (!warp_wait(&bars->accfull[b], (uint32_t)((tc >> 1) & 1), abort_flag, err, lim)) break;
       tc_after();
       const LegDims& L = c.L;
       const long long rg = c.tile * kM + row;
@@ -538,7 +555,7 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
       const LegDims& L = c.L;
       load_next(vl);
       if (need_b) {
-        if (item_n > 0 && !warp_wait(&bars->bfree, (uint32_t)((item_n - 1) & 1), abort_flag, err)) return false;
+        if (item_n > 0 && !warp_wait(&bars->bfree, (uint32_t)((item_n - 1) & 1), abort_flag, err, lim)) return false;
         // [Ah; Al]: rows n < N16 hold hi(A[n, :]), rows N16 + n hold lo(A[n, :]);
         // one block of 2 N16 rows per 32-wide K chunk
         const size_t bblk = (size_t)(2 * L.N16) * 128;
@@ -559,7 +576,7 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
         need_b = false;
       }
       const int s = st_i;
-      if (!warp_wait(&bars->empty[s], st_ph ^ 1u, abort_flag, err)) return false;
+      if (!warp_wait(&bars->empty[s], st_ph ^ 1u, abort_flag, err, lim)) return false;
       if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
       unsigned char* hi = As + (size_t)s * P.stage_bytes;
       unsigned char* lo = hi + P.stage_bytes / 2;
@@ -839,7 +856,7 @@ struct GramLoader {
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, int chimax, void* const* ptrs,
-            const int* __restrict__ ival, int* err) {
+            const int* __restrict__ ival, int* err, unsigned long long lim) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const GramSmem P = gram_smem(chimax);
@@ -893,13 +910,13 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
         const uint32_t id = idesc_tf32(kM, 2 * F8);
         for (long long c = g.c; c < g.c1 && ok;) {
           const int b = (int)(rc & 1);
-          if (!mbar_wait(&bars->accempty[b], (uint32_t)(((rc >> 1) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
+          if (!mbar_wait(&bars->accempty[b], (uint32_t)(((rc >> 1) & 1) ^ 1), abort_flag, err, lim)) { ok = false; break; }
           tc_after();
           const uint32_t d_tmem = tmem + (uint32_t)(b * 256);
           const long long cend = min(g.c1, c + kRun);
           for (long long cr = c; cr < cend; ++cr) {
             const int s = st_i;
-            if (!mbar_wait(&bars->full[s], st_ph, abort_flag, err)) { ok = false; break; }
+            if (!mbar_wait(&bars->full[s], st_ph, abort_flag, err, lim)) { ok = false; break; }
             if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
             tc_after();
             const uint32_t x0 = su32(Xs + (size_t)s * P.stage_bytes);
@@ -917,7 +934,7 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
         }
       }
       mma_commit(&bars->drain);
-      mbar_wait(&bars->drain, 0, abort_flag, err);
+      mbar_drain(&bars->drain, 0, err);
     }
     __syncwarp();
   } else if (warp >= 4 && warp < 8) {
@@ -936,7 +953,7 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
         for (int c0 = 0; c0 < F8; ++c0) { acc[(size_t)row * P.ld + c0] = 0.f; cmp[(size_t)row * P.ld + c0] = 0.f; }
       for (long long c = g.c; c < g.c1; c += kRun) {
         const int b = (int)(rc & 1);
-        if (!warp_wait(&bars->accfull[b], (uint32_t)((rc >> 1) & 1), abort_flag, err)) { ok = false; break; }
+        if (!warp_wait(&bars->accfull[b], (uint32_t)((rc >> 1) & 1), abort_flag, err, lim)) { ok = false; break; }
         tc_after();
         const uint32_t tbase = tmem + lane_base + (uint32_t)(b * 256);
         for (int c0 = 0; c0 < F8; c0 += 16) {
@@ -1010,7 +1027,7 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
       for (int u4 = 0; u4 < 4; ++u4) vs[u4] = *reinterpret_cast<const float4*>(rb + ((size_t)u4 * kConv + ct) * 16);
       const float ws = *reinterpret_cast<const float*>(rb + (size_t)kConv * 64 + (size_t)ct * 4);
       const int s = st_i;
-      if (!warp_wait(&bars->empty[s], st_ph ^ 1u, abort_flag, err)) break;
+      if (!warp_wait(&bars->empty[s], st_ph ^ 1u, abort_flag, err, lim)) break;
       if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
       unsigned char* st = Xs + (size_t)s * P.stage_bytes;
 #pragma unroll
@@ -1168,14 +1185,17 @@ __device__ __forceinline__ void rec_next(RecCursor& c, const long long* toff, in
 }
 
 struct RecBars {
-  uint64_t full[4], empty[4], accfull[2], accempty[2], drain;
+  // full: the converter warps' A stages; wfull: the bulk copy of the W block
+  // of the same stage (its own barrier, so that a CTA leaving early can wait
+  // for exactly its copies in flight)
+  uint64_t full[4], wfull[4], empty[4], accfull[2], accempty[2], drain;
   uint32_t tmem;
   int abort_flag;
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs, const int* __restrict__ ival,
-             int* err) {
+             int* err, unsigned long long lim) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const RecSmem P = rec_smem();
@@ -1193,7 +1213,11 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
       acc += D.tiles;
     }
     toff[n_items] = acc;
-    for (int s = 0; s < NS; ++s) { mbar_init(&bars->full[s], kConv / 32 + 1); mbar_init(&bars->empty[s], 1); }
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&bars->full[s], kConv / 32);
+      mbar_init(&bars->wfull[s], 1);
+      mbar_init(&bars->empty[s], 1);
+    }
     for (int b = 0; b < 2; ++b) { mbar_init(&bars->accfull[b], 1); mbar_init(&bars->accempty[b], 4); }
     mbar_init(&bars->drain, 1);
     bars->abort_flag = 0;
@@ -1218,7 +1242,7 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
       bool ok = true;
       while (live && ok) {
         const int b = (int)(tc & 1);
-        if (!mbar_wait(&bars->accempty[b], (uint32_t)(((tc >> 1) & 1) ^ 1), abort_flag, err)) break;
+        if (!mbar_wait(&bars->accempty[b], (uint32_t)(((tc >> 1) & 1) ^ 1), abort_flag, err, lim)) break;
         tc_after();
         const uint32_t d_tmem = tmem + (uint32_t)(b * 256);
         const int NB = c.D.NB, K8 = c.D.K8;
@@ -1226,7 +1250,8 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
         const int nkc = (K8 + kKC - 1) / kKC;
         for (int kc = 0; kc < nkc; ++kc) {
           const int s = st_i;
-          if (!mbar_wait(&bars->full[s], st_ph, abort_flag, err)) { ok = false; break; }
+          if (!mbar_wait(&bars->full[s], st_ph, abort_flag, err, lim)) { ok = false; break; }
+          if (!mbar_wait(&bars->wfull[s], st_ph, abort_flag, err, lim)) { ok = false; break; }
           if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
           tc_after();
           const uint32_t a_hi = su32(smem + (size_t)s * P.stage_bytes);
@@ -1249,7 +1274,7 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
         rec_next(c, toff, n_items, items, ptrs, ival);
       }
       mma_commit(&bars->drain);
-      mbar_wait(&bars->drain, 0, abort_flag, err);
+      mbar_drain(&bars->drain, 0, err);
     }
     __syncwarp();
   } else if (warp >= 4 && warp < 8) {
@@ -1261,7 +1286,7 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
     long long tc = 0;
     while (live) {
       const int b = (int)(tc & 1);
-      if (!warp_wait(&bars->accfull[b], (uint32_t)((tc >> 1) & 1), abort_flag, err)) break;
+      if (!warp_wait(&bars->accfull[b], (uint32_t)((tc >> 1) & 1), abort_flag, err, lim)) break;
       tc_after();
       const RecDims& D = c.D;
       const long long rb = c.tile / D.nnb;
@@ -1329,6 +1354,12 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
     const int i8_0 = cw >> 1;                      // A row groups i8_0 + 4 u
     const int il = lane & 7;
     const bool issuer = (tid == 256);               // issues the bulk copy of the B block
+    // stages whose wfull barrier the issuer has armed, and per stage the
+    // parity of its last arming (flipped at every arming): at most one copy
+    // per stage is in flight (a stage is re-armed only after the MMA that
+    // consumed its previous copy), so the last phase of each armed stage
+    // covers every copy this CTA issued
+    uint32_t warmed = 0, wpar = 0;
     RecCursor c;
     bool live = rec_start(c, toff, n_items, t0, t1, items, ptrs, ival);
     int st_i = 0;              // operand stage and its phase parity
@@ -1388,7 +1419,7 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
       const RecDims& D = c.D;
       const int nb = s_nb;
       const int s = st_i;
-      if (!warp_wait(&bars->empty[s], st_ph ^ 1u, abort_flag, err)) return false;
+      if (!warp_wait(&bars->empty[s], st_ph ^ 1u, abort_flag, err, lim)) return false;
       if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
       unsigned char* hi = smem + (size_t)s * P.stage_bytes;
       unsigned char* lo = hi + P.a_bytes;
@@ -1396,12 +1427,14 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
       if (issuer) {
         if (D.Wp) {
           const uint32_t bytes = (uint32_t)(2 * D.NB) * 128u;
-          mbar_arrive_tx(&bars->full[s], bytes);
-          bulk_g2s(bs, D.Wp + ((size_t)nb * D.nkc + kc) * (size_t)(2 * D.NB) * 32, bytes, &bars->full[s]);
+          mbar_arrive_tx(&bars->wfull[s], bytes);
+          bulk_g2s(bs, D.Wp + ((size_t)nb * D.nkc + kc) * (size_t)(2 * D.NB) * 32, bytes, &bars->wfull[s]);
         } else {   // no packed W workspace: flag it and keep the pipeline moving
           atomicOr(err, 2);
-          mbar_arrive(&bars->full[s]);
+          mbar_arrive(&bars->wfull[s]);
         }
+        warmed |= 1u << s;
+        wpar ^= 1u << s;
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -1426,6 +1459,10 @@ k_recon_umma(const ReconItem* __restrict__ items, int n_items, void* const* ptrs
       if (!step(v1, v0)) break;
       if (!step(v0, v1)) break;
     }
+    // no bulk copy may land after the kernel's shared memory is gone
+    if (issuer)
+      for (int q = 0; q < NS; ++q)
+        if (warmed & (1u << q)) mbar_drain(&bars->wfull[q], ((wpar >> q) & 1u) ^ 1u, err);
   }
   tc_before();
   __syncthreads();
@@ -1477,7 +1514,7 @@ __global__ void k_pack_w(const ReconItem* __restrict__ items, void* const* ptrs,
 bool umma_supported(int chimax) { return chimax >= 1 && chimax <= 128; }
 
 cudaError_t launch_leg_umma(const LegItem* items, int n_items, int chimax, void* const* ptrs, const int* ival,
-                            int* err, cudaStream_t s) {
+                            int* err, unsigned long long wait_ns, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   if (!umma_supported(chimax)) return cudaErrorInvalidValue;
   const um::LegSmem P = um::leg_smem(chimax);
@@ -1486,7 +1523,7 @@ cudaError_t launch_leg_umma(const LegItem* items, int n_items, int chimax, void*
   if (e != cudaSuccess) return e;
   for (int i0 = 0; i0 < n_items; i0 += um::kMaxItems) {
     const int n = std::min(um::kMaxItems, n_items - i0);
-    um::k_leg_umma<<<um::sm_count(), um::kThreads, P.total, s>>>(items + i0, n, chimax, ptrs, ival, err);
+    um::k_leg_umma<<<um::sm_count(), um::kThreads, P.total, s>>>(items + i0, n, chimax, ptrs, ival, err, wait_ns);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1506,7 +1543,7 @@ size_t recon_packed_floats(int nmax) {
 }
 
 cudaError_t launch_recon_umma(const ReconItem* items, int n_items, int chimax, void* const* ptrs,
-                              const int* ival, int* err, cudaStream_t s) {
+                              const int* ival, int* err, unsigned long long wait_ns, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   if (!umma_supported(chimax)) return cudaErrorInvalidValue;
   const um::RecSmem P = um::rec_smem();
@@ -1517,7 +1554,7 @@ cudaError_t launch_recon_umma(const ReconItem* items, int n_items, int chimax, v
   if (e != cudaSuccess) return e;
   for (int i0 = 0; i0 < n_items; i0 += um::kMaxItems) {
     const int n = std::min(um::kMaxItems, n_items - i0);
-    um::k_recon_umma<<<um::sm_count(), um::kThreads, P.total, s>>>(items + i0, n, ptrs, ival, err);
+    um::k_recon_umma<<<um::sm_count(), um::kThreads, P.total, s>>>(items + i0, n, ptrs, ival, err, wait_ns);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1525,7 +1562,8 @@ cudaError_t launch_recon_umma(const ReconItem* items, int n_items, int chimax, v
 }
 
 cudaError_t launch_gram_umma(const GramLegItem* items, int n_items, int splits_max, int chimax,
-                             void* const* ptrs, const int* ival, int* err, cudaStream_t s) {
+                             void* const* ptrs, const int* ival, int* err, unsigned long long wait_ns,
+                             cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   if (!umma_supported(chimax)) return cudaErrorInvalidValue;
   const um::GramSmem P = um::gram_smem(chimax);
@@ -1535,7 +1573,7 @@ cudaError_t launch_gram_umma(const GramLegItem* items, int n_items, int splits_m
   for (int i0 = 0; i0 < n_items; i0 += um::kMaxItems) {
     const int n = std::min(um::kMaxItems, n_items - i0);
     um::k_gram_umma<<<um::sm_count(), um::kThreads, P.total, s>>>(items + i0, n, splits_max, chimax, ptrs, ival,
-                                                                   err);
+                                                                   err, wait_ns);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -35,17 +35,22 @@ cudaError_t launch_vec_contract(const VecItem* items, int n_items, int grid_x,
 
 // ---- k_umma.cu (FP32 storage, TF32x3 on tcgen05 tensor cores, chi <= 128)
 bool umma_supported(int chimax);
-// err: device int; bit 0 is set when a pipeline wait of the kernel expired
+// err: device int; bit 0 is set when a pipeline wait of the kernel ran
+// longer than wait_ns (the kernel then leaves its loops, lets its own MMAs and
+// copies in flight finish, frees its tensor memory and returns), bit 1 when a
+// reconstruct item has no packed-W workspace, bit 2 when one of those exit
+// drains itself ran out of time
 cudaError_t launch_leg_umma(const LegItem* items, int n_items, int chimax, void* const* ptrs, const int* ival,
-                            int* err, cudaStream_t s);
+                            int* err, unsigned long long wait_ns, cudaStream_t s);
 // floats of the packed W workspace of one reconstruct item for n, n' <= nmax
 size_t recon_packed_floats(int nmax);
 // psi_new = psi W into the next layout (Q-less reconstruct), W from the bond core
 cudaError_t launch_recon_umma(const ReconItem* items, int n_items, int chimax, void* const* ptrs,
-                              const int* ival, int* err, cudaStream_t s);
+                              const int* ival, int* err, unsigned long long wait_ns, cudaStream_t s);
 // writes per-split partial sums S; the reduction with sym = 1 returns (S + S^T) / 2
 cudaError_t launch_gram_umma(const GramLegItem* items, int n_items, int splits_max, int chimax,
-                             void* const* ptrs, const int* ival, int* err, cudaStream_t s);
+                             void* const* ptrs, const int* ival, int* err, unsigned long long wait_ns,
+                             cudaStream_t s);
 
 // Split count shared by the Gram kernels and their reductions.
 __host__ __device__ inline int gram_rows_splits(long long K, int splits_max) {

@@ -37,6 +37,7 @@ constexpr int kLegSplits = 64;
 constexpr int kGramSplitsMax = 64;
 constexpr int kLegSplitsMax = 128;
 constexpr size_t kAlign = 256;
+constexpr unsigned long long kWaitNsDefault = 4000000000ull;   // 4 s
 
 enum { LEG_U = 0, LEG_D = 1, LEG_L = 2, LEG_R = 3 };
 
@@ -171,11 +172,13 @@ struct pepo_ctx {
   unsigned long long* d_delta2 = nullptr;
   unsigned long long* d_delta1 = nullptr;
   int* d_flags = nullptr;
-  int* d_kerr = nullptr;   // bit 0: a tensor-core pipeline wait expired
+  int* d_kerr = nullptr;   // bit 0: a tensor-core pipeline wait expired (bits: launch_leg_umma)
+  unsigned long long wait_ns = kWaitNsDefault;   // limit of every tensor-core pipeline wait
   char* d_items = nullptr;
   long long launches = 0;
   std::string err;
   bool stepped = false;
+  int phase = 0;           // colours of the current Trotter step applied so far (0: step boundary)
   pepo_tuning tune = {kLegSplits, kGramSplits};
   // learned warm start applied inside pepo_bp_converge to the instances with
   // warm_start = 1 (workspace carved only when such an instance exists)
@@ -240,6 +243,9 @@ std::string validate(const pepo_config& c) {
   if (!(c.bp_tol > 0.0)) return "bp_tol must be > 0";
   if (c.bp_max_sweeps < 1) return "bp_max_sweeps must be >= 1";
   if (c.gates != PEPO_GATES_ZZ_X && c.gates != PEPO_GATES_XX_Z) return "unknown gate set";
+  if (c.prec == PEPO_BF16X3)
+    return "PEPO_BF16X3 is not built: a BF16 split needs six products for FP32-level accuracy, "
+           "twice the tensor time of PEPO_TF32X3 (use PEPO_TF32X3)";
   if (c.prec < PEPO_FP64 || c.prec > PEPO_BF16X3) return "unknown precision";
   if (!std::isfinite(c.J) || !std::isfinite(c.h) || !std::isfinite(c.dt)) return "non-finite couplings";
   if (c.inflight_sites < 0) return "inflight_sites must be >= 0";
@@ -1105,13 +1111,18 @@ size_t layout_arena(pepo_ctx* c, char* base, Planner* keep) {
 }
 
 // ------------------------------------------------------------ kernel timing
+// Bond-layer classes (absorb legs, Cholesky-QR Gram, Householder, factors,
+// core, reconstruct, environment factors) are kept apart from the BP classes
+// (eigenbasis leg rotations, message Grams, eigenbases, message finish), so
+// that the bond-update rate counts the bond layer only.
 enum KClass {
   K_LEG = 0, K_GRAM_ROWS, K_GRAM_ROWS_RED, K_GRAM_LEG, K_GRAM_LEG_RED, K_RECON, K_HH, K_FACTOR,
-  K_CORE, K_ENV, K_VEC, K_MSG, K_OTHER, K_NCLASS
+  K_CORE, K_ENV, K_VEC, K_MSG, K_OTHER, K_BP_LEG, K_BP_EIG, K_NCLASS
 };
 const char* kClassNames[K_NCLASS] = {
   "leg_contract", "gram_rows", "gram_rows_reduce", "gram_leg", "gram_leg_reduce", "reconstruct",
-  "householder_tsqr", "factor", "core_svd", "env_factor", "vec_contract", "msg_finish", "other"};
+  "householder_tsqr", "factor", "core_svd", "env_factor", "vec_contract", "msg_finish", "other",
+  "bp_leg_contract", "bp_env_eig"};
 
 struct Work { double bytes = 0, flops = 0; };
 
@@ -1128,7 +1139,7 @@ Work work_of(const pepo_ctx* c, int cls, const void* items, int n) {
   const double ts = (double)c->tsize;
   for (int i = 0; i < n; ++i) {
     long long d[PEPO_MAXLEG];
-    if (cls == K_LEG) {
+    if (cls == K_LEG || cls == K_BP_LEG) {
       const LegItem& it = static_cast<const LegItem*>(items)[i];
       view_dims(c, it.in, d);
       double in = 4;
@@ -1202,6 +1213,18 @@ void timing_harvest(pepo_ctx* c) {
   c->pool_next = 0;
 }
 
+// A tensor-core kernel's error word was set: report it once and clear it, so
+// that the context stays usable (its state is undefined until restored or
+// re-uploaded).
+pepo_status kernel_error(pepo_ctx* c, int kerr) {
+  cudaMemsetAsync(c->d_kerr, 0, sizeof(int), c->stream);
+  cudaStreamSynchronize(c->stream);
+  return fail(c, PEPO_E_CUDA,
+              "tensor-core kernel error word %d (bit 0: a pipeline wait ran longer than the wait limit, "
+              "bit 1: missing packed-W workspace, bit 2: an exit drain ran out of time); the state is "
+              "undefined until it is restored or uploaded again", kerr);
+}
+
 // Every launch wrapper returns without launching when its item count is 0;
 // LAUNCH_T counts (and, in timing mode, brackets with events) the launches
 // that happen.
@@ -1228,18 +1251,19 @@ void timing_harvest(pepo_ctx* c) {
 // tcgen05 (TMEM accumulators) for chi_max <= 128, else the FP32 SIMT kernels
 template <typename T>
 bool use_umma(const pepo_ctx* c, int chimax) {
-  return sizeof(T) == 4 && (c->prec == PEPO_TF32X3 || c->prec == PEPO_BF16X3) && umma_supported(chimax);
+  return sizeof(T) == 4 && c->prec == PEPO_TF32X3 && umma_supported(chimax);
 }
 template <typename T>
 cudaError_t leg_dispatch(pepo_ctx* c, const LegItem* items, int n, int gx, int chimax) {
   if (use_umma<T>(c, chimax))
-    return launch_leg_umma(items, n, chimax, c->d_ptrs, c->d_ival, c->d_kerr, c->stream);
+    return launch_leg_umma(items, n, chimax, c->d_ptrs, c->d_ival, c->d_kerr, c->wait_ns, c->stream);
   return launch_leg_contract<T>(items, n, gx, chimax, c->d_ptrs, c->d_ival, c->stream);
 }
 template <typename T>
 cudaError_t gram_leg_dispatch(pepo_ctx* c, const GramLegItem* items, int n, int chimax) {
   if (use_umma<T>(c, chimax))
-    return launch_gram_umma(items, n, c->tune.gram_leg_splits, chimax, c->d_ptrs, c->d_ival, c->d_kerr, c->stream);
+    return launch_gram_umma(items, n, c->tune.gram_leg_splits, chimax, c->d_ptrs, c->d_ival, c->d_kerr, c->wait_ns,
+                            c->stream);
   return launch_gram_leg<T>(items, n, c->tune.gram_leg_splits, chimax, c->d_ptrs, c->d_ival, c->stream);
 }
 
@@ -1296,7 +1320,7 @@ pepo_status run_gate_wave_tail(pepo_ctx* c, Inst& I, GateWave& w) {
     gx = std::max(gx, 4);
     if (use_umma<T>(c, chimax))
       LAUNCH_T(K_RECON, hitems(c, w.recon), w.recon.n,
-               launch_recon_umma(w.recon.d, w.recon.n, chimax, c->d_ptrs, c->d_ival, c->d_kerr, s));
+               launch_recon_umma(w.recon.d, w.recon.n, chimax, c->d_ptrs, c->d_ival, c->d_kerr, c->wait_ns, s));
     else
       LAUNCH_T(K_RECON, hitems(c, w.recon), w.recon.n,
                launch_reconstruct<T>(w.recon.d, w.recon.n, gx, 0, c->d_ptrs, c->d_ival, s));
@@ -1310,10 +1334,10 @@ pepo_status run_bp_waves(pepo_ctx* c, Inst& I, std::vector<BpWave>& waves) {
   cudaStream_t s = c->stream;
   const int chimax = I.cfg.chi_max;
   for (auto& w : waves) {
-    LAUNCH_T(K_ENV, nullptr, w.eig.n, launch_env_eig(w.eig.d, w.eig.n, chimax, c->tsize == 4 ? 1 : 0, c->d_ival, s));
+    LAUNCH_T(K_BP_EIG, nullptr, w.eig.n, launch_env_eig(w.eig.d, w.eig.n, chimax, c->tsize == 4 ? 1 : 0, c->d_ival, s));
     for (int a = 0; a < 4; ++a) {
       int gx = std::max(8, 2 * 152 * 4 / std::max(1, w.leg[a].n));
-      LAUNCH_T(K_LEG, hitems(c, w.leg[a]), w.leg[a].n,
+      LAUNCH_T(K_BP_LEG, hitems(c, w.leg[a]), w.leg[a].n,
                leg_dispatch<T>(c, w.leg[a].d, w.leg[a].n, gx, chimax));
     }
     LAUNCH_T(K_GRAM_LEG, hitems(c, w.gram), w.gram.n,
@@ -1335,20 +1359,28 @@ pepo_status run_sl_pass(pepo_ctx* c, Inst& I) {
   return PEPO_OK;
 }
 
-// one Trotter step of every instance (grouped launches)
+// the bond gates of one colour class on every instance (grouped launches)
+template <typename T>
+pepo_status colour_launches(pepo_ctx* c, int col) {
+  Inst& G = c->grp;
+  for (auto& w : G.gwaves[col]) {
+    pepo_status st = run_gate_wave<T>(c, G, w);
+    if (st != PEPO_OK) return st;
+  }
+  LAUNCH_T(K_CORE, nullptr, G.gcore[col].n, launch_core(G.gcore[col].d, G.gcore[col].n, c->d_ival, c->d_flags, c->stream));
+  for (auto& w : G.gwaves[col]) {
+    pepo_status st = run_gate_wave_tail<T>(c, G, w);
+    if (st != PEPO_OK) return st;
+  }
+  return PEPO_OK;
+}
+
+// one Trotter step of every instance
 template <typename T>
 pepo_status step_launches(pepo_ctx* c) {
-  Inst& G = c->grp;
   for (int col = 0; col < 4; ++col) {
-    for (auto& w : G.gwaves[col]) {
-      pepo_status st = run_gate_wave<T>(c, G, w);
-      if (st != PEPO_OK) return st;
-    }
-    LAUNCH_T(K_CORE, nullptr, G.gcore[col].n, launch_core(G.gcore[col].d, G.gcore[col].n, c->d_ival, c->d_flags, c->stream));
-    for (auto& w : G.gwaves[col]) {
-      pepo_status st = run_gate_wave_tail<T>(c, G, w);
-      if (st != PEPO_OK) return st;
-    }
+    pepo_status st = colour_launches<T>(c, col);
+    if (st != PEPO_OK) return st;
   }
   return PEPO_OK;
 }
@@ -1463,7 +1495,7 @@ pepo_status do_bp(pepo_ctx* c, int* sweeps_out, double* delta_out) {
         cudaMemcpyAsync(&kerr, c->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return fail(c, PEPO_E_CUDA, "BP delta readback: %s", cudaGetErrorString(cudaGetLastError()));
-    if (kerr) return fail(c, PEPO_E_CUDA, "tensor-core kernel error word %d (bit 0: a pipeline wait expired, bit 1: missing packed-W workspace)", kerr);
+    if (kerr) return kernel_error(c, kerr);
     for (int i = 0; i < c->n_inst; ++i) {
       if (!active[i]) continue;
       Inst& I = c->inst[i];
@@ -1532,7 +1564,7 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
         cudaMemcpyAsync(&kerr, c->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return fail(c, PEPO_E_CUDA, "single-layer delta readback");
-    if (kerr) return fail(c, PEPO_E_CUDA, "tensor-core kernel error word %d (bit 0: a pipeline wait expired, bit 1: missing packed-W workspace)", kerr);
+    if (kerr) return kernel_error(c, kerr);
     for (int i = 0; i < c->n_inst; ++i) {
       if (!active[i]) continue;
       Inst& I = c->inst[i];
@@ -1558,7 +1590,7 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
       cudaMemcpyAsync(&kerr, c->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return fail(c, PEPO_E_CUDA, "flags readback");
-  if (kerr) return fail(c, PEPO_E_CUDA, "tensor-core kernel error word %d (bit 0: a pipeline wait expired, bit 1: missing packed-W workspace)", kerr);
+  if (kerr) return kernel_error(c, kerr);
   for (int i = 0; i < c->n_inst; ++i) {
     Inst& I = c->inst[i];
     double out[8];
@@ -1629,6 +1661,25 @@ pepo_status do_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
 
 // canonical position of each layout leg for site v at step boundaries
 std::vector<int> boundary_layout(const SiteG& S) { return layout_for(S, S.upd[0]); }
+
+// Layout of site v after `phase` colours of the current step: the cut of its
+// next update innermost (the step-boundary layout once every bond of the site
+// has been updated, or none yet).
+std::vector<int> phase_layout(const Inst& I, const SiteG& S, int phase) {
+  int done = 0;
+  for (int k : S.upd)
+    if (I.bonds[S.legs[k].bond].colour < phase) ++done;
+  return layout_for(S, S.upd[done % (int)S.upd.size()]);
+}
+
+// calls that need whole steps (BP, the correlator, state uploads and
+// snapshots, the warm start) refuse a partly applied step
+bool at_step_boundary(pepo_ctx* c, const char* what) {
+  if (c->phase == 0) return true;
+  fail(c, PEPO_E_STATE, "%s: a Trotter step is partly applied (colours 0..%d); apply the remaining "
+       "colours with pepo_trotter_colour first", what, c->phase - 1);
+  return false;
+}
 
 }  // namespace
 
@@ -1799,9 +1850,27 @@ pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena, size
 pepo_status pepo_trotter_step(pepo_ctx* c, int n_steps) {
   if (!c) return PEPO_E_INVALID;
   if (n_steps < 0) return fail(c, PEPO_E_INVALID, "n_steps must be >= 0");
+  if (!at_step_boundary(c, "pepo_trotter_step")) return PEPO_E_STATE;
   timing_begin(c);
   pepo_status st = c->tsize == 8 ? do_steps<double>(c, n_steps) : do_steps<float>(c, n_steps);
   return st;
+}
+
+pepo_status pepo_trotter_colour(pepo_ctx* c, int colour) {
+  if (!c) return PEPO_E_INVALID;
+  if (colour < 0 || colour > 3) return fail(c, PEPO_E_INVALID, "colour must lie in 0..3, got %d", colour);
+  if (colour != c->phase)
+    return fail(c, PEPO_E_STATE, "colour %d out of order: the current step has colours 0..%d applied, "
+                "the next is %d", colour, c->phase - 1, c->phase);
+  timing_begin(c);
+  pepo_status st = c->tsize == 8 ? colour_launches<double>(c, colour) : colour_launches<float>(c, colour);
+  if (st != PEPO_OK) return st;
+  c->phase = (colour + 1) % 4;
+  if (c->phase == 0) {
+    for (auto& I : c->inst) I.steps++;
+    c->stepped = true;
+  }
+  return PEPO_OK;
 }
 
 // The learned warm start of the instances with warm_start = 1: features of
@@ -1830,6 +1899,7 @@ static pepo_status ws_apply_all(pepo_ctx* c) {
 
 pepo_status pepo_bp_converge(pepo_ctx* c, int* sweeps_out, double* delta_out) {
   if (!c) return PEPO_E_INVALID;
+  if (!at_step_boundary(c, "pepo_bp_converge")) return PEPO_E_STATE;
   if (c->ws_ready) {
     const pepo_status ws = ws_apply_all(c);
     if (ws != PEPO_OK) return ws;
@@ -1842,6 +1912,7 @@ pepo_status pepo_bp_converge(pepo_ctx* c, int* sweeps_out, double* delta_out) {
 
 pepo_status pepo_correlator(pepo_ctx* c, double* C_out, pepo_diag* diag_out) {
   if (!c) return PEPO_E_INVALID;
+  if (!at_step_boundary(c, "pepo_correlator")) return PEPO_E_STATE;
   timing_begin(c);
   pepo_status st = c->tsize == 8 ? do_correlator<double>(c, C_out, diag_out) : do_correlator<float>(c, C_out, diag_out);
   timing_harvest(c);
@@ -1886,7 +1957,7 @@ pepo_status pepo_get_site(pepo_ctx* c, int inst, int site, double* out, size_t c
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return fail(c, PEPO_E_CUDA, "site readback");
   const SiteG& S = I.sites[site];
-  std::vector<int> lay = boundary_layout(S);
+  std::vector<int> lay = phase_layout(I, S, c->phase);
   std::vector<int> dl(S.deg), dc(S.deg);
   size_t n = 4;
   for (int k = 0; k < S.deg; ++k) { dl[k] = chi[S.legs[lay[k]].bond]; dc[k] = chi[S.legs[k].bond]; n *= dc[k]; }
@@ -1923,6 +1994,7 @@ pepo_status pepo_get_site(pepo_ctx* c, int inst, int site, double* out, size_t c
 
 pepo_status pepo_set_bonds(pepo_ctx* c, int inst, const int* chi, const double* lam, const double* msgs) {
   if (!c) return PEPO_E_INVALID;
+  if (!at_step_boundary(c, "pepo_set_bonds")) return PEPO_E_STATE;
   if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
   Inst& I = c->inst[inst];
   if (!chi || !lam || !msgs) return fail(c, PEPO_E_INVALID, "null argument");
@@ -1942,6 +2014,7 @@ pepo_status pepo_set_bonds(pepo_ctx* c, int inst, const int* chi, const double* 
 
 pepo_status pepo_set_site(pepo_ctx* c, int inst, int site, const void* data, int dtype, size_t count) {
   if (!c) return PEPO_E_INVALID;
+  if (!at_step_boundary(c, "pepo_set_site")) return PEPO_E_STATE;
   if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
   Inst& I = c->inst[inst];
   if (site < 0 || site >= I.N || !data || (dtype != 0 && dtype != 1))
@@ -2017,6 +2090,7 @@ static pepo_status static_stage(pepo_ctx* c, void** out) {
 
 pepo_status pepo_set_site_static(pepo_ctx* c, int inst, int site, const void* data, int dtype, size_t count) {
   if (!c) return PEPO_E_INVALID;
+  if (!at_step_boundary(c, "pepo_set_site_static")) return PEPO_E_STATE;
   if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
   Inst& I = c->inst[inst];
   if (site < 0 || site >= I.N || !data || (dtype != 0 && dtype != 1))
@@ -2092,6 +2166,7 @@ size_t pepo_state_bytes(const pepo_ctx* c, int inst) {
 
 static pepo_status state_copy(pepo_ctx* c, int inst, char* buf, size_t bytes, bool save) {
   if (!c) return PEPO_E_INVALID;
+  if (!at_step_boundary(c, save ? "pepo_save_state" : "pepo_load_state")) return PEPO_E_STATE;
   if (inst < 0 || inst >= c->n_inst || !buf) return fail(c, PEPO_E_INVALID, "bad arguments");
   Inst& I = c->inst[inst];
   size_t off[7];
@@ -2240,6 +2315,7 @@ int pepo_ws_rows(pepo_ctx* c, int inst) {
 
 pepo_status pepo_ws_features(pepo_ctx* c, int inst, float* X_dev, int max_rows) {
   if (!c) return PEPO_E_INVALID;
+  if (!at_step_boundary(c, "pepo_ws_features")) return PEPO_E_STATE;
   if (inst < 0 || inst >= c->n_inst || !X_dev || max_rows < 0) return fail(c, PEPO_E_INVALID, "bad arguments");
   Inst& I = c->inst[inst];
   const float t = (float)(I.steps * I.cfg.dt);
@@ -2251,6 +2327,7 @@ pepo_status pepo_ws_features(pepo_ctx* c, int inst, float* X_dev, int max_rows) 
 
 pepo_status pepo_ws_targets(pepo_ctx* c, int inst, float* t_dev, int max_rows) {
   if (!c) return PEPO_E_INVALID;
+  if (!at_step_boundary(c, "pepo_ws_targets")) return PEPO_E_STATE;
   if (inst < 0 || inst >= c->n_inst || !t_dev || max_rows < 0) return fail(c, PEPO_E_INVALID, "bad arguments");
   Inst& I = c->inst[inst];
   cudaError_t e = launch_ws_targets(I.nb, c->d_ival + I.chi0, I.msg, I.cfg.chi_max, t_dev, max_rows, c->stream);
@@ -2260,6 +2337,7 @@ pepo_status pepo_ws_targets(pepo_ctx* c, int inst, float* t_dev, int max_rows) {
 
 pepo_status pepo_ws_apply(pepo_ctx* c, int inst, const float* y_dev, float gamma) {
   if (!c) return PEPO_E_INVALID;
+  if (!at_step_boundary(c, "pepo_ws_apply")) return PEPO_E_STATE;
   if (inst < 0 || inst >= c->n_inst || !y_dev || !(gamma >= 0.f && gamma <= 1.f))
     return fail(c, PEPO_E_INVALID, "bad arguments");
   Inst& I = c->inst[inst];
@@ -2271,6 +2349,7 @@ pepo_status pepo_ws_apply(pepo_ctx* c, int inst, const float* y_dev, float gamma
 pepo_status pepo_set_state(pepo_ctx* c, int inst, const double* sites, size_t count, const int* chi,
                            const double* lam, const double* msgs) {
   if (!c) return PEPO_E_INVALID;
+  if (!at_step_boundary(c, "pepo_set_state")) return PEPO_E_STATE;
   if (inst < 0 || inst >= c->n_inst) return fail(c, PEPO_E_INVALID, "bad instance");
   Inst& I = c->inst[inst];
   if (!sites) return fail(c, PEPO_E_INVALID, "null argument");
@@ -2400,6 +2479,23 @@ pepo_status pepo_set_tuning(pepo_ctx* c, const pepo_tuning* t) {
   }
   c->tune.gram_leg_splits = gl;
   c->tune.gram_rows_splits = gr;
+  return PEPO_OK;
+}
+
+pepo_status pepo_set_wait_limit(pepo_ctx* c, double seconds) {
+  if (!c) return PEPO_E_INVALID;
+  if (!(seconds >= 1e-9 && seconds <= 60.0))
+    return fail(c, PEPO_E_INVALID, "wait limit must lie in [1e-9, 60] s, got %g", seconds);
+  const unsigned long long ns = (unsigned long long)std::llround(seconds * 1e9);
+  if (ns == c->wait_ns) return PEPO_OK;
+  // captured graphs hold the old limit in their kernel parameters
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, PEPO_E_CUDA, "pepo_set_wait_limit: %s", cudaGetErrorString(e));
+  for (cudaGraphExec_t* x : {&c->step_exec, &c->bp_exec, &c->sl_exec}) {
+    if (*x) cudaGraphExecDestroy(*x);
+    *x = nullptr;
+  }
+  c->wait_ns = ns;
   return PEPO_OK;
 }
 

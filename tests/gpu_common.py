@@ -34,18 +34,38 @@ def oracle_bond_lams(net, Lx, Ly):
     return out
 
 
-def compare(cfg, nsteps):
-    recs, lam = gpu_run(cfg, nsteps)
-    ref, net = oracle_run.simulate(oracle_cfg(cfg), nsteps=nsteps)
-    C = np.array([r["C"] for r in recs])
-    Cr = np.array([r["C"] for r in ref])
-    lref = oracle_bond_lams(net, cfg.Lx, cfg.Ly)
-    lam_err = 0.0
+# floor of the per-value relative check of the spectra: values below it carry
+# little weight and their relative error is set by the absolute one
+LAM_REL_FLOOR = 1e-2
+
+
+def lam_errors(lam, lref):
+    """(max |l_k - r_k| over bonds with lam_0 = 1 normalisation and the
+    unmatched tail, max |l_k - r_k| / r_k over r_k >= LAM_REL_FLOOR r_0)."""
+    lam_err, rel_err = 0.0, 0.0
     for b, l in lam.items():
         r = lref[b]
         k = min(len(l), len(r))
         e = np.max(np.abs(l[:k] - r[:k])) if k else 0.0
         tail = max(np.max(l[k:], initial=0.0), np.max(r[k:], initial=0.0))
         lam_err = max(lam_err, e, tail)
-    return dict(C=C, Cref=Cr, dC=float(np.max(np.abs(C - Cr))), lam_err=lam_err,
-                recs=recs, ref=ref)
+        if k:
+            sel = r[:k] >= LAM_REL_FLOOR * r[0]
+            rel_err = max(rel_err, float(np.max(np.abs(l[:k][sel] - r[:k][sel]) / r[:k][sel])))
+    return lam_err, rel_err
+
+
+def compare(cfg, nsteps):
+    recs, lam = gpu_run(cfg, nsteps)
+    ref, net = oracle_run.simulate(oracle_cfg(cfg), nsteps=nsteps)
+    C = np.array([r["C"] for r in recs])
+    Cr = np.array([r["C"] for r in ref])
+    lref = oracle_bond_lams(net, cfg.Lx, cfg.Ly)
+    lam_err, lam_rel = lam_errors(lam, lref)
+    # the Q-less update equals the literal one only with full-rank messages
+    # (flags bit 0 marks a rank-deficient one): a parity pass must not hide it
+    flags = 0
+    for r in recs:
+        flags |= int(r["flags"])
+    return dict(C=C, Cref=Cr, dC=float(np.max(np.abs(C - Cr))), lam_err=lam_err, lam_rel=lam_rel,
+                flags=flags, recs=recs, ref=ref)

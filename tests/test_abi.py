@@ -87,6 +87,7 @@ def test_required_bytes_rejects_invalid_raw_fields(lib):
     assert raw() > 0
     assert raw(obs_pauli=0) == 0 and raw(obs_pauli=4) == 0
     assert raw(gates=2) == 0 and raw(prec=4) == 0 and raw(prec=-1) == 0
+    assert raw(prec=2) > 0 and raw(prec=3) == 0          # BF16X3 is refused, not aliased
     assert raw(Lx=65, Ly=65) == 0                      # more than 4096 sites
     assert raw(Lx=2, Ly=1, obs_x=1, obs_y=0) > 0       # a two-site chain is a valid grid
 
@@ -96,6 +97,8 @@ def test_every_context_call_refuses_a_null_context(lib):
     null = None
     I, D = ctypes.c_int, ctypes.c_double
     assert lib.pepo_trotter_step(null, 1) == 1
+    assert lib.pepo_trotter_colour(null, 0) == 1
+    assert lib.pepo_set_wait_limit(null, 1.0) == 1
     assert lib.pepo_bp_converge(null, None, None) == 1
     assert lib.pepo_correlator(null, None, None) == 1
     assert lib.pepo_get_spectrum(null, 0, 0, (D * 4)(), ctypes.byref(I())) == 1
