@@ -235,6 +235,19 @@ size_t pepo_state_bytes(const pepo_ctx* ctx, int inst);
 pepo_status pepo_save_state(pepo_ctx* ctx, int inst, void* dev_buf, size_t bytes);
 pepo_status pepo_load_state(pepo_ctx* ctx, int inst, const void* dev_buf, size_t bytes);
 
+/* Checkpoint of one instance to host memory and restart from it (the
+ * paper's long runs, Appendix A; not a step of the method): the same layout
+ * as pepo_save_state (pepo_state_bytes bytes), copied between the device
+ * state and the caller's host array host_buf (page-locked memory copies
+ * fastest).  *steps_out receives the instance's step count, which
+ * pepo_load_state_host restores from `steps` (the measurement history used
+ * by the Sec. 6.3 C-drop check starts afresh).  Both synchronise the stream.
+ * Errors: PEPO_E_INVALID (NULL context or buffer, bad instance, a buffer
+ * smaller than pepo_state_bytes, steps < 0), PEPO_E_STATE (a step partly
+ * applied), PEPO_E_CUDA. */
+pepo_status pepo_save_state_host(pepo_ctx* ctx, int inst, void* host_buf, size_t bytes, int* steps_out);
+pepo_status pepo_load_state_host(pepo_ctx* ctx, int inst, const void* host_buf, size_t bytes, int steps);
+
 /* pepo_set_site without any memory allocation (the paper has no counterpart:
  * it is an interface variant, not a step of the method).  Same arguments and
  * result as pepo_set_site, but the host data is staged in a fixed 16 MiB

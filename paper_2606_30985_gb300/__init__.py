@@ -65,7 +65,7 @@ EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trot
            "pepo_mlp_forward", "pepo_mlp_gradient", "pepo_mlp_adam_step", "pepo_mlp_destroy",
            "pepo_ws_rows", "pepo_ws_features", "pepo_ws_targets", "pepo_ws_apply", "pepo_set_warmstart_weights",
            "pepo_c_drop", "pepo_set_bp_params", "pepo_get_messages", "pepo_set_messages",
-           "pepo_set_wait_limit"]
+           "pepo_set_wait_limit", "pepo_save_state_host", "pepo_load_state_host"]
 
 _lib = None
 
@@ -141,6 +141,10 @@ def load_library(path=LIB_PATH):
     lib.pepo_save_state.restype = I
     lib.pepo_load_state.argtypes = [P, I, P, S]
     lib.pepo_load_state.restype = I
+    lib.pepo_save_state_host.argtypes = [P, I, P, S, ctypes.POINTER(I)]
+    lib.pepo_save_state_host.restype = I
+    lib.pepo_load_state_host.argtypes = [P, I, P, S, I]
+    lib.pepo_load_state_host.restype = I
     F = ctypes.c_float
     FP = ctypes.POINTER(ctypes.c_float)
     lib.pepo_mlp_num_params.argtypes = []
@@ -507,6 +511,33 @@ class Engine:
         _device_tensor(buf, torch.uint8, self.state_bytes(inst), "load_state")
         self._check(self.lib.pepo_load_state(self.ctx, inst, ctypes.c_void_p(buf.data_ptr()), buf.numel()),
                     "pepo_load_state")
+
+    # -- checkpoint / restart through host memory
+    def checkpoint(self, path, inst=0):
+        """Write instance inst's state (pepo_save_state_host) and its step
+        count to `path` (numpy .npz)."""
+        buf = np.empty(self.state_bytes(inst), dtype=np.uint8)
+        steps = ctypes.c_int()
+        self._check(self.lib.pepo_save_state_host(self.ctx, inst, ctypes.c_void_p(buf.ctypes.data), buf.size,
+                                                  ctypes.byref(steps)), "pepo_save_state_host")
+        c = self.cfgs[inst]
+        np.savez(path, state=buf, steps=steps.value,
+                 config=np.array(repr(sorted(vars(c).items()))))
+        return steps.value
+
+    def restore(self, path, inst=0):
+        """Restart instance inst from a checkpoint written by checkpoint()
+        for the same configuration."""
+        with np.load(path) as z:
+            if str(z["config"]) != repr(sorted(vars(self.cfgs[inst]).items())):
+                raise PepoError("restore: the checkpoint was written for another configuration")
+            buf = np.ascontiguousarray(z["state"])
+            steps = int(z["steps"])
+        if buf.size != self.state_bytes(inst):
+            raise PepoError("restore: %d bytes in the checkpoint, %d expected" % (buf.size, self.state_bytes(inst)))
+        self._check(self.lib.pepo_load_state_host(self.ctx, inst, ctypes.c_void_p(buf.ctypes.data), buf.size,
+                                                  steps), "pepo_load_state_host")
+        return steps
 
     # -- learned warm start
     def ws_rows(self, inst=0):

@@ -2164,7 +2164,9 @@ size_t pepo_state_bytes(const pepo_ctx* c, int inst) {
   return state_layout(c, c->inst[inst], nullptr);
 }
 
-static pepo_status state_copy(pepo_ctx* c, int inst, char* buf, size_t bytes, bool save) {
+// host = true: buf is host memory (checkpoint to / restart from the host;
+// the copies synchronise the stream), else device memory
+static pepo_status state_copy(pepo_ctx* c, int inst, char* buf, size_t bytes, bool save, bool host = false) {
   if (!c) return PEPO_E_INVALID;
   if (!at_step_boundary(c, save ? "pepo_save_state" : "pepo_load_state")) return PEPO_E_STATE;
   if (inst < 0 || inst >= c->n_inst || !buf) return fail(c, PEPO_E_INVALID, "bad arguments");
@@ -2177,7 +2179,7 @@ static pepo_status state_copy(pepo_ctx* c, int inst, char* buf, size_t bytes, bo
                       c->stream) != cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return fail(c, PEPO_E_CUDA, "site pointer readback");
-  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind k = !host ? cudaMemcpyDeviceToDevice : (save ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
   auto cp = [&](void* dev, size_t o, size_t n) {
     return save ? cudaMemcpyAsync(buf + o, dev, n, k, c->stream) : cudaMemcpyAsync(dev, buf + o, n, k, c->stream);
   };
@@ -2195,6 +2197,8 @@ static pepo_status state_copy(pepo_ctx* c, int inst, char* buf, size_t bytes, bo
       cp(I.sigma, off[5], sizeof(double) * I.N) != cudaSuccess ||
       cp(I.disc, off[6], sizeof(double) * I.nb) != cudaSuccess)
     return fail(c, PEPO_E_CUDA, "state copy");
+  if (host && cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "state copy: %s", cudaGetErrorString(cudaGetLastError()));
   return PEPO_OK;
 }
 
@@ -2208,6 +2212,22 @@ pepo_status pepo_load_state(pepo_ctx* c, int inst, const void* dev_buf, size_t b
   pepo_status st = state_copy(c, inst, const_cast<char*>(static_cast<const char*>(dev_buf)), bytes, false);
   if (st == PEPO_OK) {
     c->inst[inst].steps = c->inst[inst].saved_steps;
+    c->inst[inst].meas_valid = c->inst[inst].prev_valid = 0;
+  }
+  return st;
+}
+
+pepo_status pepo_save_state_host(pepo_ctx* c, int inst, void* host_buf, size_t bytes, int* steps_out) {
+  pepo_status st = state_copy(c, inst, static_cast<char*>(host_buf), bytes, true, true);
+  if (st == PEPO_OK && steps_out) *steps_out = c->inst[inst].steps;
+  return st;
+}
+
+pepo_status pepo_load_state_host(pepo_ctx* c, int inst, const void* host_buf, size_t bytes, int steps) {
+  if (c && steps < 0) return fail(c, PEPO_E_INVALID, "steps must be >= 0");
+  pepo_status st = state_copy(c, inst, const_cast<char*>(static_cast<const char*>(host_buf)), bytes, false, true);
+  if (st == PEPO_OK) {
+    c->inst[inst].steps = steps;
     c->inst[inst].meas_valid = c->inst[inst].prev_valid = 0;
   }
   return st;

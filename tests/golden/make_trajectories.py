@@ -10,6 +10,8 @@ Usage: python tests/golden/make_trajectories.py CASE [NSTEPS]
 Cases:
   c2_chi20, c2_chi40, c2_chi60   4x4, J = 1, h = 2, Z at (1, 1), second-order
                                  split, dt = 0.05, ZZ / X gates (40 steps = t 2)
+  paper4x4_chi40                 the paper's convention on 4x4 (XX / Z gates,
+                                 h = J = -1, dt = 0.1, Z at (1, 1)), 20 steps
 Output: tests/golden/traj_<CASE>.txt
 """
 import os
@@ -26,10 +28,15 @@ from oracle.pepo import Network, bond_key  # noqa: E402
 
 C2 = dict(Lx=4, Ly=4, J=1.0, h=2.0, dt=0.05, order=2, obs=(1, 1), obs_pauli="Z", eps_cut=1e-11,
           bp_alpha=0.5, bp_tol=1e-5, bp_max_sweeps=100, gateset="ZZ_X", pinv_rel=1e-12)
+# the paper's own convention (Sec. 6): XX / Z gates, h = J = -1, dt = 0.1,
+# symmetric split, Z at (1, 1) of the 4x4 grid
+PAPER_4X4 = dict(Lx=4, Ly=4, J=-1.0, h=-1.0, dt=0.1, order=2, obs=(1, 1), obs_pauli="Z", eps_cut=1e-11,
+                 bp_alpha=0.5, bp_tol=1e-5, bp_max_sweeps=100, gateset="XX_Z", pinv_rel=1e-12)
 CASES = {
     "c2_chi20": dict(C2, chi_max=20, nsteps=40),
     "c2_chi40": dict(C2, chi_max=40, nsteps=40),
     "c2_chi60": dict(C2, chi_max=60, nsteps=40),
+    "paper4x4_chi40": dict(PAPER_4X4, chi_max=40, nsteps=20),
 }
 
 

@@ -99,6 +99,8 @@ def test_every_context_call_refuses_a_null_context(lib):
     assert lib.pepo_trotter_step(null, 1) == 1
     assert lib.pepo_trotter_colour(null, 0) == 1
     assert lib.pepo_set_wait_limit(null, 1.0) == 1
+    assert lib.pepo_save_state_host(null, 0, None, 0, None) == 1
+    assert lib.pepo_load_state_host(null, 0, None, 0, 0) == 1
     assert lib.pepo_bp_converge(null, None, None) == 1
     assert lib.pepo_correlator(null, None, None) == 1
     assert lib.pepo_get_spectrum(null, 0, 0, (D * 4)(), ctypes.byref(I())) == 1
