@@ -5,10 +5,21 @@ the oracle's trajectories, stored by tests/golden/make_trajectories.py (which
 calls only the oracle; the chi_max = 60 file holds the prefix the oracle
 finished, the run taking many hours on the host).
 
-Bounds: |dC| <= 1e-5 (FP32), 1e-3 (split TF32) at every stored step; the
+Bounds: |dC| <= 1e-5 (FP32), 1e-3 (split TF32) at every compared step; the
 Vidal spectra after the last step (when stored) within 1e-5 / 1e-4 of
 lam_0; flags bit 0 clear (no rank-deficient message, where the GPU's Q-less
 update would depart from the literal one).
+
+Trapped layers are reported, not compared (the parity rule for the Sec. 6.3
+traps): a layer where the single-layer BP of either side needs 30 sweeps or
+more (Type 1) or hits its budget (Type 2) has a C(t) that depends on where
+the slowly converging or non-converging iteration stops, so it is excluded;
+the single-layer messages feed nothing else, so later layers stay
+comparable.  A double-layer trap on either side ends the comparison: its
+messages are the environments of the next bond updates, and the two sides
+may continue from different BP fixed points.  On this workload the oracle's
+single-layer BP traps from t = 1.2 on (chi_max = 20: 31-100 sweeps near the
+zero crossing of C) while its double-layer BP converges in at most 16 sweeps.
 """
 import os
 
@@ -24,9 +35,13 @@ HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 TOL = {"fp32": (1e-5, 1e-5), "tf32x3": (1e-3, 1e-4)}
 
 
+TRAP_SWEEPS = 30
+
+
 def load(chi):
+    """C, double- and single-layer sweeps per step, final spectra (if stored)."""
     path = os.path.join(HERE, "traj_c2_chi%d.txt" % chi)
-    C, lam = [], {}
+    C, sw2, sw1, lam = [], [], [], {}
     with open(path) as f:
         for line in f:
             p = line.split()
@@ -37,25 +52,46 @@ def load(chi):
             else:
                 assert int(p[0]) == len(C)
                 C.append(float(p[2]))
-    return np.array(C), lam
+                sw2.append(int(p[5]))
+                sw1.append(int(p[6]))
+    return np.array(C), np.array(sw2), np.array(sw1), lam
+
+
+def compared_steps(sw2_a, sw1_a, sw2_b, sw1_b):
+    """Steps compared under the trap rule above, and the excluded ones."""
+    keep, skipped = [], []
+    for s in range(len(sw2_a)):
+        if sw2_a[s] >= TRAP_SWEEPS or sw2_b[s] >= TRAP_SWEEPS:
+            break
+        if sw1_a[s] >= TRAP_SWEEPS or sw1_b[s] >= TRAP_SWEEPS:
+            skipped.append(s)
+        else:
+            keep.append(s)
+    return keep, skipped
 
 
 @pytest.mark.parametrize("chi", [20, 40, 60])
 @pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
 def test_config2_trajectory(chi, prec):
-    Cref, lref = load(chi)
+    Cref, sw2r, sw1r, lref = load(chi)
     n = len(Cref) - 1
     assert n >= 10
     cfg = pkg.Config(Lx=4, Ly=4, J=1.0, h=2.0, dt=0.05, order=2, obs=(1, 1), chi_max=chi, precision=prec)
     recs, lam = gpu_run(cfg, n)
     C = np.array([r["C"] for r in recs])
-    dC = float(np.max(np.abs(C - Cref)))
-    print("config 2 chi %d %s: %d steps, max |dC| = %.3g" % (chi, prec, n, dC))
+    sw2 = np.array([r["bp_sweeps"] for r in recs])
+    sw1 = np.array([r["bp1_sweeps"] for r in recs])
+    keep, skipped = compared_steps(sw2, sw1, sw2r, sw1r)
+    dC = float(np.max(np.abs(C[keep] - Cref[keep])))
+    dC_skipped = float(np.max(np.abs(C[skipped] - Cref[skipped]))) if skipped else 0.0
+    print("config 2 chi %d %s: %d steps, %d compared, max |dC| = %.3g; %d trapped layers reported "
+          "(max |dC| there %.3g)" % (chi, prec, n, len(keep), dC, len(skipped), dC_skipped))
+    assert len(keep) >= 10
     assert dC < TOL[prec][0], dC
     flags = 0
     for r in recs:
         flags |= int(r["flags"])
     assert flags & 1 == 0
-    if lref:
+    if lref and len(keep) + len(skipped) == n + 1:
         lam_err, _ = lam_errors(lam, lref)
         assert lam_err < TOL[prec][1], lam_err
