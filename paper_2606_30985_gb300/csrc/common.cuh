@@ -135,7 +135,8 @@ struct EnvFactorItem {
 // operator-Schmidt factors turn it into the factor T of X = (gate half) cv.
 struct SiteFacItem {
   TView cv;                // absorbed tensor, cut leg innermost (env dims = factor ranks)
-  int branch_idx;          // ival: 1 Cholesky-QR, 0 Householder
+  int branch_idx;          // ival: 1 Cholesky-QR, 0 Householder, 2 Householder after a
+                           // Gram too ill-conditioned for Cholesky-QR
   int kfac_idx;            // ival: rows of the R-factor (Householder branch)
   int rg_idx;              // ival: operator-Schmidt rank of the bond gate
   const double* F;         // gate factors [kappa][4][4] of this side
@@ -146,6 +147,7 @@ struct SiteFacItem {
   int* perm;               // pivot order (r entries)
   int rank_idx;            // ival: rank of the factor
   double rel;              // rank threshold
+  double rel_safe;         // smallest pivot ratio of the Gram that Cholesky-QR trusts
   int n_thr;               // Eq. 10 branch thresholds of the instance
   double ratio_thr;
 };

@@ -227,8 +227,16 @@ __device__ void hh_block_qr(T* A, long long rows, int n, double* v, double* part
         __syncthreads();
         if (rg < RG && kb + kk < nc) {
           const double tw = part[RG * KC + kk];
-          for (long long i = j + rg; i < rows; i += RG)
-            A[i * n + k] = (T)((double)A[i * n + k] - v[i - j] * tw);
+          if (sizeof(T) == 4) {
+            // FP32 storage: the reflection in FP32 (backward stable to the
+            // data's own precision; FP64 here would run at 1/64 of the rate)
+            const float twf = (float)tw;
+            for (long long i = j + rg; i < rows; i += RG)
+              A[i * n + k] = (T)fmaf(-(float)v[i - j], twf, (float)A[i * n + k]);
+          } else {
+            for (long long i = j + rg; i < rows; i += RG)
+              A[i * n + k] = (T)((double)A[i * n + k] - v[i - j] * tw);
+          }
         }
         __syncthreads();
       }
@@ -238,9 +246,9 @@ __device__ void hh_block_qr(T* A, long long rows, int n, double* v, double* part
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_hh_level(const SiteFacItem* __restrict__ items, int level, void* const* ptrs, const int* ival) {
+k_hh_level(const SiteFacItem* __restrict__ items, int level, void* const* ptrs, const int* ival, int pass) {
   const SiteFacItem it = items[blockIdx.y];
-  if (ival[it.branch_idx] != 0) return;
+  if (ival[it.branch_idx] != pass) return;
   long long m;
   int n;
   cv_shape(it.cv, ival, m, n);
@@ -289,22 +297,22 @@ k_hh_level(const SiteFacItem* __restrict__ items, int level, void* const* ptrs, 
 
 template <typename T>
 cudaError_t launch_hh_level(const SiteFacItem* items, int n_items, int level, int grid_x, int nmax,
-                            void* const* ptrs, const int* ival, cudaStream_t s) {
+                            void* const* ptrs, const int* ival, cudaStream_t s, int pass) {
   if (n_items == 0) return cudaSuccess;
   long long L = hh_leaf_rows(nmax);
   size_t smem = sizeof(double) * ((size_t)(L > 4 * nmax ? L : 4 * nmax) + 256 + 256);
   cudaError_t e = cudaFuncSetAttribute(k_hh_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_hh_level<T><<<dim3(grid_x, n_items), 256, smem, s>>>(items, level, ptrs, ival);
+  k_hh_level<T><<<dim3(grid_x, n_items), 256, smem, s>>>(items, level, ptrs, ival, pass);
   return cudaGetLastError();
 }
 
 // R (top min(m, n) rows of cv after the tree) -> FP64 C buffer, rows -> kfac
 template <typename T>
-__global__ void k_hh_extract(const SiteFacItem* __restrict__ items, void* const* ptrs, int* ival) {
+__global__ void k_hh_extract(const SiteFacItem* __restrict__ items, void* const* ptrs, int* ival, int pass) {
   const SiteFacItem it = items[blockIdx.x];
-  if (ival[it.branch_idx] != 0) return;
+  if (ival[it.branch_idx] != pass) return;
   long long m;
   int n;
   cv_shape(it.cv, ival, m, n);
@@ -319,17 +327,18 @@ __global__ void k_hh_extract(const SiteFacItem* __restrict__ items, void* const*
 
 template <typename T>
 cudaError_t launch_hh_extract(const SiteFacItem* items, int n_items, void* const* ptrs, int* ival,
-                              cudaStream_t s) {
+                              cudaStream_t s, int pass) {
   if (n_items == 0) return cudaSuccess;
-  k_hh_extract<T><<<n_items, 256, 0, s>>>(items, ptrs, ival);
+  k_hh_extract<T><<<n_items, 256, 0, s>>>(items, ptrs, ival, pass);
   return cudaGetLastError();
 }
 
 // ============================================================ formG / formB
 // Cholesky branch: G[(c,k),(c',k')] = sum_{p,q} (F_k^T F_k')[p,q] C[(c,p),(c',q)].
 // Householder branch: B[(a,p'),(c,k)] = sum_p F_k[p',p] R[a,(c,p)].
-__global__ void k_form(const SiteFacItem* __restrict__ items, const int* ival) {
+__global__ void k_form(const SiteFacItem* __restrict__ items, const int* ival, int only) {
   const SiteFacItem it = items[blockIdx.y];
+  if (only >= 0 && ival[it.branch_idx] != only) return;
   long long m;
   int n;
   cv_shape(it.cv, ival, m, n);
@@ -381,20 +390,74 @@ __global__ void k_form(const SiteFacItem* __restrict__ items, const int* ival) {
 }
 
 cudaError_t launch_form(const SiteFacItem* items, int n_items, int grid_x, const int* ival,
-                        cudaStream_t s) {
+                        cudaStream_t s, int only) {
   if (n_items == 0) return cudaSuccess;
-  k_form<<<dim3(grid_x, n_items), 256, 0, s>>>(items, ival);
+  k_form<<<dim3(grid_x, n_items), 256, 0, s>>>(items, ival, only);
   return cudaGetLastError();
 }
 
 // =================================================================== factor
+// Whether the Cholesky-QR branch can be trusted with this Gram C = cv^T cv
+// (n x n): its factor is only as accurate as C, whose accumulation noise
+// (FP32 runs flushed into FP64: ~1e-8 of the diagonal; FP64: ~1e-14) makes
+// Q = cv R^-1 non-orthonormal in the directions whose Schur complement is
+// within a few orders of it, and the Q-less update treats Q as orthonormal.
+// The pivoted Cholesky of C (pivot values only, in precision R, in the
+// scratch Cw) must keep every pivot above `safe` times the first: false (use
+// Householder) for a numerically rank-deficient or ill-conditioned Gram.
+// Block-uniform result.
+template <typename R>
+__device__ bool gram_trusted(const SiteFacItem& it, int n, R* Cw, double* dg, double safe, double* rv, int* ri) {
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e - (long long)i * n);
+    Cw[e] = (R)it.C[(long long)i * it.ldc + j];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dg[i] = (double)Cw[(long long)i * n + i];
+  __syncthreads();
+  double d0 = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const int p = block_argmax(dg, j, n, rv, ri);
+    const double dp = dg[p];
+    if (j == 0) d0 = dp;
+    if (!(dp > safe * d0) || !(dp > 0.0)) return false;
+    if (p != j) {
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        R t = Cw[(long long)j * n + k]; Cw[(long long)j * n + k] = Cw[(long long)p * n + k]; Cw[(long long)p * n + k] = t;
+      }
+      __syncthreads();
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        R t = Cw[(long long)k * n + j]; Cw[(long long)k * n + j] = Cw[(long long)k * n + p]; Cw[(long long)k * n + p] = t;
+      }
+      if (threadIdx.x == 0) { double t = dg[j]; dg[j] = dg[p]; dg[p] = t; }
+      __syncthreads();
+    }
+    const R rjj = sqrt(Cw[(long long)j * n + j]);
+    __syncthreads();
+    for (int k = j + 1 + threadIdx.x; k < n; k += blockDim.x) Cw[(long long)j * n + k] /= rjj;
+    __syncthreads();
+    const int mm = n - j - 1;
+    for (long long e = threadIdx.x; e < (long long)mm * mm; e += blockDim.x) {
+      const int a = j + 1 + (int)(e / mm), b = j + 1 + (int)(e % mm);
+      Cw[(long long)a * n + b] -= Cw[(long long)j * n + a] * Cw[(long long)j * n + b];
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) dg[i] = (double)Cw[(long long)i * n + i];
+    __syncthreads();
+  }
+  return true;
+}
+
 // Cholesky branch: pivoted Cholesky of G (r x r, in place, row-major).
 // Householder branch: column-pivoted Householder QR of B (4k x r, in place).
 // Output: T (rank x r upper trapezoidal, pivoted column order) in place,
 // perm[q] = original column of pivoted column q, rank -> ival.
+// A Cholesky-branch site whose Gram fails gram_trusted is marked branch 2 and
+// left for the Householder pass that follows (only = 2 runs that pass only).
 __global__ void __launch_bounds__(512)
-k_factor(const SiteFacItem* __restrict__ items, int* ival) {
+k_factor(const SiteFacItem* __restrict__ items, int* ival, int only) {
   const SiteFacItem it = items[blockIdx.x];
+  if (only >= 0 && ival[it.branch_idx] != only) return;
   long long m;
   int n;
   cv_shape(it.cv, ival, m, n);
@@ -411,6 +474,17 @@ k_factor(const SiteFacItem* __restrict__ items, int* ival) {
   __shared__ double rv[16];
   __shared__ int ri[16];
   __shared__ double red[16];
+  if (ival[it.branch_idx] == 1) {
+    // the scratch after G (r x ld) holds the copy of C; v (4n doubles) the pivots
+    double* scratch = A + (long long)ld * ld;
+    const bool ok = it.rel_safe >= 1e-7
+                        ? gram_trusted<float>(it, n, reinterpret_cast<float*>(scratch), v, it.rel_safe, rv, ri)
+                        : gram_trusted<double>(it, n, scratch, v, it.rel_safe, rv, ri);
+    if (!ok) {
+      if (threadIdx.x == 0) ival[it.branch_idx] = 2;
+      return;
+    }
+  }
   for (int i = threadIdx.x; i < r; i += blockDim.x) perm[i] = i;
   int rank = 0;
   if (ival[it.branch_idx] == 1) {
@@ -518,13 +592,13 @@ k_factor(const SiteFacItem* __restrict__ items, int* ival) {
 }
 
 cudaError_t launch_factor(const SiteFacItem* items, int n_items, int rmax, int nmax, int* ival,
-                          cudaStream_t s) {
+                          cudaStream_t s, int only) {
   if (n_items == 0) return cudaSuccess;
   size_t smem = sizeof(double) * ((size_t)2 * rmax + 4 * nmax);
   cudaError_t e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_factor<<<n_items, 512, smem, s>>>(items, ival);
+  k_factor<<<n_items, 512, smem, s>>>(items, ival, only);
   return cudaGetLastError();
 }
 
@@ -672,7 +746,8 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
     if (!tr) Tc[(long long)b * M + a] = s; else Tc[(long long)a * M + b] = s;
   }
   __syncthreads();
-  for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) V[e] = Tc[e];   // copy of Tcore
+  // copy of Tcore (the mixed path multiplies it by its FP64 subspace basis)
+  for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) V[e] = Tc[e];
   __syncthreads();
   // columns the FP64 Jacobi below works on (all N, or the mixed path's subspace)
   int NK = N;
@@ -784,7 +859,11 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
   {   // FP64 one-sided Jacobi on Tcore (or on its restriction T Q)
     // mixed path: the rotations W64 (NK x NK) are accumulated in the V block
     // (the copy of T is no longer needed); the right vectors are then Q W64
-    const int sw64 = jacobi_svd<double>(Tc, M, NK, it.mixed_svd ? V : nullptr, 60, &sh_capped, red, 1e-17);
+    // the right vectors are always accumulated (V): recovering them as
+    // T^T u / s would carry the columns' absolute rounding (~1e-16 of the
+    // largest) divided by s^2, which for kept values near eps_cut (1e-11 of
+    // the largest) leaves nothing of the vector
+    const int sw64 = jacobi_svd<double>(Tc, M, NK, V, 60, &sh_capped, red, 1e-17);
     if (threadIdx.x == 0 && it.sweeps) {
       it.sweeps[1] = sw64;
       if (!it.mixed_svd) it.sweeps[0] = 0;
@@ -896,12 +975,7 @@ k_core(const CoreItem* __restrict__ items, int* ival, int* flags_base) {
       } else if (it.mixed_svd) {
         x = V[(long long)a * chi + c];                  // Ritz right vector (above)
       } else {
-        // other side: (copy^T u_j)_a / s_j, copy = Tcore column-major M x N, u_j = column j / s_j
-        double acc = 0.0;
-        const double* col = V + (long long)a * M;      // column a of the copy
-        const double* uj = Tc + (long long)j * M;
-        for (int i = 0; i < M; ++i) acc = fma(col[i], uj[i], acc);
-        x = s > 0.0 ? acc / (s * s) : 0.0;
+        x = V[(long long)j * N + a];                    // accumulated right vector j (column-major N x N)
       }
       Z[(long long)a * chi + c] = x * sqrt(s) * inv;
     }
@@ -945,13 +1019,13 @@ cudaError_t launch_core(const CoreItem* items, int n_items, int* ival, int* flag
 }
 
 template cudaError_t launch_hh_level<float>(const SiteFacItem*, int, int, int, int, void* const*,
-                                            const int*, cudaStream_t);
+                                            const int*, cudaStream_t, int);
 template cudaError_t launch_hh_level<double>(const SiteFacItem*, int, int, int, int, void* const*,
-                                             const int*, cudaStream_t);
+                                             const int*, cudaStream_t, int);
 template cudaError_t launch_hh_extract<float>(const SiteFacItem*, int, void* const*, int*,
-                                              cudaStream_t);
+                                              cudaStream_t, int);
 template cudaError_t launch_hh_extract<double>(const SiteFacItem*, int, void* const*, int*,
-                                               cudaStream_t);
+                                               cudaStream_t, int);
 
 }  // namespace pepo
 

@@ -7,15 +7,17 @@ cudaError_t launch_env_factor(const EnvFactorItem* items, int n_items, int chima
                               cudaStream_t s);
 cudaError_t launch_branch(const SiteFacItem* items, int n_items, int* ival, cudaStream_t s);
 template <typename T>
+// pass: the branch value of the sites processed (0: the Householder branch,
+// 2: the sites the Cholesky branch handed over); only < 0: every site
 cudaError_t launch_hh_level(const SiteFacItem* items, int n_items, int level, int grid_x, int nmax,
-                            void* const* ptrs, const int* ival, cudaStream_t s);
+                            void* const* ptrs, const int* ival, cudaStream_t s, int pass);
 template <typename T>
 cudaError_t launch_hh_extract(const SiteFacItem* items, int n_items, void* const* ptrs, int* ival,
-                              cudaStream_t s);
+                              cudaStream_t s, int pass);
 cudaError_t launch_form(const SiteFacItem* items, int n_items, int grid_x, const int* ival,
-                        cudaStream_t s);
+                        cudaStream_t s, int only);
 cudaError_t launch_factor(const SiteFacItem* items, int n_items, int rmax, int nmax, int* ival,
-                          cudaStream_t s);
+                          cudaStream_t s, int only);
 cudaError_t launch_core(const CoreItem* items, int n_items, int* ival, int* flags_base, cudaStream_t s);
 }  // namespace pepo
 

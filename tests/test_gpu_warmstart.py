@@ -47,6 +47,13 @@ def test_forward_and_gradient_match_oracle():
         got = G[k].reshape(-1)
         err = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
         assert err < 1e-2, (k, err)
+        # element by element: both sides round to BF16 at the same points, so
+        # an entry differs by the FP32 accumulation order and by an occasional
+        # BF16 rounding that falls the other way (2^-8 of the entry's largest
+        # contributions): bounded by 2^-7 of the entry plus 2^-7 of the tensor's scale
+        bound = 2.0 ** -7 * (np.abs(ref) + np.max(np.abs(ref)))
+        worst = int(np.argmax(np.abs(got - ref) - bound))
+        assert np.all(np.abs(got - ref) <= bound), (k, worst, got[worst], ref[worst])
 
 
 def test_adam_step_matches_oracle():
