@@ -43,6 +43,7 @@ struct LegItem {
   int a_rows;              // ival index of A's row count (== out size)
   const double* A;         // row-major, leading dimension lda
   int lda;
+  const double* a_scale;   // row scale of A (A[i, :] * a_scale[i]) or nullptr
 };
 
 // Gram over rows: C[f, f'] = sum_k X[k, f] Y[k, f'], X, Y row-major K x F with
@@ -82,10 +83,13 @@ struct EnvEigItem {
   double* sqrtD;           // chi
 };
 
-// Back-rotation of one weighted Gram: out = V G V^T (G from the rotated tensor).
+// Back-rotation of one Gram of the rotated tensor: out = V G' V^T with
+// G' = G / (sd sd^T) when the rotated tensor carries the square roots of the
+// message eigenvalues on its legs (the Gram's weights folded into the rotation).
 struct RotItem {
   const double* G;         // chi x chi, leading dimension ld
   const double* Vt;        // chi x chi, leading dimension ld
+  const double* sd;        // G is scaled by sd[i] sd[i'] (undone before the rotation), or nullptr
   double* out;             // chi x chi, leading dimension ld
   int ld;
   int chi_idx;

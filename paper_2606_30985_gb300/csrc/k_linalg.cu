@@ -1031,6 +1031,26 @@ template cudaError_t launch_hh_extract<double>(const SiteFacItem*, int, void* co
 
 namespace pepo {
 // ============================================================ message eigen
+// The square roots of a message's eigenvalues scale the rotated legs (they
+// are the weights of every Gram that sums over the leg) and divide the Gram
+// of that leg back out, so they are floored at kSqrtEigFloor of the largest:
+// an eigenvalue below 1e-12 of the largest counts as 1e-12 of it, which
+// moves no message by more than that relative amount.
+constexpr double kSqrtEigFloor = 1e-6;
+__device__ void floor_sqrt_eigs(double* sd, int n, double* red) {
+  __syncthreads();
+  double m = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) m = fmax(m, sd[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
+  const double lo = kSqrtEigFloor * (m > 0.0 ? m : 1.0);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) sd[j] = fmax(sd[j], lo);
+}
+
 // M (symmetrised, PSD) -> one-sided Jacobi on its columns: M V = U S with
 // S = |eigenvalues| and V the eigenvectors (U = V up to signs of numerically
 // zero eigenvalues).  Outputs Vt (row i = column i of V) and sqrt(S).
@@ -1063,6 +1083,7 @@ k_env_eig(const EnvEigItem* __restrict__ items, const int* ival, int fp32) {
       int i = e / n, j = e - i * n;
       it.Vt[i * it.ld + j] = (double)V[(long long)i * n + j];
     }
+    floor_sqrt_eigs(it.sqrtD, n, red);
     return;
   }
   double* A = it.work;                      // n x n column-major
@@ -1083,6 +1104,7 @@ k_env_eig(const EnvEigItem* __restrict__ items, const int* ival, int fp32) {
     int i = e / n, j = e - i * n;
     it.Vt[i * it.ld + j] = V[(long long)i * n + j];   // row i of Vt = column i of V
   }
+  floor_sqrt_eigs(it.sqrtD, n, red);
 }
 
 cudaError_t launch_env_eig(const EnvEigItem* items, int n_items, int chimax, int fp32, const int* ival,
@@ -1102,11 +1124,16 @@ __global__ void k_rotate_back(const RotItem* __restrict__ items, const int* ival
   const RotItem it = items[blockIdx.x];
   const int n = ival[it.chi_idx];
   extern __shared__ __align__(16) double sm[];
-  double* T = sm;   // n x n: T = G Vt
+  double* T = sm;   // n x n: T = G' Vt
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     int i = e / n, j = e - i * n;
     double s = 0.0;
-    for (int k = 0; k < n; ++k) s = fma(it.G[i * it.ld + k], it.Vt[k * it.ld + j], s);
+    if (it.sd) {
+      for (int k = 0; k < n; ++k) s = fma(it.G[i * it.ld + k] / it.sd[k], it.Vt[k * it.ld + j], s);
+      s /= it.sd[i];
+    } else {
+      for (int k = 0; k < n; ++k) s = fma(it.G[i * it.ld + k], it.Vt[k * it.ld + j], s);
+    }
     T[e] = s;
   }
   __syncthreads();

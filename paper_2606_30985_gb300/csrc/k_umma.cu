@@ -3,7 +3,7 @@
 // message products (Eq. 13) and of the absorb step (Sec. 2.5 step 1).
 //
 //   k_leg_umma   out[o, i, q] = sum_j A[i, j] in[o, j, q]
-//   k_gram_umma  S[i, i'] = sum_k w_k^2 (Xh[i,k] Xh[i',k] + 2 Xh[i,k] Xl[i',k])
+//   k_gram_umma  S[i, i'] = sum_k (Xh[i,k] Xh[i',k] + 2 Xh[i,k] Xl[i',k])
 //                over one K-range (split) of k = (o, q); the reduction sums the
 //                splits and symmetrises: G = (S + S^T) / 2 = sum w^2 X X^T up
 //                to the dropped lo*lo term.
@@ -28,7 +28,7 @@
 //   warps 8-15    converters: coalesced global loads (leg, reconstruct:
 //                 a register ring two or one chunks ahead; Gram: per-thread
 //                 cp.async into a ring of raw shared-memory stages four chunks
-//                 ahead), weight, split, and 16-byte conflict-free stores into
+//                 ahead), split, and 16-byte conflict-free stores into
 //                 the swizzled K-major layout the MMA descriptors describe
 //                 (below); the reconstruct's W block arrives by bulk copy
 // Stages and accumulators are handed over with mbarriers.  Every wait is
@@ -55,7 +55,11 @@ constexpr int kConv = 256;              // converter threads (warps 8..15)
 constexpr int kM = 128;                 // accumulator rows = TMEM lanes
 constexpr int kKC = 32;                 // K values per staged chunk
 constexpr int kTmemCols = 512;          // two accumulators of 256 columns
-constexpr int kRun = 8;                 // Gram chunks per FP32 accumulator run
+// Gram chunks per FP32 accumulator run (1024 K terms summed in TMEM before
+// the compensated shared-memory sums take them): the FP32 rounding of a run
+// is ~1e-6 of its sum in the worst case, below the split-TF32 product error,
+// and the epilogue's pass over the accumulator is paid once per run
+constexpr int kRun = 32;
 constexpr unsigned long long kDrainNs = 2000000000ull;   // bound of the exit drains
 constexpr int kMaxItems = 512;
 
@@ -560,10 +564,11 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
         // one block of 2 N16 rows per 32-wide K chunk
         const size_t bblk = (size_t)(2 * L.N16) * 128;
         const int K32 = (L.K8 + kKC - 1) / kKC * kKC;
+        const double* asc = items[c.item].a_scale;
         for (int e = ct; e < L.N16 * K32; e += kConv) {
           const int n = e / K32, j = e - n * K32;
           float x = 0.f;
-          if (n < L.Jout && j < L.J) x = (float)L.A[(long long)n * L.lda + j];
+          if (n < L.Jout && j < L.J) x = (float)(L.A[(long long)n * L.lda + j] * (asc ? asc[n] : 1.0));
           const float h = tf32_hi(x);
           const float l = x - h;
           unsigned char* blk = Bs + (size_t)(j / kKC) * bblk + (size_t)(j & 3) * 4;
@@ -649,12 +654,12 @@ __device__ inline void gram_dims(const GramLegItem& it, void* const* ptrs, const
 
 // Converter raw staging: each converter thread copies its four 16-byte
 // pieces of a chunk with cp.async into its own slots of a raw stage (piece u
-// of thread t at (u kConv + t) 16 bytes, then one FP32 weight and the item's
-// padded row count per thread),
-// kRawMax chunks ahead of the chunk it converts, so the loads of several
-// chunks are in flight without holding registers.
+// of thread t at (u kConv + t) 16 bytes, then the item's padded row count per
+// thread), kRawMax chunks ahead of the chunk it converts, so the loads of
+// several chunks are in flight without holding registers.
 constexpr int kRawMax = 6;
-constexpr size_t kRawBytes = (size_t)kConv * 4 * 16 + (size_t)kConv * 8;   // pieces, weight, F8
+constexpr size_t kRawF8Off = (size_t)kConv * 4 * 16;                      // after the pieces
+constexpr size_t kRawBytes = kRawF8Off + (size_t)kConv * 4;                 // pieces, F8
 
 struct GramSmem {
   int f8max, stages, ld, raw;
@@ -709,14 +714,11 @@ struct GramBars {
 // Load side of the Gram converters: the cursor of one converter thread over
 // the chunks of its CTA's units (items x splits), kept in registers.  Per
 // chunk, issue() copies the thread's column group (4 K values) of its four
-// rows with cp.async into its slots of a raw stage, with the group's weight
-// and the item's padded row count F8 (0 once the CTA's work is done).  The
-// flattened index g of the column group over the non-free legs (the outer
-// legs of o, then the legs of q / 4) is kept as three mixed-radix digits
-// advanced by small additions; the source pointer advances incrementally; the
-// weights of the digits are loaded one chunk before they are used (indices
-// clamped into the tables: the value only matters for valid columns, whose
-// digits are in range).
+// rows with cp.async into its slots of a raw stage, with the item's padded row
+// count F8 (0 once the CTA's work is done); the source pointer advances
+// incrementally.  The Gram is unweighted: the BP message weights are carried
+// by the rotated tensor itself (its legs are scaled by the square roots of the
+// message eigenvalues).
 struct GramLoader {
   int kq, row0;
   long long lu, lcur, lend, stride_u;
@@ -727,10 +729,8 @@ struct GramLoader {
   const float* X;
   long long roff0, roff1, roff2, roff3;
   bool rv0, rv1, rv2, rv3;
-  int rd0, rd1, rd2, dg0, dg1, dg2, lqb;
+  int lqb;
   long long lo;
-  const double *ws0, *ws1, *ws2;
-  float pw0, pw1, pw2;
   const float* lp;
 
   __device__ __forceinline__ void init(int kq_, int row0_, long long first_unit) {
@@ -740,22 +740,6 @@ struct GramLoader {
     stride_u = gridDim.x;
     item = -1;
     live = false;
-    pw0 = pw1 = pw2 = 1.f;
-  }
-  __device__ __forceinline__ void dig_set(long long gv) {
-    dg2 = (int)(gv % rd2); gv /= rd2;
-    dg1 = (int)(gv % rd1); gv /= rd1;
-    dg0 = (int)gv;
-  }
-  __device__ __forceinline__ void dig_add(int inc) {
-    dg2 += inc;
-    while (dg2 >= rd2) { dg2 -= rd2; ++dg1; }
-    while (dg1 >= rd1) { dg1 -= rd1; ++dg0; }
-  }
-  __device__ __forceinline__ void prefetch_w() {
-    pw0 = ws0 ? (float)__ldg(ws0 + min(dg0, rd0 - 1)) : 1.f;
-    pw1 = ws1 ? (float)__ldg(ws1 + min(dg1, rd1 - 1)) : 1.f;
-    pw2 = ws2 ? (float)__ldg(ws2 + min(dg2, rd2 - 1)) : 1.f;
   }
   // position the cursor at the first chunk of unit lu (item constants are
   // reloaded when the item changes)
@@ -776,20 +760,6 @@ struct GramLoader {
       const int r0 = row0, r1 = row0 + 32, r2 = row0 + 64, r3 = row0 + 96;
       roff0 = (long long)r0 * Q; roff1 = (long long)r1 * Q; roff2 = (long long)r2 * Q; roff3 = (long long)r3 * Q;
       rv0 = r0 < F; rv1 = r1 < F; rv2 = r2 < F; rv3 = r3 < F;
-      // digit slots: the non-free legs in layout order, right-aligned
-      int slot = 2;
-      rd0 = rd1 = rd2 = 1;
-      ws0 = ws1 = ws2 = nullptr;
-      const GramLegItem& it = items[i];
-#pragma unroll
-      for (int uu = PEPO_MAXLEG - 1; uu >= 0; --uu) {
-        if (uu >= G.nlegs || uu == G.k) continue;
-        const double* w = it.sw[uu];
-        if (slot == 2) { rd2 = G.d[uu]; ws2 = w; }
-        else if (slot == 1) { rd1 = G.d[uu]; ws1 = w; }
-        else { rd0 = G.d[uu]; ws0 = w; }
-        --slot;
-      }
     }
     const long long NC = gram_leg_chunks(O, Q);
     const int S = gram_leg_splits_k(O * Q, splits_max);
@@ -799,54 +769,44 @@ struct GramLoader {
     if (wide) {
       lo = lcur / qpc;
       lqb = (int)(lcur - lo * qpc);
-      dig_set(lo * Q4 + (long long)lqb * 8 + kq);
       lp = X + lo * FQ + (long long)lqb * kKC + 4 * kq;
     } else {
       lo = lcur * opc;
       const int ooff = kq / Q4, q4 = kq - ooff * Q4;
-      dig_set((lo + ooff) * Q4 + q4);
       lp = X + (lo + ooff) * FQ + 4 * q4;
     }
-    prefetch_w();
   }
   // copy the chunk at the cursor into raw stage rb (one copy group) and
   // advance; returns true when the unit is finished (the caller then enters
-  // the next one)
+  // the next one).  Columns outside the item are zero-filled (no read).
   __device__ __forceinline__ bool issue(unsigned char* rb, int ct) {
-    int* f8slot = reinterpret_cast<int*>(rb + (size_t)kConv * 68 + (size_t)ct * 4);
+    int* f8slot = reinterpret_cast<int*>(rb + kRawF8Off + (size_t)ct * 4);
     if (!live) {
       *f8slot = 0;
       cp_async_commit();   // empty group: keeps one group per chunk slot
       return false;
     }
     const bool kvalid = wide ? (lqb * 8 + kq < Q4) : (kq / Q4 < opc && lo + kq / Q4 < O);
-    const float w = kvalid ? pw0 * pw1 * pw2 : 0.f;
     const void* z = (const void*)X;
     cp_async16(rb + ((size_t)0 * kConv + ct) * 16, (kvalid && rv0) ? (const void*)(lp + roff0) : z, (kvalid && rv0) ? 16 : 0);
     cp_async16(rb + ((size_t)1 * kConv + ct) * 16, (kvalid && rv1) ? (const void*)(lp + roff1) : z, (kvalid && rv1) ? 16 : 0);
     cp_async16(rb + ((size_t)2 * kConv + ct) * 16, (kvalid && rv2) ? (const void*)(lp + roff2) : z, (kvalid && rv2) ? 16 : 0);
     cp_async16(rb + ((size_t)3 * kConv + ct) * 16, (kvalid && rv3) ? (const void*)(lp + roff3) : z, (kvalid && rv3) ? 16 : 0);
-    *reinterpret_cast<float*>(rb + (size_t)kConv * 64 + (size_t)ct * 4) = w;
     *f8slot = F8;
     cp_async_commit();
     if (++lcur < lend) {
       if (wide) {
         if (++lqb == qpc) {
-          const int inc = Q4 - 8 * (qpc - 1);
           lqb = 0;
           ++lo;
           lp += FQ - (long long)(qpc - 1) * kKC;
-          dig_add(inc);
         } else {
           lp += kKC;
-          dig_add(8);
         }
       } else {
         lo += opc;
         lp += (long long)opc * FQ;
-        dig_add(opc * Q4);
       }
-      prefetch_w();
       return false;
     }
     lu += stride_u;
@@ -992,12 +952,9 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
     // ------------------------------------------------------------ converters
     // Load side: this thread's column group of each chunk (4 K values) for
     // its four rows is copied with cp.async into its own slots of a raw stage,
-    // P.raw chunks ahead of the conversion, together with the group's weight
-    // and the item's padded row count F8 (0 marks the end of the CTA's work).
-    // All cursor state lives in registers: the flattened index g of the
-    // column group over the non-free legs (outer legs of o, then the legs of
-    // q / 4) is kept as three mixed-radix digits advanced by small additions,
-    // and the source pointer advances incrementally.
+    // P.raw chunks ahead of the conversion, together with the item's padded
+    // row count F8 (0 marks the end of the CTA's work).  The cursor lives in
+    // registers and the source pointer advances incrementally.
     const int ct = tid - 256, cw = ct >> 5;
     const int kq = 4 * (cw & 1) + (lane >> 3);     // this thread's 4-wide K group of a chunk
     const int i8_0 = cw >> 1;                      // row groups i8_0 + 4 u, u = 0..3
@@ -1012,20 +969,19 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
         ld.enter_unit(items, n_items, uoff, U, ptrs, ival, splits_max);
     };
     for (int d = 0; d < DR; ++d) issue_next(d);
-    // conversion side: wait for this thread's copies of chunk cc, weight,
-    // split and store into the operand stage, then refill the raw stage
+    // conversion side: wait for this thread's copies of chunk cc, split and
+    // store into the operand stage, then refill the raw stage
     int rs = 0;                // raw stage of the chunk being converted
     int st_i = 0;              // operand stage and its phase parity
     uint32_t st_ph = 0;
     while (true) {
       cp_async_wait(DR - 1);
       const unsigned char* rb = raw + (size_t)rs * kRawBytes;
-      const int F8 = *reinterpret_cast<const int*>(rb + (size_t)kConv * 68 + (size_t)ct * 4);
+      const int F8 = *reinterpret_cast<const int*>(rb + kRawF8Off + (size_t)ct * 4);
       if (F8 == 0) break;
       float4 vs[4];
 #pragma unroll
       for (int u4 = 0; u4 < 4; ++u4) vs[u4] = *reinterpret_cast<const float4*>(rb + ((size_t)u4 * kConv + ct) * 16);
-      const float ws = *reinterpret_cast<const float*>(rb + (size_t)kConv * 64 + (size_t)ct * 4);
       const int s = st_i;
       if (!warp_wait(&bars->empty[s], st_ph ^ 1u, abort_flag, err, lim)) break;
       if (++st_i == NS) { st_i = 0; st_ph ^= 1u; }
@@ -1034,7 +990,7 @@ k_gram_umma(const GramLegItem* __restrict__ items, int n_items, int splits_max, 
       for (int u4 = 0; u4 < 4; ++u4) {
         const int i = 8 * (i8_0 + 4 * u4) + il;
         if (i < F8) {
-          const float4 x = make_float4(vs[u4].x * ws, vs[u4].y * ws, vs[u4].z * ws, vs[u4].w * ws);
+          const float4 x = vs[u4];
           const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
           const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
           *reinterpret_cast<float4*>(st + swz(i, kq)) = h;

@@ -494,11 +494,12 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
 
   // ---- gate-update waves
   const double rel_fac = (c->prec == PEPO_FP64) ? 1e-15 : 1e-13;
-  // smallest Gram pivot ratio the Cholesky-QR branch trusts (above the
-  // Gram's accumulation noise by three orders: ~1e-8 of the diagonal for the
-  // FP32-storage Gram, ~1e-13 for the FP64 one); below it the site takes the
+  // smallest Gram pivot ratio the Cholesky-QR branch trusts: above the
+  // Gram's accumulation noise (FP32-storage Gram: ~1e-8 of the diagonal for
+  // 1e6 rows, ~1e-7 for 1e4; FP64: ~1e-13), where the pivots of directions
+  // that are zero in exact arithmetic land; below it the site takes the
   // Householder branch
-  const double rel_safe = (c->prec == PEPO_FP64) ? 1e-10 : 1e-5;
+  const double rel_safe = (c->prec == PEPO_FP64) ? 1e-10 : 1e-6;
   const double rel_env = I.cfg.pinv_rel;
   for (int col = 0; col < 4; ++col) {
     const auto& bl = I.colours[col];
@@ -590,6 +591,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
               li.a_rows = W.rank_idx[r];
               li.A = W.L[r];
               li.lda = chimax;
+              li.a_scale = nullptr;
               leg[r].push_back(li);
               t.dim[r] = W.rank_idx[r];
               cur_ref = li.out_ref;
@@ -762,6 +764,9 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
           li.a_rows = view.dim[j];
           li.A = W.L[j];
           li.lda = chimax;
+          // the rotated leg carries the square roots of the message's
+          // eigenvalues: the Grams below then need no weights
+          li.a_scale = W.sqrtD[j];
           leg[j].push_back(li);
           cur = li.out_ref;
         }
@@ -775,11 +780,12 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
           g.partial = W.partial + (size_t)w * kLegSplitsMax * cm2;
           g.out = W.C + (size_t)w * cm2;
           g.ldo = chimax;
-          for (int u = 0; u < PEPO_MAXLEG; ++u) g.sw[u] = (u < d && u != w) ? W.sqrtD[u] : nullptr;
+          for (int u = 0; u < PEPO_MAXLEG; ++u) g.sw[u] = nullptr;
           gram.push_back(g);
           RotItem r;
           r.G = g.out;
           r.Vt = W.L[w];
+          r.sd = W.sqrtD[w];
           r.out = mptr(I.hat, msg_out(v, bw_));
           r.ld = chimax;
           r.chi_idx = chi_idx(bw_);
