@@ -43,7 +43,6 @@ struct LegItem {
   int a_rows;              // ival index of A's row count (== out size)
   const double* A;         // row-major, leading dimension lda
   int lda;
-  const double* a_scale;   // row scale of A (A[i, :] * a_scale[i]) or nullptr
 };
 
 // Gram over rows: C[f, f'] = sum_k X[k, f] Y[k, f'], X, Y row-major K x F with
@@ -81,6 +80,7 @@ struct EnvEigItem {
   double* work;            // 2 * chimax^2 doubles
   double* Vt;              // chi x chi, leading dimension ld
   double* sqrtD;           // chi
+  double* Vs;              // diag(sqrtD) Vt (the rotation that also carries the weights), ld
 };
 
 // Back-rotation of one Gram of the rotated tensor: out = V G' V^T with
@@ -151,7 +151,7 @@ struct SiteFacItem {
   int* perm;               // pivot order (r entries)
   int rank_idx;            // ival: rank of the factor
   double rel;              // rank threshold
-  double rel_safe;         // smallest pivot ratio of the Gram that Cholesky-QR trusts
+  double rel_safe;         // smallest fraction of its column's Gram diagonal a Cholesky-QR pivot keeps
   int n_thr;               // Eq. 10 branch thresholds of the instance
   double ratio_thr;
 };

@@ -83,7 +83,7 @@ k_leg_contract(const LegItem* __restrict__ items, void* const* ptrs, const int* 
   T* Bs = At + Jin * TL;                      // [Jin][TC]
   for (int e = threadIdx.x; e < Jin * TL; e += blockDim.x) {
     int j = e / TL, i = e - j * TL;
-    At[e] = (i < Jout) ? (T)(it.A[(long long)i * it.lda + j] * (it.a_scale ? it.a_scale[i] : 1.0)) : T(0);
+    At[e] = (i < Jout) ? (T)it.A[(long long)i * it.lda + j] : T(0);
   }
   long long G, nqb, units;
   if (Q >= TC) { G = 1; nqb = (Q + TC - 1) / TC; units = O * nqb; }

@@ -169,6 +169,7 @@ cudaError_t launch_branch(const SiteFacItem* items, int n_items, int* ival, cuda
 // factors the stack.  R replaces the top rows of the block; entries below the
 // diagonal are zeroed (Q is never needed: the update is Q-less).
 __host__ __device__ inline long long hh_leaf_rows(int n) { return n * 4 > 256 ? (long long)n * 4 : 256; }
+constexpr int kHhThreads = 512;   // threads of a TSQR block
 
 template <typename T>
 __device__ void hh_block_qr(T* A, long long rows, int n, double* v, double* part, double* red) {
@@ -196,7 +197,10 @@ __device__ void hh_block_qr(T* A, long long rows, int n, double* v, double* part
     for (long long i = j + threadIdx.x; i < rows; i += blockDim.x) A[i * n + j] = (i == j) ? (T)beta : T(0);
     const int nc = n - j - 1;
     if (nc > 0) {
-      const int KC = nc < (int)blockDim.x ? nc : (int)blockDim.x;
+      // columns per pass: at most a quarter of the block, so that at least
+      // four row groups share each column's dot product (short chains)
+      const int kcap = (int)blockDim.x / 4 > 32 ? (int)blockDim.x / 4 : 32;
+      const int KC = nc < kcap ? nc : kcap;
       const int RG = blockDim.x / KC;
       const int t = threadIdx.x;
       const int kk = t % KC, rg = t / KC;
@@ -204,17 +208,28 @@ __device__ void hh_block_qr(T* A, long long rows, int n, double* v, double* part
         const int k = j + 1 + kb + kk;
         double acc = 0.0;
         if (rg < RG && kb + kk < nc) {
-          float accf = 0.f;
-          int run = 0;
-          for (long long i = j + rg; i < rows; i += RG) {
-            if (sizeof(T) == 4) {
-              accf = fmaf((float)v[i - j], (float)A[i * n + k], accf);
-              if (++run == 64) { acc += (double)accf; accf = 0.f; run = 0; }
-            } else {
-              acc = fma(v[i - j], (double)A[i * n + k], acc);
+          if (sizeof(T) == 4) {
+            // four independent FP32 runs of 16 terms each, flushed into FP64
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            int run = 0;
+            long long i = j + rg;
+            const long long step = RG;
+            for (; i + 3 * step < rows; i += 4 * step) {
+              a0 = fmaf((float)v[i - j], (float)A[i * n + k], a0);
+              a1 = fmaf((float)v[i + step - j], (float)A[(i + step) * n + k], a1);
+              a2 = fmaf((float)v[i + 2 * step - j], (float)A[(i + 2 * step) * n + k], a2);
+              a3 = fmaf((float)v[i + 3 * step - j], (float)A[(i + 3 * step) * n + k], a3);
+              if (++run == 16) {
+                acc += ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
+                a0 = a1 = a2 = a3 = 0.f;
+                run = 0;
+              }
             }
+            for (; i < rows; i += step) a0 = fmaf((float)v[i - j], (float)A[i * n + k], a0);
+            acc += ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
+          } else {
+            for (long long i = j + rg; i < rows; i += RG) acc = fma(v[i - j], (double)A[i * n + k], acc);
           }
-          acc += (double)accf;
         }
         __syncthreads();
         if (rg < RG) part[rg * KC + kk] = acc;
@@ -245,7 +260,7 @@ __device__ void hh_block_qr(T* A, long long rows, int n, double* v, double* part
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kHhThreads)
 k_hh_level(const SiteFacItem* __restrict__ items, int level, void* const* ptrs, const int* ival, int pass) {
   const SiteFacItem it = items[blockIdx.y];
   if (ival[it.branch_idx] != pass) return;
@@ -267,7 +282,7 @@ k_hh_level(const SiteFacItem* __restrict__ items, int level, void* const* ptrs, 
   extern __shared__ __align__(16) double sh[];
   double* v = sh;                            // up to 4n (or L) rows
   double* part = v + (L > 4 * n ? L : 4 * n);
-  __shared__ double red[8];
+  __shared__ double red[kHhThreads / 32];
   T* base = A + g * span * n;
   long long rows;
   if (level == 0) {
@@ -300,11 +315,11 @@ cudaError_t launch_hh_level(const SiteFacItem* items, int n_items, int level, in
                             void* const* ptrs, const int* ival, cudaStream_t s, int pass) {
   if (n_items == 0) return cudaSuccess;
   long long L = hh_leaf_rows(nmax);
-  size_t smem = sizeof(double) * ((size_t)(L > 4 * nmax ? L : 4 * nmax) + 256 + 256);
+  size_t smem = sizeof(double) * ((size_t)(L > 4 * nmax ? L : 4 * nmax) + 2 * kHhThreads);
   cudaError_t e = cudaFuncSetAttribute(k_hh_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_hh_level<T><<<dim3(grid_x, n_items), 256, smem, s>>>(items, level, ptrs, ival, pass);
+  k_hh_level<T><<<dim3(grid_x, n_items), kHhThreads, smem, s>>>(items, level, ptrs, ival, pass);
   return cudaGetLastError();
 }
 
@@ -398,29 +413,35 @@ cudaError_t launch_form(const SiteFacItem* items, int n_items, int grid_x, const
 
 // =================================================================== factor
 // Whether the Cholesky-QR branch can be trusted with this Gram C = cv^T cv
-// (n x n): its factor is only as accurate as C, whose accumulation noise
-// (FP32 runs flushed into FP64: ~1e-8 of the diagonal; FP64: ~1e-14) makes
-// Q = cv R^-1 non-orthonormal in the directions whose Schur complement is
-// within a few orders of it, and the Q-less update treats Q as orthonormal.
-// The pivoted Cholesky of C (pivot values only, in precision R, in the
-// scratch Cw) must keep every pivot above `safe` times the first: false (use
-// Householder) for a numerically rank-deficient or ill-conditioned Gram.
-// Block-uniform result.
+// (n x n): its factor is only as accurate as C.  The Gram's rounding is
+// relative to the norms of the columns it pairs (FP32 runs flushed into
+// FP64: ~1e-8 of that scale; FP64: ~1e-14), so a column that is a linear
+// combination of the others in exact arithmetic keeps a Schur complement of
+// that relative size, and the Q-less update would take the noise for a
+// direction (Q = cv R^-1 is then far from orthonormal).  The pivoted Cholesky
+// of C (pivot values only, in precision R, in the scratch Cw) therefore
+// checks every accepted pivot against the column's own diagonal: false (use
+// Householder) when some pivot keeps less than `safe` of it.  Pivots below
+// rel_cut of the first end the check (directions too small to matter: the
+// factorisation of G cuts them as rank).  Block-uniform result.
 template <typename R>
-__device__ bool gram_trusted(const SiteFacItem& it, int n, R* Cw, double* dg, double safe, double* rv, int* ri) {
+__device__ bool gram_trusted(const SiteFacItem& it, int n, R* Cw, double* dg, double safe, double rel_cut,
+                             double* rv, int* ri) {
+  double* od = dg + n;                       // the pivoted columns' original diagonals
   for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
     const int i = (int)(e / n), j = (int)(e - (long long)i * n);
     Cw[e] = (R)it.C[(long long)i * it.ldc + j];
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dg[i] = (double)Cw[(long long)i * n + i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dg[i] = od[i] = (double)Cw[(long long)i * n + i];
   __syncthreads();
   double d0 = 0.0;
   for (int j = 0; j < n; ++j) {
     const int p = block_argmax(dg, j, n, rv, ri);
     const double dp = dg[p];
     if (j == 0) d0 = dp;
-    if (!(dp > safe * d0) || !(dp > 0.0)) return false;
+    if (!(dp > rel_cut * d0) || !(dp > 0.0)) return true;
+    if (!(dp >= safe * od[p])) return false;
     if (p != j) {
       for (int k = threadIdx.x; k < n; k += blockDim.x) {
         R t = Cw[(long long)j * n + k]; Cw[(long long)j * n + k] = Cw[(long long)p * n + k]; Cw[(long long)p * n + k] = t;
@@ -429,7 +450,10 @@ __device__ bool gram_trusted(const SiteFacItem& it, int n, R* Cw, double* dg, do
       for (int k = threadIdx.x; k < n; k += blockDim.x) {
         R t = Cw[(long long)k * n + j]; Cw[(long long)k * n + j] = Cw[(long long)k * n + p]; Cw[(long long)k * n + p] = t;
       }
-      if (threadIdx.x == 0) { double t = dg[j]; dg[j] = dg[p]; dg[p] = t; }
+      if (threadIdx.x == 0) {
+        double t = dg[j]; dg[j] = dg[p]; dg[p] = t;
+        t = od[j]; od[j] = od[p]; od[p] = t;
+      }
       __syncthreads();
     }
     const R rjj = sqrt(Cw[(long long)j * n + j]);
@@ -475,11 +499,12 @@ k_factor(const SiteFacItem* __restrict__ items, int* ival, int only) {
   __shared__ int ri[16];
   __shared__ double red[16];
   if (ival[it.branch_idx] == 1) {
-    // the scratch after G (r x ld) holds the copy of C; v (4n doubles) the pivots
+    // the scratch after G (r x ld) holds the copy of C; v (4n doubles) the
+    // pivots and the original diagonals
     double* scratch = A + (long long)ld * ld;
-    const bool ok = it.rel_safe >= 1e-7
-                        ? gram_trusted<float>(it, n, reinterpret_cast<float*>(scratch), v, it.rel_safe, rv, ri)
-                        : gram_trusted<double>(it, n, scratch, v, it.rel_safe, rv, ri);
+    const bool ok = it.rel_safe >= 1e-6
+                        ? gram_trusted<float>(it, n, reinterpret_cast<float*>(scratch), v, it.rel_safe, it.rel, rv, ri)
+                        : gram_trusted<double>(it, n, scratch, v, it.rel_safe, it.rel, rv, ri);
     if (!ok) {
       if (threadIdx.x == 0) ival[it.branch_idx] = 2;
       return;
@@ -1049,6 +1074,17 @@ __device__ void floor_sqrt_eigs(double* sd, int n, double* red) {
   for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
   const double lo = kSqrtEigFloor * (m > 0.0 ? m : 1.0);
   for (int j = threadIdx.x; j < n; j += blockDim.x) sd[j] = fmax(sd[j], lo);
+  __syncthreads();
+}
+
+// Vs = diag(sd) Vt: the BP rotation of a leg scaled by the square roots of
+// the message's eigenvalues
+__device__ void scaled_rotation(const EnvEigItem& it, int n) {
+  if (!it.Vs) return;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    it.Vs[i * it.ld + j] = it.sqrtD[i] * it.Vt[i * it.ld + j];
+  }
 }
 
 // M (symmetrised, PSD) -> one-sided Jacobi on its columns: M V = U S with
@@ -1084,6 +1120,7 @@ k_env_eig(const EnvEigItem* __restrict__ items, const int* ival, int fp32) {
       it.Vt[i * it.ld + j] = (double)V[(long long)i * n + j];
     }
     floor_sqrt_eigs(it.sqrtD, n, red);
+    scaled_rotation(it, n);
     return;
   }
   double* A = it.work;                      // n x n column-major
@@ -1105,6 +1142,7 @@ k_env_eig(const EnvEigItem* __restrict__ items, const int* ival, int fp32) {
     it.Vt[i * it.ld + j] = V[(long long)i * n + j];   // row i of Vt = column i of V
   }
   floor_sqrt_eigs(it.sqrtD, n, red);
+  scaled_rotation(it, n);
 }
 
 cudaError_t launch_env_eig(const EnvEigItem* items, int n_items, int chimax, int fp32, const int* ival,

@@ -564,11 +564,10 @@ k_leg_umma(const LegItem* __restrict__ items, int n_items, int chimax, void* con
         // one block of 2 N16 rows per 32-wide K chunk
         const size_t bblk = (size_t)(2 * L.N16) * 128;
         const int K32 = (L.K8 + kKC - 1) / kKC * kKC;
-        const double* asc = items[c.item].a_scale;
         for (int e = ct; e < L.N16 * K32; e += kConv) {
           const int n = e / K32, j = e - n * K32;
           float x = 0.f;
-          if (n < L.Jout && j < L.J) x = (float)(L.A[(long long)n * L.lda + j] * (asc ? asc[n] : 1.0));
+          if (n < L.Jout && j < L.J) x = (float)L.A[(long long)n * L.lda + j];
           const float h = tf32_hi(x);
           const float l = x - h;
           unsigned char* blk = Bs + (size_t)(j / kKC) * bblk + (size_t)(j & 3) * 4;

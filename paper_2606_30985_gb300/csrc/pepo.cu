@@ -346,6 +346,7 @@ template <class I> DArr<I> stage(Planner& P, const std::vector<I>& v) {
 
 struct SlotWS {              // per in-flight site slot (gate update)
   double* L[4];
+  double* Ls[4];             // BP: the rotation scaled by the eigenvalue square roots
   int rank_idx[4];
   double* sqrtD[4];
   int branch_idx, kfac_idx, rankT_idx;
@@ -428,6 +429,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
     SlotWS& w = slots[k];
     for (int j = 0; j < 4; ++j) {
       w.L[j] = cv.take<double>(cm2);
+      w.Ls[j] = cv.take<double>(cm2);
       w.rank_idx[j] = P.new_ival(1);
       w.sqrtD[j] = cv.take<double>(chimax);
     }
@@ -494,12 +496,13 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
 
   // ---- gate-update waves
   const double rel_fac = (c->prec == PEPO_FP64) ? 1e-15 : 1e-13;
-  // smallest Gram pivot ratio the Cholesky-QR branch trusts: above the
-  // Gram's accumulation noise (FP32-storage Gram: ~1e-8 of the diagonal for
-  // 1e6 rows, ~1e-7 for 1e4; FP64: ~1e-13), where the pivots of directions
-  // that are zero in exact arithmetic land; below it the site takes the
-  // Householder branch
-  const double rel_safe = (c->prec == PEPO_FP64) ? 1e-10 : 1e-6;
+  // smallest fraction of a column's own Gram diagonal that a Cholesky-QR
+  // pivot must keep: far above the Gram's relative rounding (FP32-storage
+  // Gram: ~1e-8 of the paired columns' scale; FP64: ~1e-14) and the FP32
+  // pivot check's own (~1e-6), where the pivots of columns that depend
+  // linearly on the others land; below it the site takes the Householder
+  // branch
+  const double rel_safe = (c->prec == PEPO_FP64) ? 1e-10 : 1e-4;
   const double rel_env = I.cfg.pinv_rel;
   for (int col = 0; col < 4; ++col) {
     const auto& bl = I.colours[col];
@@ -591,7 +594,6 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
               li.a_rows = W.rank_idx[r];
               li.A = W.L[r];
               li.lda = chimax;
-              li.a_scale = nullptr;
               leg[r].push_back(li);
               t.dim[r] = W.rank_idx[r];
               cur_ref = li.out_ref;
@@ -751,6 +753,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
           e.work = W.T + (size_t)j * 2 * cm2;
           e.Vt = W.L[j];
           e.sqrtD = W.sqrtD[j];
+          e.Vs = W.Ls[j];
           eig.push_back(e);
         }
         int cur = refs[0];
@@ -762,11 +765,10 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
           li.leg = j;
           li.out_dim = view.dim[j];
           li.a_rows = view.dim[j];
-          li.A = W.L[j];
-          li.lda = chimax;
           // the rotated leg carries the square roots of the message's
           // eigenvalues: the Grams below then need no weights
-          li.a_scale = W.sqrtD[j];
+          li.A = W.Ls[j];
+          li.lda = chimax;
           leg[j].push_back(li);
           cur = li.out_ref;
         }
