@@ -190,6 +190,16 @@ pepo_status pepo_bp_converge(pepo_ctx* ctx, int* sweeps_out, double* delta_out);
  * pepo_bp_converge. */
 pepo_status pepo_correlator(pepo_ctx* ctx, double* C_out, pepo_diag* diag_out);
 
+/* Per-site Pauli weights of the last pepo_correlator call (Sec. 6.4 and
+ * Appendix A.3: the non-identity weight n(r, t) is 1 - out[4 v + 0]): for
+ * every site v the Hilbert-Schmidt weights of the Pauli components I, X, Y, Z
+ * of its tensor with the converged double-layer messages contracted on every
+ * leg, normalised to sum 1 per site.  out: host array of 4 * Lx * Ly doubles,
+ * site-major.  Synchronises the stream.  Errors: PEPO_E_INVALID (bad
+ * instance, NULL array), PEPO_E_CUDA.  Zero rows before the first
+ * correlator call. */
+pepo_status pepo_pauli_weights(pepo_ctx* ctx, int inst, double* out);
+
 /* Vidal-normalised singular values of a bond (Eq. 12) from its last update.
  * lam_out: at least chi_max doubles; *chi_out receives the live chi. */
 pepo_status pepo_get_spectrum(pepo_ctx* ctx, int inst, int bond, double* lam_out,

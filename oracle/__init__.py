@@ -12,9 +12,9 @@ Representation (deliberately different from the GPU path):
     ``[..., s, s']`` in complex128 (the GPU stores real Pauli coefficients);
   * gates act by literal conjugation ``g^dagger O g`` with the 2x2 / 4x4
     unitaries (the GPU uses real Pauli transfer matrices);
-  * every step follows the paper's order: absorb the square-rooted environment,
-    permute, Householder QR, RR = R1 R2, gate, SVD + truncation, Q M,
-    inverse permute, deabsorb (Sec. 2.5 "Gate Update", Algorithm 1).
+  * the bond update is the gauge change, QR reduction, gate, truncated SVD
+    and inverse gauge change of Sec. 2.5 "Gate Update" (Eqs. 11-12), each
+    written with plain numpy calls and no fusion.
 
 Modules
   lattice   geometry and the four-colour bond partition (Sec. 2.3)

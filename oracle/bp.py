@@ -25,6 +25,12 @@ the normalised trace.  Dividing by sqrt(N) (the paper's "Bethe norm",
 Table 1) makes the estimate independent of the network's overall scale; when
 N = 1 it is the paper's Eq. 9.
 
+Pauli weights (pauli_weights, n(r, t) of Sec. 6.4) are pinned by
+tests/test_oracle_spatial.py: on chains BP is exact, so they equal the
+dense operator's site weights (dense.site_pauli_weights); the initial
+network gives the observable at its site and the identity elsewhere; a
+centred observable on an odd grid gives C4-symmetric weights.
+
 Pinned by: tests/test_oracle_pepo.py -- on trees (1 x N chains and the star
 around an edge site) BP is exact, so the Bethe value must equal the dense
 C(t), including the negative values of cos(2 J t)^3.  On loops the Bethe
@@ -173,3 +179,43 @@ def bethe(net, t, m, M):
     C = float(np.real(phase)) * np.exp(logc - 0.5 * logn)
     return {"C": C, "C_proj": float(np.real(phase)) * np.exp(logc), "norm": float(np.exp(logn)),
             "log_norm": logn, "phase_imag": float(np.imag(phase))}
+
+
+def pauli_weights(net, M):
+    """Per-site Pauli weights in the double-layer BP environment (Sec. 6.4
+    n(r, t); reading: the Hilbert-Schmidt weight of each Pauli component of
+    the site with the converged messages on its legs).  With
+    A_p = Tr(P_p O_v) / 2 (the Pauli coefficients of the 2x2 pair),
+    w_p = sum conj(A_p[J]) A_p[J'] prod_u M_{u->v}[j_u, j'_u], normalised to
+    sum 1 per site.  Returns an N x 4 array (I, X, Y, Z)."""
+    out = np.zeros((net.N, 4))
+    for v in range(net.N):
+        for p, P in enumerate(G.PAULI_BY_INDEX):
+            A = np.einsum("...ab,ba->...", net.O[v], P) / 2.0
+            Y = A
+            for k, (_, u) in enumerate(net.legs[v]):
+                Y = leg_apply(Y, k, M[(u, v)])
+            out[v, p] = float(np.real(np.vdot(A.ravel(), Y.ravel())))
+        out[v] /= np.sum(out[v])
+    return out
+
+
+def spatial_observables(n, Lx, Ly, obs_xy):
+    """Appendix A.3: with p(r) = n(r) / sum n, the mean Manhattan radius
+    R_L1 = sum p |r - r_c|_1, the RMS radius R_L2 = sqrt(sum p |r - r_c|^2)
+    and S_frac = -sum p ln p / ln(Lx Ly).  n is a flat array in site order."""
+    n = np.asarray(n, dtype=np.float64)
+    tot = float(np.sum(n))
+    r1 = r2 = S = 0.0
+    if tot > 0.0:
+        for v in range(Lx * Ly):
+            x, y = v % Lx, v // Lx
+            pv = n[v] / tot
+            dx, dy = x - obs_xy[0], y - obs_xy[1]
+            r1 += pv * (abs(dx) + abs(dy))
+            r2 += pv * (dx * dx + dy * dy)
+            if pv > 0.0:
+                S -= pv * np.log(pv)
+        r2 = np.sqrt(r2)
+        S /= np.log(Lx * Ly)
+    return {"R_L1": r1, "R_L2": r2, "S_frac": S}

@@ -96,3 +96,19 @@ def operator_schmidt_values(O, N, cut):
     T = np.transpose(T, perm).reshape(4 ** cut, 4 ** (N - cut))
     s = np.linalg.svd(T, compute_uv=False)
     return s / np.linalg.norm(s)
+
+
+def site_pauli_weights(O, N):
+    """Pauli weights of every site of the dense operator O (Sec. 6.4 n(r, t)):
+    writing O = sum_p P_p (on qubit r) (x) B_p, the weight of p at r is
+    ||B_p||^2 / sum_q ||B_q||^2 (B_p = Tr_r[(P_p (x) 1) O] / 2).  Returns an
+    N x 4 array (I, X, Y, Z)."""
+    T = O.reshape([2] * (2 * N))
+    out = np.zeros((N, 4))
+    for r in range(N):
+        for p, P in enumerate(G.PAULI_BY_INDEX):
+            # contract P[b, a] with T[..., a (row r), ..., b (column r), ...]
+            B = np.tensordot(P, T, axes=([1, 0], [r, N + r])) / 2.0
+            out[r, p] = float(np.sum(np.abs(B) ** 2))
+        out[r] /= np.sum(out[r])
+    return out

@@ -13,18 +13,27 @@ State (Sec. 2.3 "Pauli Basis Tensor Network", Sec. 3.1 IsingState):
 Initial state (Sec. 2.3, Fig. 1): the observable Pauli at site c, the identity
 elsewhere, every bond dimension 1 and every message [[1]].
 
-Bond update (Sec. 2.5 steps 1-8, Algorithm 1), applied literally:
-  1. pseudo square roots of the environment messages by eigh of (M + M^H)/2,
-     eigenvalues below pinv_rel * max treated as zero (Sec. 4 Fig. 1 step 1);
-  2. absorb sqrt(M) on every leg except the cut;
-  3. permute the cut leg next to the physical pair;
-  4. Householder QR (numpy.linalg.qr) of the (env) x (cut, s, s') matrix;
-  5. RR4 = R1 . R2 contracted over the cut (Fig. 1 step 5);
-  6. the gate acts by g^dagger (.) g on the two physical pairs (Sec. 2.5 step 4);
-  7. SVD, truncation chi_new = min(#{s_i >= eps_cut s_0}, chi_max) (Eq. 11);
-  8. M1 = U sqrt(S), M2 = sqrt(S) V^H with the raw singular values; Q M;
-     inverse permute; deabsorb with M^{-1/2}; messages <- diag(lam) with
-     lam = s / ||s_kept|| (Eq. 12).
+Bond update (Sec. 2.5, Eqs. 11-12).  The update of the pair (v1, v2) is a
+gauge change, a reduction, the gate, a truncation and the inverse gauge
+change, in that order because each step needs the one before it:
+  * Gauge.  The converged double-layer messages are Gram matrices of the
+    environment seen by each leg; their (pseudo) square roots, from the
+    eigen-decomposition of the Hermitian part with eigenvalues below
+    pinv_rel times the largest set to zero, are absorbed on every leg but
+    the shared bond, so the bond sees an orthonormalised environment.
+  * Reduction.  Each site, reshaped to (environment legs) x (bond, s, s'),
+    factors as Q R (numpy's Householder QR); the isometry Q does not take
+    part in the gate, so only the two small R factors are contracted over
+    the bond into the two-site block.
+  * Gate.  The two-site Heisenberg-picture conjugation g^dagger (.) g acts
+    on the two physical pairs of the block.
+  * Truncation (Eq. 11).  The SVD of the block keeps
+    chi_new = min(#{s_i >= eps_cut s_0}, chi_max) values; U sqrt(S) and
+    sqrt(S) V^H (raw singular values) become the new R factors.
+  * Inverse gauge.  The new R factors are multiplied back into Q, the legs
+    return to canonical order, the absorbed square roots are removed with
+    the pseudo-inverse square roots, and the bond's messages become
+    diag(lam) with lam = s / ||s_kept|| (Eq. 12).
 
 Pinned by: tests/test_oracle_pepo.py -- without truncation the network
 contracts to the dense operator exactly on a 3 x 3 grid (loops) and on chains;
@@ -145,7 +154,8 @@ def apply_site_gates(net, g):
 
 
 def _absorbed_matrix(net, v, other, pinv_rel):
-    """Steps 1-3 for one site: cv as an (env) x (cut, s, s') matrix."""
+    """The gauged site: square-rooted messages on every leg but the cut, the
+    cut moved next to the physical pair, as an (env) x (cut, s, s') matrix."""
     O = net.O[v]
     deg = len(net.legs[v])
     kc = net.axis(v, other)

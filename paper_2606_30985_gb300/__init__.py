@@ -65,7 +65,7 @@ EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trot
            "pepo_mlp_forward", "pepo_mlp_gradient", "pepo_mlp_adam_step", "pepo_mlp_destroy",
            "pepo_ws_rows", "pepo_ws_features", "pepo_ws_targets", "pepo_ws_apply", "pepo_set_warmstart_weights",
            "pepo_c_drop", "pepo_set_bp_params", "pepo_get_messages", "pepo_set_messages",
-           "pepo_set_wait_limit", "pepo_save_state_host", "pepo_load_state_host"]
+           "pepo_set_wait_limit", "pepo_save_state_host", "pepo_load_state_host", "pepo_pauli_weights"]
 
 _lib = None
 
@@ -173,6 +173,8 @@ def load_library(path=LIB_PATH):
     lib.pepo_ws_apply.restype = I
     lib.pepo_set_warmstart_weights.argtypes = [P, P, S]
     lib.pepo_set_warmstart_weights.restype = I
+    lib.pepo_pauli_weights.argtypes = [P, I, ctypes.POINTER(D)]
+    lib.pepo_pauli_weights.restype = I
     lib.pepo_get_message.argtypes = [P, I, I, I, ctypes.POINTER(D), ctypes.POINTER(I)]
     lib.pepo_get_message.restype = I
     lib.pepo_num_bonds.argtypes = [P, I]
@@ -442,6 +444,24 @@ class Engine:
         n = 4 * int(np.prod(d)) if d else 4
         return buf[:n].reshape(tuple(d) + (4,)), list(dims)
 
+    def pauli_weights(self, inst=0):
+        """[Ly, Lx, 4] Pauli weights (I, X, Y, Z) per site from the last
+        correlator call (pepo_pauli_weights); rows sum to 1."""
+        c = self.cfgs[inst]
+        out = np.zeros(4 * c.Lx * c.Ly)
+        self._check(self.lib.pepo_pauli_weights(self.ctx, inst, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                    "pepo_pauli_weights")
+        return out.reshape(c.Ly, c.Lx, 4)
+
+    def spatial(self, inst=0):
+        """Operator spreading of the last correlator call (Sec. 6.4, Appendix
+        A.3): n(r) = 1 - I-weight per site, the mean Manhattan radius R_L1 and
+        the RMS Euclidean radius R_L2 from the observable site with weights
+        p(r) = n(r) / sum n, and S_frac = -sum p ln p / ln(number of sites)."""
+        w = self.pauli_weights(inst)
+        n = 1.0 - w[..., 0]
+        return spatial_observables(n, self.cfgs[inst])
+
     def message(self, inst, bond, direction):
         cm = self.cfgs[inst].chi_max
         buf = np.zeros(cm * cm)
@@ -680,6 +700,24 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def spatial_observables(n, cfg):
+    """R_L1, R_L2 and S_frac of a non-identity weight map n[y, x] around the
+    observable site of cfg (Appendix A.3, Eq. sfrac)."""
+    n = np.asarray(n, dtype=np.float64)
+    Ly, Lx = n.shape
+    ox, oy = cfg.obs if cfg.obs is not None else ((cfg.Lx - 1) // 2, (cfg.Ly - 1) // 2)
+    tot = float(np.sum(n))
+    yy, xx = np.mgrid[0:Ly, 0:Lx]
+    if not tot > 0.0:
+        return dict(n=n, R_L1=0.0, R_L2=0.0, S_frac=0.0)
+    p = n / tot
+    r1 = float(np.sum(p * (np.abs(xx - ox) + np.abs(yy - oy))))
+    r2 = float(np.sqrt(np.sum(p * ((xx - ox) ** 2 + (yy - oy) ** 2))))
+    nz = p[p > 0.0]
+    S = float(-np.sum(nz * np.log(nz)) / np.log(Lx * Ly)) if Lx * Ly > 1 else 0.0
+    return dict(n=n, R_L1=r1, R_L2=r2, S_frac=S)
 
 
 def flat_params(p):

@@ -209,6 +209,15 @@ struct SiteScalarItem {
   int ld;
 };
 
+// Per-site Pauli weights of the double-layer environment: out[p] =
+// sum_J x[J, p]^2 over the site tensor x rotated (and scaled by the square
+// roots of the message eigenvalues) on every leg, i.e. the Hilbert-Schmidt
+// weight of Pauli p at the site with the converged BP messages around it.
+struct PauliWItem {
+  TView x;
+  double* out;             // 4 doubles
+};
+
 // Per-bond edge factors: Z_e = m_ab . m_ba, Z2_e = sum M_ab * M_ba.
 struct EdgeItem {
   int chi_idx;

@@ -181,6 +181,49 @@ __global__ void k_edge_scalars(const EdgeItem* __restrict__ items, const int* iv
   if (threadIdx.x == 0) { *it.ze = z; *it.z2e = z2; }
 }
 
+// ======================================================= Pauli weights
+// Zero the outputs, then each block of grid.x sums its slice of one item's
+// squares per Pauli index (the index is the innermost one) and adds them in.
+__global__ void k_pauli_zero(const PauliWItem* __restrict__ items) {
+  if (threadIdx.x < 4) items[blockIdx.x].out[threadIdx.x] = 0.0;
+}
+
+template <typename T>
+__global__ void k_pauli_weights(const PauliWItem* __restrict__ items, void* const* ptrs, const int* ival) {
+  const PauliWItem it = items[blockIdx.y];
+  long long n = 4;
+  for (int k = 0; k < it.x.nlegs; ++k) n *= ival[it.x.dim[k]];
+  const T* x = static_cast<const T*>(ptrs[it.x.ref]);
+  // each thread visits whole groups of 4 (one J), so its p-th partial is Pauli p
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const long long groups = n / 4;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < groups;
+       g += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double v = (double)x[g * 4 + q];
+      acc[q] = fma(v, v, acc[q]);
+    }
+  }
+  __shared__ double red[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double t = bsum(acc[q], red);
+    if (threadIdx.x == 0) atomicAdd(&it.out[q], t);
+  }
+}
+
+template <typename T>
+cudaError_t launch_pauli_weights(const PauliWItem* items, int n, void* const* ptrs, const int* ival,
+                                 cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_pauli_zero<<<n, 32, 0, s>>>(items);
+  k_pauli_weights<T><<<dim3(64, n), 256, 0, s>>>(items, ptrs, ival);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pauli_weights<float>(const PauliWItem*, int, void* const*, const int*, cudaStream_t);
+template cudaError_t launch_pauli_weights<double>(const PauliWItem*, int, void* const*, const int*, cudaStream_t);
+
 cudaError_t launch_site_scalars(const SiteScalarItem* items, int n, const int* ival, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   k_site_scalars<<<n, 256, 0, s>>>(items, ival);

@@ -107,6 +107,7 @@ struct BpWave {
   DArr<LegItem> leg[4];
   DArr<GramLegItem> gram;
   DArr<RotItem> rot;
+  DArr<PauliWItem> pw;     // final waves only: Pauli weights of the rotated sites
 };
 
 struct SlLevel {
@@ -129,6 +130,7 @@ struct Inst {
   WsGeom* ws_geom = nullptr;          // 2 nb directed-bond descriptors of the warm-start features
   int* core_sweeps = nullptr;         // 2 nb: FP32 / FP64 Jacobi sweeps of each bond core
   double *sigma = nullptr, *disc = nullptr, *svals = nullptr, *vs = nullptr, *fv = nullptr;
+  double* pw = nullptr;    // per site: Pauli weights of the double-layer environment (4)
   double *ze = nullptr, *z2e = nullptr, *bethe_out = nullptr, *ptm = nullptr, *FA = nullptr, *FB = nullptr;
   int* nsv = nullptr;
   // plan
@@ -391,6 +393,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
   I.vhat = cv.take<double>(2 * I.nb * (size_t)chimax);
   I.sigma = cv.take<double>(I.N);
   I.disc = cv.take<double>(I.nb);
+  I.pw = cv.take<double>((size_t)4 * I.N);
   I.svals = cv.take<double>(I.nb * (size_t)rmax);
   I.nsv = cv.take<int>(I.nb);
   I.vs = cv.take<double>(I.N);
@@ -727,6 +730,7 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
       std::vector<LegItem> leg[4];
       std::vector<GramLegItem> gram;
       std::vector<RotItem> rot;
+      std::vector<PauliWItem> pws;
       int cls_used[5] = {0, 0, 0, 0, 0};
       int slot_base[5];
       {
@@ -793,11 +797,19 @@ bool plan_instance(Planner& P, Inst& I, int inst_id) {
           r.chi_idx = chi_idx(bw_);
           rot.push_back(r);
         }
+        if (fv_only) {
+          PauliWItem pw;
+          pw.x = view;
+          pw.x.ref = cur;
+          pw.out = I.pw + (size_t)4 * v;
+          pws.push_back(pw);
+        }
       }
       bw.eig = stage(P, eig);
       for (int j = 0; j < 4; ++j) bw.leg[j] = stage(P, leg[j]);
       bw.gram = stage(P, gram);
       bw.rot = stage(P, rot);
+      bw.pw = stage(P, pws);
       out.push_back(bw);
     }
   };
@@ -974,6 +986,7 @@ void resolve_all(pepo_ctx* c) {
         for (int a = 0; a < 4; ++a) resolve(w.leg[a], d);
         resolve(w.gram, d);
         resolve(w.rot, d);
+        resolve(w.pw, d);
       }
     for (int l = 0; l < 4; ++l) resolve(I.sl[l].items, d);
     resolve(I.msgs, d); resolve(I.sscal, d); resolve(I.escal, d); resolve(I.bethe, d);
@@ -1052,6 +1065,7 @@ void build_group(Planner& P, pepo_ctx* c) {
       std::vector<const DArr<LegItem>*> leg[4];
       std::vector<const DArr<GramLegItem>*> gram;
       std::vector<const DArr<RotItem>*> rot;
+      std::vector<const DArr<PauliWItem>*> pw;
       for (auto& I : c->inst) {
         const std::vector<BpWave>& src = f ? I.fwaves : I.bwaves;
         if (w >= src.size()) continue;
@@ -1059,11 +1073,13 @@ void build_group(Planner& P, pepo_ctx* c) {
         for (int a = 0; a < 4; ++a) leg[a].push_back(&src[w].leg[a]);
         gram.push_back(&src[w].gram);
         rot.push_back(&src[w].rot);
+        pw.push_back(&src[w].pw);
       }
       out[w].eig = cat_items(P, eig);
       for (int a = 0; a < 4; ++a) out[w].leg[a] = cat_items(P, leg[a]);
       out[w].gram = cat_items(P, gram);
       out[w].rot = cat_items(P, rot);
+      out[w].pw = cat_items(P, pw);
     }
   }
   for (int l = 0; l < 4; ++l) {
@@ -1371,6 +1387,10 @@ pepo_status run_bp_waves(pepo_ctx* c, Inst& I, std::vector<BpWave>& waves) {
              launch_gram_leg_reduce(w.gram.d, w.gram.n, chimax, c->tune.gram_leg_splits, use_umma<T>(c, chimax) ? 1 : 0,
                                     c->d_ival, s));
     LAUNCH_T(K_MSG, nullptr, w.rot.n, launch_rotate_back(w.rot.d, w.rot.n, chimax, c->d_ival, s));
+    if (w.pw.n > 0) {
+      LAUNCH_T(K_OTHER, nullptr, w.pw.n, launch_pauli_weights<T>(w.pw.d, w.pw.n, c->d_ptrs, c->d_ival, s));
+      c->launches++;   // the zeroing kernel
+    }
   }
   return PEPO_OK;
 }
@@ -2409,6 +2429,22 @@ pepo_status pepo_set_state(pepo_ctx* c, int inst, const double* sites, size_t co
     st = pepo_set_site(c, inst, v, sites + off, 1, n);
     if (st != PEPO_OK) return st;
     off += n;
+  }
+  return PEPO_OK;
+}
+
+pepo_status pepo_pauli_weights(pepo_ctx* c, int inst, double* out) {
+  if (!c) return PEPO_E_INVALID;
+  if (inst < 0 || inst >= c->n_inst || !out) return fail(c, PEPO_E_INVALID, "bad arguments");
+  Inst& I = c->inst[inst];
+  std::vector<double> w((size_t)4 * I.N);
+  if (cudaMemcpyAsync(w.data(), I.pw, sizeof(double) * w.size(), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "Pauli weights: %s", cudaGetErrorString(cudaGetLastError()));
+  for (int v = 0; v < I.N; ++v) {
+    double t = 0.0;
+    for (int p = 0; p < 4; ++p) t += w[4 * (size_t)v + p];
+    for (int p = 0; p < 4; ++p) out[4 * (size_t)v + p] = t > 0.0 ? w[4 * (size_t)v + p] / t : 0.0;
   }
   return PEPO_OK;
 }
