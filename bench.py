@@ -162,8 +162,10 @@ PAPER_STEPS_PER_S_10X10_CHI100 = 1.0 / 1440.0
 # measured DRAM bytes (read + write) per algorithmic byte, per kernel class,
 # with the profile summary it comes from; an entry is removed when its kernel
 # changes (traffic is then reported as null until it is measured again)
-TRAFFIC_RATIO = {"leg_contract": (0.986, "profiles/k_leg_umma_3x3_chi100_dram.md"),
-                 "bp_leg_contract": (0.986, "profiles/k_leg_umma_3x3_chi100_dram.md")}
+TRAFFIC_RATIO = {"leg_contract": (0.986, "profiles/k_leg_umma_bp_3x3_chi100_dram.md"),
+                 "bp_leg_contract": (0.986, "profiles/k_leg_umma_bp_3x3_chi100_dram.md")}
+# kernel classes that run on the tensor cores in the split-TF32 mode
+TENSOR_CLASSES = ("leg_contract", "bp_leg_contract", "gram_leg", "reconstruct")
 
 
 def fp32_alu_peak_tflops():
@@ -312,6 +314,7 @@ def run_gpu(args, rank, world, local):
     clocks = Clocks(local, os.path.join(clocks_dir(), "clocks_rank%d.csv" % rank))
     eng.reset_timing()
     eng.set_timing(True)
+    eng.qr_branch_counts(reset=True)
     l0 = eng.launches()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -332,6 +335,7 @@ def run_gpu(args, rank, world, local):
     launches = eng.launches() - l0
     ms = e0.elapsed_time(e1)
     timing = eng.timing()
+    qr = eng.qr_branch_counts(reset=True)
     ms, wall = max_over_ranks([ms, wall], "cuda:%d" % local)
     steps_total = args.steps * world
     value = steps_total / (ms / 1e3)
@@ -344,7 +348,8 @@ def run_gpu(args, rank, world, local):
     nl = max(1, tk["launches"])
     gbs = (tk["bytes"] / nl) / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
     tfs = (tk["flops"] / nl) / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
-    tensor_mode = w["precision"] == "tf32x3"
+    # the tcgen05 classes of the split-TF32 mode; every other class is SIMT
+    tensor_mode = w["precision"] == "tf32x3" and name in TENSOR_CLASSES
     alu_peak = fp32_alu_peak_tflops()
     cpeak = bf16 * TF32_PER_BF16 if tensor_mode else alu_peak
     if tfs / cpeak >= gbs / hbm:
@@ -421,6 +426,7 @@ def run_gpu(args, rank, world, local):
                                "3 |psi| per site update, one read of every tensor per BP sweep)"},
         "kernel_ms": {k: round(v["ms"], 3) for k, v in timing.items() if v["launches"]},
         "kernel_bytes_per_step": {k: v["bytes"] / args.steps for k, v in timing.items() if v["launches"]},
+        "kernel_launches_per_step": {k: v["launches"] / args.steps for k, v in timing.items() if v["launches"]},
         "clocks": clk,
         # end to end through the public API: the timed steps (results read back
         # to the host every step) plus the host -> device upload of the state
@@ -431,6 +437,8 @@ def run_gpu(args, rank, world, local):
                 "h2d_source": "page-locked host memory" if pinned else "pageable host memory",
                 "state_generation_and_upload_s": upload_s},
         "gpu_launches": launches,
+        # sites per hybrid-QR branch per step (Sec. 4.2)
+        "qr_branches_per_step": {k: v / args.steps for k, v in qr.items()},
         "C_last": diags[-1]["C"],
     }
     eng.close()

@@ -408,6 +408,14 @@ pepo_status pepo_get_tuning(const pepo_ctx* ctx, pepo_tuning* tuning);
  * the paper's method: failure handling of this implementation. */
 pepo_status pepo_set_wait_limit(pepo_ctx* ctx, double seconds);
 
+/* Sites factored by each branch of the hybrid QR (Sec. 4.2, Eq. 10) since the
+ * last reset, over all instances: out[0] Householder by the branch rule,
+ * out[1] Cholesky-QR, out[2] Cholesky-QR sites handed to Householder because
+ * a pivot of their Gram kept too small a share of its column's diagonal.
+ * `out` is host memory of 3 values; reset != 0 zeroes the counters after the
+ * read.  Synchronises the stream.  Errors: PEPO_E_INVALID (null), PEPO_E_CUDA. */
+pepo_status pepo_qr_branch_counts(pepo_ctx* ctx, long long* out, int reset);
+
 /* Number of kernel launches enqueued by this context so far. */
 long long pepo_launch_count(const pepo_ctx* ctx);
 

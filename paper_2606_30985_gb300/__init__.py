@@ -65,7 +65,8 @@ EXPORTS = ["pepo_config_default", "pepo_required_bytes", "pepo_init", "pepo_trot
            "pepo_mlp_forward", "pepo_mlp_gradient", "pepo_mlp_adam_step", "pepo_mlp_destroy",
            "pepo_ws_rows", "pepo_ws_features", "pepo_ws_targets", "pepo_ws_apply", "pepo_set_warmstart_weights",
            "pepo_c_drop", "pepo_set_bp_params", "pepo_get_messages", "pepo_set_messages",
-           "pepo_set_wait_limit", "pepo_save_state_host", "pepo_load_state_host", "pepo_pauli_weights"]
+           "pepo_set_wait_limit", "pepo_save_state_host", "pepo_load_state_host", "pepo_pauli_weights",
+           "pepo_qr_branch_counts"]
 
 _lib = None
 
@@ -196,6 +197,8 @@ def load_library(path=LIB_PATH):
     lib.pepo_get_timing.restype = I
     lib.pepo_reset_timing.argtypes = [P]
     lib.pepo_reset_timing.restype = I
+    lib.pepo_qr_branch_counts.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), I]
+    lib.pepo_qr_branch_counts.restype = I
     lib.pepo_launch_count.argtypes = [P]
     lib.pepo_launch_count.restype = ctypes.c_longlong
     lib.pepo_last_error.argtypes = [P]
@@ -328,6 +331,14 @@ class Engine:
 
     def launches(self):
         return int(self.lib.pepo_launch_count(self.ctx))
+
+    def qr_branch_counts(self, reset=True):
+        """Sites factored by each hybrid-QR branch (Sec. 4.2) since the last
+        reset: householder (branch rule), cholesky, cholesky_fallback (a Gram
+        pivot kept too small a share of its column's diagonal)."""
+        out = (ctypes.c_longlong * 3)()
+        self._check(self.lib.pepo_qr_branch_counts(self.ctx, out, 1 if reset else 0), "pepo_qr_branch_counts")
+        return dict(householder=int(out[0]), cholesky=int(out[1]), cholesky_fallback=int(out[2]))
 
     def set_tuning(self, gram_leg_splits=0, gram_rows_splits=0):
         """Launch shapes (pepo_set_tuning): K splits of the free-leg and the

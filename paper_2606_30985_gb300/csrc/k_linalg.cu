@@ -7,7 +7,8 @@
 //   k_branch       Eq. 10 branch rule: Cholesky-QR when n > n_thr and
 //                  m / n > ratio_thr, Householder otherwise (Sec. 4.2).
 //   k_hh_level     Householder QR (TSQR tree, R only) of cv in its storage
-//                  precision with FP64 reductions (Sec. 4.2 Householder-QR).
+//                  precision with FP64 reductions (Sec. 4.2 Householder-QR);
+//                  each tree block factored in panels (compact WY).
 //   k_formG / k_formB   fold the gate's operator-Schmidt factors into the
 //                  R-factor: X = (F_kappa (x) 1) cv, G = X^T X or B = R-side of X.
 //   k_factor       rank-revealing factor T of X: pivoted Cholesky of G
@@ -171,90 +172,250 @@ cudaError_t launch_branch(const SiteFacItem* items, int n_items, int* ival, cuda
 __host__ __device__ inline long long hh_leaf_rows(int n) { return n * 4 > 256 ? (long long)n * 4 : 256; }
 constexpr int kHhThreads = 512;   // threads of a TSQR block
 
+// Panel width of the blocked QR: the panel (L x NB) lives in shared memory.
+template <typename T> struct HhPanel;
+template <> struct HhPanel<float> { static constexpr int NB = 16; };
+template <> struct HhPanel<double> { static constexpr int NB = 8; };
+
+// Shared-memory plan of one TSQR block (leaf rows L): panel V (column-major,
+// leading dimension L + 1 so that consecutive rows of a column and the rows
+// of consecutive columns fall in different banks), per-warp partial products
+// of the trailing update, W = V^T A and W2 = T^T W, V^T V and the T factor of
+// the compact WY form, tau, a block-reduction scratch.
+struct HhSmem {
+  size_t p, red, wd, w2, vtv, tm, tau, bred, total;
+  int lp;
+};
 template <typename T>
-__device__ void hh_block_qr(T* A, long long rows, int n, double* v, double* part, double* red) {
+__host__ __device__ inline HhSmem hh_smem(long long L) {
+  constexpr int NB = HhPanel<T>::NB;
+  HhSmem m;
+  m.lp = (int)L + 1;
+  size_t o = 0;
+  m.p = o;    o += sizeof(T) * (size_t)NB * m.lp;
+  o = (o + 15) & ~(size_t)15;
+  m.red = o;  o += sizeof(T) * (size_t)(kHhThreads / 32) * NB * 32;
+  m.wd = o;   o += sizeof(double) * (size_t)NB * 32;
+  m.w2 = o;   o += sizeof(T) * (size_t)NB * 32;
+  o = (o + 15) & ~(size_t)15;
+  m.vtv = o;  o += sizeof(double) * (size_t)NB * NB;
+  m.tm = o;   o += sizeof(double) * (size_t)NB * NB;
+  m.tau = o;  o += sizeof(double) * (size_t)NB;
+  m.bred = o; o += sizeof(double) * (size_t)(kHhThreads / 32);
+  m.total = o;
+  return m;
+}
+
+__device__ inline void ld4(const float* p, float (&x)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+}
+__device__ inline void st4(float* p, const float (&x)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+__device__ inline void ld4(const double* p, double (&x)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+}
+__device__ inline void st4(double* p, const double (&x)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(x[0], x[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(x[2], x[3]);
+}
+
+// Householder QR of one TSQR block A (rows x n, row-major, n % 4 == 0, base
+// 16-byte aligned) in place: R in the top rows, zeros below (Q is not kept).
+// Blocked by panels of NB columns in the compact WY form H_1 ... H_nb =
+// I - V T V^T: the panel is factored in shared memory, then the trailing
+// columns take all nb reflections in one pass, A <- A - V (T^T (V^T A)),
+// instead of one pass per reflection.  Arithmetic in T's precision (FP32
+// storage: FP32 reflections, backward stable to the data's own precision),
+// norms, cross-warp sums and the T factor in FP64.  512 threads.
+template <typename T>
+__device__ void hh_block_qr(T* A, long long rows, int n, unsigned char* smem, const HhSmem& S) {
+  constexpr int NB = HhPanel<T>::NB;
+  T* P = reinterpret_cast<T*>(smem + S.p);
+  T* red = reinterpret_cast<T*>(smem + S.red);
+  double* Wd = reinterpret_cast<double*>(smem + S.wd);
+  T* W2 = reinterpret_cast<T*>(smem + S.w2);
+  double* VtV = reinterpret_cast<double*>(smem + S.vtv);
+  double* Tm = reinterpret_cast<double*>(smem + S.tm);
+  double* tau = reinterpret_cast<double*>(smem + S.tau);
+  double* bred = reinterpret_cast<double*>(smem + S.bred);
+  const int lp = S.lp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarp = blockDim.x >> 5;
   const int kmax = (int)(rows < n ? rows : n);
-  for (int j = 0; j < kmax; ++j) {
-    double s = 0.0;
-    for (long long i = j + threadIdx.x; i < rows; i += blockDim.x) {
-      double x = (double)A[i * n + j];
-      s = fma(x, x, s);
-    }
-    s = block_sum(s, red);
-    const double alpha = (double)A[(long long)j * n + j];
-    const double normx = sqrt(s);
-    __syncthreads();
-    if (normx == 0.0) continue;
-    const double beta = alpha >= 0.0 ? -normx : normx;
-    const double v0 = alpha - beta;
-    const double tau = (beta - alpha) / beta;
-    // v (unit leading entry) into shared memory; the column becomes (beta, 0, ...)
-    for (long long i = j + threadIdx.x; i < rows; i += blockDim.x) {
-      double vi = (i == j) ? 1.0 : (double)A[i * n + j] / v0;
-      v[i - j] = vi;
+  for (int j0 = 0; j0 < kmax; j0 += NB) {
+    const int nb = kmax - j0 < NB ? kmax - j0 : NB;
+    const int pr = (int)(rows - j0);
+    // ---- panel rows j0.., columns j0..j0+nb-1 (zero columns beyond nb)
+    for (int e = tid; e < pr * NB; e += blockDim.x) {
+      const int i = e / NB, l = e - i * NB;
+      P[l * lp + i] = (l < nb) ? A[(long long)(j0 + i) * n + j0 + l] : T(0);
     }
     __syncthreads();
-    for (long long i = j + threadIdx.x; i < rows; i += blockDim.x) A[i * n + j] = (i == j) ? (T)beta : T(0);
-    const int nc = n - j - 1;
-    if (nc > 0) {
-      // columns per pass: at most a quarter of the block, so that at least
-      // four row groups share each column's dot product (short chains)
-      const int kcap = (int)blockDim.x / 4 > 32 ? (int)blockDim.x / 4 : 32;
-      const int KC = nc < kcap ? nc : kcap;
-      const int RG = blockDim.x / KC;
-      const int t = threadIdx.x;
-      const int kk = t % KC, rg = t / KC;
-      for (int kb = 0; kb < nc; kb += KC) {
-        const int k = j + 1 + kb + kk;
-        double acc = 0.0;
-        if (rg < RG && kb + kk < nc) {
-          if (sizeof(T) == 4) {
-            // four independent FP32 runs of 16 terms each, flushed into FP64
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-            int run = 0;
-            long long i = j + rg;
-            const long long step = RG;
-            for (; i + 3 * step < rows; i += 4 * step) {
-              a0 = fmaf((float)v[i - j], (float)A[i * n + k], a0);
-              a1 = fmaf((float)v[i + step - j], (float)A[(i + step) * n + k], a1);
-              a2 = fmaf((float)v[i + 2 * step - j], (float)A[(i + 2 * step) * n + k], a2);
-              a3 = fmaf((float)v[i + 3 * step - j], (float)A[(i + 3 * step) * n + k], a3);
-              if (++run == 16) {
-                acc += ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
-                a0 = a1 = a2 = a3 = 0.f;
-                run = 0;
-              }
-            }
-            for (; i < rows; i += step) a0 = fmaf((float)v[i - j], (float)A[i * n + k], a0);
-            acc += ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
-          } else {
-            for (long long i = j + rg; i < rows; i += RG) acc = fma(v[i - j], (double)A[i * n + k], acc);
-          }
-        }
-        __syncthreads();
-        if (rg < RG) part[rg * KC + kk] = acc;
-        __syncthreads();
-        if (t < KC && kb + t < nc) {
-          double w = 0.0;
-          for (int g = 0; g < RG; ++g) w += part[g * KC + t];
-          part[RG * KC + t] = tau * w;
-        }
-        __syncthreads();
-        if (rg < RG && kb + kk < nc) {
-          const double tw = part[RG * KC + kk];
-          if (sizeof(T) == 4) {
-            // FP32 storage: the reflection in FP32 (backward stable to the
-            // data's own precision; FP64 here would run at 1/64 of the rate)
-            const float twf = (float)tw;
-            for (long long i = j + rg; i < rows; i += RG)
-              A[i * n + k] = (T)fmaf(-(float)v[i - j], twf, (float)A[i * n + k]);
-          } else {
-            for (long long i = j + rg; i < rows; i += RG)
-              A[i * n + k] = (T)((double)A[i * n + k] - v[i - j] * tw);
-          }
-        }
-        __syncthreads();
+    // ---- unblocked Householder on the panel
+    for (int jj = 0; jj < nb; ++jj) {
+      T* col = P + jj * lp;
+      double s = 0.0;
+      for (int i = jj + tid; i < pr; i += blockDim.x) {
+        const double x = (double)col[i];
+        s = fma(x, x, s);
       }
+      s = block_sum(s, bred);
+      const double alpha = (double)col[jj];
+      const double normx = sqrt(s);
+      double beta = alpha, tj = 0.0, v0 = 1.0;
+      if (normx > 0.0) {
+        beta = alpha >= 0.0 ? -normx : normx;
+        v0 = alpha - beta;
+        tj = (beta - alpha) / beta;
+      }
+      __syncthreads();
+      if (normx > 0.0)
+        for (int i = jj + 1 + tid; i < pr; i += blockDim.x) col[i] = (T)((double)col[i] / v0);
+      if (tid == 0) {
+        col[jj] = (T)beta;
+        tau[jj] = tj;
+      }
+      __syncthreads();
+      // the reflection on the panel's later columns, one warp per column
+      if (tj != 0.0) {
+        for (int c = jj + 1 + warp; c < nb; c += nwarp) {
+          T* pc = P + c * lp;
+          T acc = T(0);
+          for (int i = jj + 1 + lane; i < pr; i += 32) acc += col[i] * pc[i];
+          const double w = tj * (warp_sum((double)acc) + (double)pc[jj]);
+          __syncwarp();
+          if (lane == 0) pc[jj] = (T)((double)pc[jj] - w);
+          const T wt = (T)w;
+          for (int i = jj + 1 + lane; i < pr; i += 32) pc[i] -= col[i] * wt;
+        }
+      }
+      __syncthreads();
+    }
+    // ---- R of the panel and zeros below it back to A; then V explicit in P
+    // (unit diagonal, zeros above) for the WY products
+    for (int e = tid; e < pr * nb; e += blockDim.x) {
+      const int i = e / nb, l = e - i * nb;
+      A[(long long)(j0 + i) * n + j0 + l] = (i <= l) ? P[l * lp + i] : T(0);
+    }
+    __syncthreads();
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      const int l = e / NB, i = e - l * NB;
+      if (l < nb && i <= l && i < pr) P[l * lp + i] = (i == l) ? T(1) : T(0);
+    }
+    __syncthreads();
+    const int c0 = j0 + nb;
+    if (c0 >= n) continue;
+    // ---- T factor: T[0:j, j] = -tau_j T[0:j, 0:j] (V[:, 0:j]^T v_j)
+    for (int q = warp; q < NB * NB; q += nwarp) {
+      const int l = q / NB, j = q - l * NB;
+      if (l >= j || j >= nb) continue;
+      const T* vl = P + l * lp;
+      const T* vj = P + j * lp;
+      double acc = 0.0;
+      for (int i = j + lane; i < pr; i += 32) acc = fma((double)vl[i], (double)vj[i], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) VtV[l * NB + j] = acc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int j = 0; j < NB; ++j) {
+        for (int l = 0; l < NB; ++l) Tm[l * NB + j] = 0.0;
+        if (j >= nb) continue;
+        Tm[j * NB + j] = tau[j];
+        for (int l = 0; l < j; ++l) {
+          double z = 0.0;
+          for (int m = l; m < j; ++m) z += Tm[l * NB + m] * VtV[m * NB + j];
+          Tm[l * NB + j] = -tau[j] * z;
+        }
+      }
+    }
+    __syncthreads();
+    // ---- trailing columns in blocks of 32: 8 column quads x 64 row groups
+    const int cs = c0 & ~3;
+    const int kq = tid & 7, rgi = tid >> 3, nrg = blockDim.x >> 3;
+    for (int cb = cs; cb < n; cb += 32) {
+      const int cq = cb + 4 * kq;
+      const bool colok = cq < n;
+      T acc[NB][4];
+#pragma unroll
+      for (int l = 0; l < NB; ++l)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[l][q] = T(0);
+      if (colok) {
+        for (int i = rgi; i < pr; i += nrg) {
+          T a[4];
+          ld4(A + (long long)(j0 + i) * n + cq, a);
+#pragma unroll
+          for (int l = 0; l < NB; ++l) {
+            const T v = P[l * lp + i];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[l][q] += v * a[q];
+          }
+        }
+      }
+      // sum over the four row groups of a warp, then over the warps
+#pragma unroll
+      for (int l = 0; l < NB; ++l)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          T x = acc[l][q];
+          x += __shfl_xor_sync(0xffffffffu, x, 8);
+          x += __shfl_xor_sync(0xffffffffu, x, 16);
+          acc[l][q] = x;
+        }
+      if (lane < 8) {
+#pragma unroll
+        for (int l = 0; l < NB; ++l)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) red[(warp * NB + l) * 32 + 4 * kq + q] = acc[l][q];
+      }
+      __syncthreads();
+      for (int e = tid; e < NB * 32; e += blockDim.x) {
+        const int l = e >> 5, k = e & 31;
+        double z = 0.0;
+        for (int w = 0; w < nwarp; ++w) z += (double)red[(w * NB + l) * 32 + k];
+        Wd[e] = z;
+      }
+      __syncthreads();
+      for (int e = tid; e < NB * 32; e += blockDim.x) {
+        const int l = e >> 5, k = e & 31;
+        double z = 0.0;
+        for (int m = 0; m <= l; ++m) z += Tm[m * NB + l] * Wd[m * 32 + k];
+        // the panel's own columns (below c0, in the first block) stay as written
+        W2[e] = (cb + k < c0) ? T(0) : (T)z;
+      }
+      __syncthreads();
+      if (colok) {
+        T w2[NB][4];
+#pragma unroll
+        for (int l = 0; l < NB; ++l)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) w2[l][q] = W2[l * 32 + 4 * kq + q];
+        for (int i = rgi; i < pr; i += nrg) {
+          T* pa = A + (long long)(j0 + i) * n + cq;
+          T a[4];
+          ld4(pa, a);
+#pragma unroll
+          for (int l = 0; l < NB; ++l) {
+            const T v = P[l * lp + i];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a[q] -= v * w2[l][q];
+          }
+          if (cq < c0) {
+            // quad straddling the panel: keep the panel's columns untouched
+            T o[4];
+            ld4(pa, o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (cq + q < c0) a[q] = o[q];
+          }
+          st4(pa, a);
+        }
+      }
+      __syncthreads();
     }
   }
 }
@@ -279,10 +440,8 @@ k_hh_level(const SiteFacItem* __restrict__ items, int level, void* const* ptrs, 
   const long long g = blockIdx.x;
   if (g >= nblk) return;
   T* A = static_cast<T*>(ptrs[it.cv.ref]);
-  extern __shared__ __align__(16) double sh[];
-  double* v = sh;                            // up to 4n (or L) rows
-  double* part = v + (L > 4 * n ? L : 4 * n);
-  __shared__ double red[kHhThreads / 32];
+  extern __shared__ __align__(16) unsigned char hh_sh[];
+  const HhSmem S = hh_smem<T>(L);            // within the launch's plan for nmax >= n
   T* base = A + g * span * n;
   long long rows;
   if (level == 0) {
@@ -307,15 +466,14 @@ k_hh_level(const SiteFacItem* __restrict__ items, int level, void* const* ptrs, 
       rows += rr;
     }
   }
-  hh_block_qr<T>(base, rows, n, v, part, red);
+  hh_block_qr<T>(base, rows, n, hh_sh, S);
 }
 
 template <typename T>
 cudaError_t launch_hh_level(const SiteFacItem* items, int n_items, int level, int grid_x, int nmax,
                             void* const* ptrs, const int* ival, cudaStream_t s, int pass) {
   if (n_items == 0) return cudaSuccess;
-  long long L = hh_leaf_rows(nmax);
-  size_t smem = sizeof(double) * ((size_t)(L > 4 * nmax ? L : 4 * nmax) + 2 * kHhThreads);
+  const size_t smem = hh_smem<T>(hh_leaf_rows(nmax)).total;
   cudaError_t e = cudaFuncSetAttribute(k_hh_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -324,14 +482,26 @@ cudaError_t launch_hh_level(const SiteFacItem* items, int n_items, int level, in
 }
 
 // R (top min(m, n) rows of cv after the tree) -> FP64 C buffer, rows -> kfac
+// acct (2 doubles, may be null): algorithmic FLOPs and bytes of the QR of
+// each factored m x n matrix (2 m n^2 - 2 n^3 / 3 for m >= n, else
+// 2 m^2 n - 2 m^3 / 3; one read of the matrix), accumulated on the device
+// because only the device knows which sites took this branch.
 template <typename T>
-__global__ void k_hh_extract(const SiteFacItem* __restrict__ items, void* const* ptrs, int* ival, int pass) {
+__global__ void k_hh_extract(const SiteFacItem* __restrict__ items, void* const* ptrs, int* ival, int pass,
+                             double* acct) {
   const SiteFacItem it = items[blockIdx.x];
   if (ival[it.branch_idx] != pass) return;
   long long m;
   int n;
   cv_shape(it.cv, ival, m, n);
   const int k = (int)(m < n ? m : n);
+  if (acct && threadIdx.x == 0) {
+    const double dm = (double)m, dn = (double)n;
+    const double f = m >= n ? 2.0 * dm * dn * dn - 2.0 * dn * dn * dn / 3.0
+                            : 2.0 * dm * dm * dn - 2.0 * dm * dm * dm / 3.0;
+    atomicAdd(&acct[0], f);
+    atomicAdd(&acct[1], dm * dn * (double)sizeof(T));
+  }
   const T* A = static_cast<const T*>(ptrs[it.cv.ref]);
   for (int e = threadIdx.x; e < k * n; e += blockDim.x) {
     int a = e / n, q = e - a * n;
@@ -342,9 +512,9 @@ __global__ void k_hh_extract(const SiteFacItem* __restrict__ items, void* const*
 
 template <typename T>
 cudaError_t launch_hh_extract(const SiteFacItem* items, int n_items, void* const* ptrs, int* ival,
-                              cudaStream_t s, int pass) {
+                              cudaStream_t s, int pass, double* acct) {
   if (n_items == 0) return cudaSuccess;
-  k_hh_extract<T><<<n_items, 256, 0, s>>>(items, ptrs, ival, pass);
+  k_hh_extract<T><<<n_items, 256, 0, s>>>(items, ptrs, ival, pass, acct);
   return cudaGetLastError();
 }
 
@@ -479,9 +649,10 @@ __device__ bool gram_trusted(const SiteFacItem& it, int n, R* Cw, double* dg, do
 // A Cholesky-branch site whose Gram fails gram_trusted is marked branch 2 and
 // left for the Householder pass that follows (only = 2 runs that pass only).
 __global__ void __launch_bounds__(512)
-k_factor(const SiteFacItem* __restrict__ items, int* ival, int only) {
+k_factor(const SiteFacItem* __restrict__ items, int* ival, int only, unsigned long long* qcount) {
   const SiteFacItem it = items[blockIdx.x];
   if (only >= 0 && ival[it.branch_idx] != only) return;
+  if (qcount && threadIdx.x == 0 && ival[it.branch_idx] == 0) atomicAdd(&qcount[0], 1ull);
   long long m;
   int n;
   cv_shape(it.cv, ival, m, n);
@@ -505,6 +676,7 @@ k_factor(const SiteFacItem* __restrict__ items, int* ival, int only) {
     const bool ok = it.rel_safe >= 1e-6
                         ? gram_trusted<float>(it, n, reinterpret_cast<float*>(scratch), v, it.rel_safe, it.rel, rv, ri)
                         : gram_trusted<double>(it, n, scratch, v, it.rel_safe, it.rel, rv, ri);
+    if (threadIdx.x == 0 && qcount) atomicAdd(&qcount[ok ? 1 : 2], 1ull);
     if (!ok) {
       if (threadIdx.x == 0) ival[it.branch_idx] = 2;
       return;
@@ -617,13 +789,13 @@ k_factor(const SiteFacItem* __restrict__ items, int* ival, int only) {
 }
 
 cudaError_t launch_factor(const SiteFacItem* items, int n_items, int rmax, int nmax, int* ival,
-                          cudaStream_t s, int only) {
+                          cudaStream_t s, int only, unsigned long long* qcount) {
   if (n_items == 0) return cudaSuccess;
   size_t smem = sizeof(double) * ((size_t)2 * rmax + 4 * nmax);
   cudaError_t e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_factor<<<n_items, 512, smem, s>>>(items, ival, only);
+  k_factor<<<n_items, 512, smem, s>>>(items, ival, only, qcount);
   return cudaGetLastError();
 }
 
@@ -1048,9 +1220,9 @@ template cudaError_t launch_hh_level<float>(const SiteFacItem*, int, int, int, i
 template cudaError_t launch_hh_level<double>(const SiteFacItem*, int, int, int, int, void* const*,
                                              const int*, cudaStream_t, int);
 template cudaError_t launch_hh_extract<float>(const SiteFacItem*, int, void* const*, int*,
-                                              cudaStream_t, int);
+                                              cudaStream_t, int, double*);
 template cudaError_t launch_hh_extract<double>(const SiteFacItem*, int, void* const*, int*,
-                                               cudaStream_t, int);
+                                               cudaStream_t, int, double*);
 
 }  // namespace pepo
 

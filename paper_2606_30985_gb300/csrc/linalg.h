@@ -11,13 +11,16 @@ template <typename T>
 // 2: the sites the Cholesky branch handed over); only < 0: every site
 cudaError_t launch_hh_level(const SiteFacItem* items, int n_items, int level, int grid_x, int nmax,
                             void* const* ptrs, const int* ival, cudaStream_t s, int pass);
+// acct (may be null): 2 doubles accumulating the QR's algorithmic FLOPs and bytes
 template <typename T>
 cudaError_t launch_hh_extract(const SiteFacItem* items, int n_items, void* const* ptrs, int* ival,
-                              cudaStream_t s, int pass);
+                              cudaStream_t s, int pass, double* acct);
 cudaError_t launch_form(const SiteFacItem* items, int n_items, int grid_x, const int* ival,
                         cudaStream_t s, int only);
+// qcount (3 counters, may be null): sites per outcome of this pass, indexed
+// by the final branch value (0 Householder, 1 Cholesky-QR, 2 handed back)
 cudaError_t launch_factor(const SiteFacItem* items, int n_items, int rmax, int nmax, int* ival,
-                          cudaStream_t s, int only);
+                          cudaStream_t s, int only, unsigned long long* qcount);
 cudaError_t launch_core(const CoreItem* items, int n_items, int* ival, int* flags_base, cudaStream_t s);
 }  // namespace pepo
 

@@ -174,6 +174,8 @@ struct pepo_ctx {
   unsigned long long* d_delta2 = nullptr;
   unsigned long long* d_delta1 = nullptr;
   int* d_flags = nullptr;
+  unsigned long long* d_qr_count = nullptr;   // sites per QR branch (k_factor)
+  double* d_hh_acct = nullptr;   // Householder QR FLOPs and bytes (k_hh_extract; timing class K_HH)
   int* d_kerr = nullptr;   // bit 0: a tensor-core pipeline wait expired (bits: launch_leg_umma)
   unsigned long long wait_ns = kWaitNsDefault;   // limit of every tensor-core pipeline wait
   char* d_items = nullptr;
@@ -1119,6 +1121,8 @@ size_t layout_arena(pepo_ctx* c, char* base, Planner* keep) {
   c->d_delta1 = cv.take<unsigned long long>(c->n_inst);
   c->d_flags = cv.take<int>(c->n_inst);
   c->d_kerr = cv.take<int>(1);
+  c->d_qr_count = cv.take<unsigned long long>(3);
+  c->d_hh_acct = cv.take<double>(2);
   c->d_active = cv.take<int>(c->n_inst);
   c->d_items = cv.take<char>(P.st.bytes.size() + 256);
   // warm-start workspace: one network and one feature / prediction buffer
@@ -1332,19 +1336,19 @@ pepo_status run_gate_wave(pepo_ctx* c, Inst& I, GateWave& w) {
                                 c->d_ival, s, pass));
       g = (g + 3) / 4;
     }
-    LAUNCH_T(K_HH, nullptr, w.fac.n, launch_hh_extract<T>(w.fac.d, w.fac.n, c->d_ptrs, c->d_ival, s, pass));
+    LAUNCH_T(K_HH, nullptr, w.fac.n, launch_hh_extract<T>(w.fac.d, w.fac.n, c->d_ptrs, c->d_ival, s, pass, c->d_hh_acct));
     return PEPO_OK;
   };
   pepo_status st = tsqr(0);
   if (st != PEPO_OK) return st;
   LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_form(w.fac.d, w.fac.n, 16, c->d_ival, s, -1));
-  LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_factor(w.fac.d, w.fac.n, rmax, nmax, c->d_ival, s, -1));
+  LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_factor(w.fac.d, w.fac.n, rmax, nmax, c->d_ival, s, -1, c->d_qr_count));
   // the sites k_factor handed back (branch 2): Householder on the same absorbed
   // tensor, which the Gram only read
   st = tsqr(2);
   if (st != PEPO_OK) return st;
   LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_form(w.fac.d, w.fac.n, 16, c->d_ival, s, 2));
-  LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_factor(w.fac.d, w.fac.n, rmax, nmax, c->d_ival, s, 2));
+  LAUNCH_T(K_FACTOR, nullptr, w.fac.n, launch_factor(w.fac.d, w.fac.n, rmax, nmax, c->d_ival, s, 2, nullptr));
   return PEPO_OK;
 }
 
@@ -1824,6 +1828,8 @@ pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena, size
                              s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->d_flags, 0, sizeof(int) * n_inst, s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->d_kerr, 0, sizeof(int), s) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->d_qr_count, 0, 3 * sizeof(unsigned long long), s) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->d_hh_acct, 0, 2 * sizeof(double), s) == cudaSuccess;
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     c->cap_stream = nullptr;   // graphs off; launches go to the stream directly
     cudaGetLastError();
@@ -2535,6 +2541,18 @@ int pepo_num_bonds(const pepo_ctx* c, int inst) {
 
 long long pepo_launch_count(const pepo_ctx* c) { return c ? c->launches : 0; }
 
+pepo_status pepo_qr_branch_counts(pepo_ctx* c, long long* out, int reset) {
+  if (!c) return PEPO_E_INVALID;
+  if (!out) return fail(c, PEPO_E_INVALID, "pepo_qr_branch_counts: null output");
+  unsigned long long h[3] = {0, 0, 0};
+  if (cudaMemcpyAsync(h, c->d_qr_count, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      (reset && cudaMemsetAsync(c->d_qr_count, 0, sizeof(h), c->stream) != cudaSuccess) ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "pepo_qr_branch_counts: %s", cudaGetErrorString(cudaGetLastError()));
+  for (int i = 0; i < 3; ++i) out[i] = (long long)h[i];
+  return PEPO_OK;
+}
+
 const char* pepo_last_error(const pepo_ctx* c) { return c ? c->err.c_str() : kStaticErr; }
 
 void pepo_destroy(pepo_ctx* c) {
@@ -2603,10 +2621,18 @@ pepo_status pepo_get_timing(pepo_ctx* c, int k, long long* launches, double* ms,
   if (k < 0 || k >= K_NCLASS) return fail(c, PEPO_E_INVALID, "bad kernel class");
   timing_harvest(c);
   const auto& t = c->tot[k];
+  double dev[2] = {0.0, 0.0};
+  if (k == K_HH) {
+    // which sites take the Householder branch is decided on the device, so
+    // this class's work is counted there (k_hh_extract)
+    if (cudaMemcpyAsync(dev, c->d_hh_acct, sizeof(dev), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return fail(c, PEPO_E_CUDA, "pepo_get_timing: %s", cudaGetErrorString(cudaGetLastError()));
+  }
   if (launches) *launches = t.n;
   if (ms) *ms = t.ms;
-  if (bytes) *bytes = t.bytes;
-  if (flops) *flops = t.flops;
+  if (bytes) *bytes = t.bytes + dev[1];
+  if (flops) *flops = t.flops + dev[0];
   return PEPO_OK;
 }
 
@@ -2614,6 +2640,8 @@ pepo_status pepo_reset_timing(pepo_ctx* c) {
   if (!c) return PEPO_E_INVALID;
   timing_harvest(c);
   c->tot.assign(K_NCLASS, pepo_ctx::Tot());
+  if (cudaMemsetAsync(c->d_hh_acct, 0, 2 * sizeof(double), c->stream) != cudaSuccess)
+    return fail(c, PEPO_E_CUDA, "pepo_reset_timing: %s", cudaGetErrorString(cudaGetLastError()));
   return PEPO_OK;
 }
 
