@@ -92,7 +92,11 @@ typedef struct {
   double bp_tol;           /* Eq. 14 tolerance on the message diagonals */
   int bp_max_sweeps;       /* sweep budget (100) */
   int qr_n_thresh;         /* Eq. 10 branch: Cholesky-QR if n > qr_n_thresh ... */
-  double qr_ratio_thresh;  /* ... and m / n > qr_ratio_thresh (150, 150) */
+  double qr_ratio_thresh;  /* ... and m / n > qr_ratio_thresh (150, 150).  A Cholesky-QR
+                              site whose Gram has an accepted pivot keeping less than
+                              1e-4 (FP32 storage) / 1e-10 (FP64) of its own column's
+                              diagonal is factored by Householder instead (Sec. 4.2's
+                              fallback; counted by pepo_qr_branch_counts) */
   double pinv_rel;         /* rank threshold for message square roots (1e-12) */
   int gates;               /* pepo_gateset */
   int prec;                /* pepo_precision */
