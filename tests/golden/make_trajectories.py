@@ -12,6 +12,9 @@ Cases:
                                  split, dt = 0.05, ZZ / X gates (40 steps = t 2)
   paper4x4_chi40                 the paper's convention on 4x4 (XX / Z gates,
                                  h = J = -1, dt = 0.1, Z at (1, 1)), 20 steps
+  c4_chi64                       8x8, J = 1, h = 2, Z at (3, 3), second-order
+                                 split, dt = 0.05, chi_max = 64 (the prefix the
+                                 oracle finishes)
 Output: tests/golden/traj_<CASE>.txt
 """
 import os
@@ -37,6 +40,7 @@ CASES = {
     "c2_chi40": dict(C2, chi_max=40, nsteps=40),
     "c2_chi60": dict(C2, chi_max=60, nsteps=40),
     "paper4x4_chi40": dict(PAPER_4X4, chi_max=40, nsteps=20),
+    "c4_chi64": dict(C2, Lx=8, Ly=8, obs=(3, 3), chi_max=64, nsteps=24),
 }
 
 
