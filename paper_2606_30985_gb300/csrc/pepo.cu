@@ -1830,6 +1830,8 @@ pepo_status pepo_init(const pepo_config* cfgs, int n_inst, void* dev_arena, size
   ok = ok && cudaMemsetAsync(c->d_kerr, 0, sizeof(int), s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->d_qr_count, 0, 3 * sizeof(unsigned long long), s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->d_hh_acct, 0, 2 * sizeof(double), s) == cudaSuccess;
+  for (auto& I : c->inst)   // Pauli weights read as zero rows until the first correlator call
+    ok = ok && cudaMemsetAsync(I.pw, 0, sizeof(double) * 4 * (size_t)I.N, s) == cudaSuccess;
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     c->cap_stream = nullptr;   // graphs off; launches go to the stream directly
     cudaGetLastError();
