@@ -139,3 +139,48 @@ def test_dropped_first_site_gates_are_caught(monkeypatch):
     monkeypatch.setattr(run, "apply_site_gates", skip_first)
     with pytest.raises(AssertionError):
         ts.test_bond_dimension_grows_exactly_inside_the_light_cone((2, 1), 2, 1, "ZZ_X")
+
+
+def chain_weights(M_of=None, pauli=None, monkeypatch=None):
+    """Pauli weights of a 6-site chain after 4 untruncated steps (BP exact on
+    a tree), one bond regauged by a non-orthogonal X X^-1 so that its two
+    messages differ, against the dense operator's weights; M_of maps the
+    converged messages to the ones handed to the weights (a planted mistake)."""
+    N, nsteps = 6, 4
+    cfg = run.full_config(dict(Lx=N, Ly=1, J=1.0, h=0.7, dt=0.1, order=2, obs=(2, 0), chi_max=64, eps_cut=0.0,
+                               bp_alpha=1.0, bp_tol=1e-14, bp_max_sweeps=200))
+    net = pepo.Network(N, 1, cfg["obs"], "Z")
+    for _ in range(nsteps):
+        run.trotter_step(net, cfg)
+    a, b = 2, 3
+    ka, kb = net.axis(a, b), net.axis(b, a)
+    X = np.eye(net.O[a].shape[ka]) + 0.4 * np.random.default_rng(5).standard_normal((net.O[a].shape[ka],) * 2)
+    net.O[a] = pepo.leg_apply(net.O[a], ka, X.T)
+    net.O[b] = pepo.leg_apply(net.O[b], kb, np.linalg.inv(X))
+    run.measure(net, cfg)
+    ref = dense.site_pauli_weights(dense.evolve(N, 1, 1.0, 0.7, 0.1, 2, nsteps, (2, 0))["O"], N)
+    M = net.M if M_of is None else M_of(net.M)
+    if pauli is not None:
+        monkeypatch.setattr(obp.G, "PAULI_BY_INDEX", pauli)
+    w = obp.pauli_weights(net, M)
+    return float(np.max(np.abs(w - ref)))
+
+
+def test_unpatched_pauli_weights_pass():
+    assert chain_weights() < 1e-10
+
+
+def test_messages_of_the_wrong_direction_are_caught():
+    # M_{v->u} contracted on v's leg instead of M_{u->v}
+    assert chain_weights(lambda M: {(u, v): M[(v, u)] for (u, v) in M}) > 1e-3
+
+
+def test_dropped_environment_is_caught():
+    # the bare site tensor's weights (identity messages)
+    assert chain_weights(lambda M: {k: np.eye(m.shape[0]) for k, m in M.items()}) > 1e-3
+
+
+def test_swapped_pauli_components_are_caught(monkeypatch):
+    # Y and Z exchanged when the weights are read off
+    P = list(gates.PAULI_BY_INDEX)
+    assert chain_weights(pauli=[P[0], P[1], P[3], P[2]], monkeypatch=monkeypatch) > 1e-3

@@ -6,7 +6,10 @@ A.3 radii and spatial entropy).
 * Chains are trees, where BP is exact: after untruncated Trotter steps the
   weights from the BP environment equal the weights of the dense Trotter-
   evolved operator, O = sum_p P_p (x) B_p at each site, computed by partial
-  traces (an independent method).
+  traces (an independent method).  One bond is first regauged by a
+  non-orthogonal X X^-1 (the operator is unchanged, the two messages of
+  that bond then differ), so the pin also fixes which message of a bond
+  belongs to which site.
 * A centred observable on a 3x3 grid: the weights in the converged BP
   environment are C4-symmetric (the paper's exact four-fold symmetry of
   n(r, t), Sec. 6.4), although the colour order breaks the symmetry of the
@@ -18,7 +21,7 @@ import numpy as np
 
 from oracle import bp as obp
 from oracle import dense
-from oracle.pepo import Network
+from oracle.pepo import Network, leg_apply
 from oracle.run import full_config, measure, trotter_step
 
 
@@ -48,7 +51,14 @@ def test_chain_weights_equal_the_dense_operator():
     net = Network(N, 1, cfg["obs"], "Z")
     for _ in range(nsteps):
         trotter_step(net, cfg)
+    a, b = 2, 3
+    ka, kb = net.axis(a, b), net.axis(b, a)
+    chi = net.O[a].shape[ka]
+    X = np.eye(chi) + 0.4 * np.random.default_rng(5).standard_normal((chi, chi))
+    net.O[a] = leg_apply(net.O[a], ka, X.T)
+    net.O[b] = leg_apply(net.O[b], kb, np.linalg.inv(X))
     measure(net, cfg)
+    assert np.max(np.abs(net.M[(a, b)] - net.M[(b, a)])) > 1e-2
     w = obp.pauli_weights(net, net.M)
     ref = dense.site_pauli_weights(dense.evolve(N, 1, 1.0, 0.7, 0.1, 2, nsteps, (2, 0))["O"], N)
     assert np.max(np.abs(w - ref)) < 1e-10, np.max(np.abs(w - ref))
