@@ -23,3 +23,22 @@ def test_device_tensor_checks_on_cuda():
         pkg._device_tensor(t, torch.uint8, 17, "x")
     with pytest.raises(pkg.PepoError, match="contiguous"):
         pkg._device_tensor(torch.zeros(4, 4, dtype=torch.uint8, device="cuda").t(), torch.uint8, 1, "x")
+
+
+@pytest.mark.parametrize("Lx,Ly,obs", [(4, 3, (2, 1)), (5, 5, None), (1, 6, (0, 2)), (7, 2, (6, 0))])
+def test_spatial_observables_match_the_oracle_formulas(Lx, Ly, obs):
+    # the binding's R_L1, R_L2, S_frac of a weight map (host arithmetic, no
+    # GPU) against the oracle's restatement of Appendix A.3
+    import numpy as np
+    from oracle import bp as obp
+    cfg = pkg.Config(Lx=Lx, Ly=Ly, obs=obs)
+    rng = np.random.default_rng(Lx * 10 + Ly)
+    n = rng.random((Ly, Lx)) ** 3
+    n[rng.random((Ly, Lx)) < 0.3] = 0.0
+    got = pkg.spatial_observables(n, cfg)
+    o = obs if obs is not None else ((Lx - 1) // 2, (Ly - 1) // 2)
+    want = obp.spatial_observables(n.reshape(-1), Lx, Ly, o)
+    for k in ("R_L1", "R_L2", "S_frac"):
+        assert abs(got[k] - want[k]) < 1e-12, k
+    zero = pkg.spatial_observables(np.zeros((Ly, Lx)), cfg)
+    assert zero["R_L1"] == zero["R_L2"] == zero["S_frac"] == 0.0
