@@ -731,6 +731,23 @@ def spatial_observables(n, cfg):
     return dict(n=n, R_L1=r1, R_L2=r2, S_frac=S)
 
 
+def difference_field(n1, n2):
+    """The spatial chi-convergence field of Sec. 6.4: dn(r, t) = n_chi1(r, t) -
+    n_chi2(r, t) for two weight maps n[y, x] of the same grid, its largest
+    magnitude and, on a square grid, the largest deviation from four-fold
+    rotation symmetry about the grid centre (zero for a centred observable
+    on an odd grid when both runs are C4-symmetric)."""
+    a = np.asarray(n1, dtype=np.float64)
+    b = np.asarray(n2, dtype=np.float64)
+    if a.shape != b.shape or a.ndim != 2:
+        raise PepoError("difference_field: two [Ly, Lx] maps of the same grid expected")
+    d = a - b
+    out = dict(dn=d, max_abs=float(np.max(np.abs(d))) if d.size else 0.0)
+    if d.shape[0] == d.shape[1]:
+        out["c4_asym"] = float(max(np.max(np.abs(np.rot90(d, k) - d)) for k in (1, 2, 3)))
+    return out
+
+
 def flat_params(p):
     """Flat parameter vector (library order) from a dict W1, b1, W2, b2, W3, b3."""
     return np.concatenate([np.asarray(p[k], dtype=np.float32).reshape(-1) for k in ("W1", "b1", "W2", "b2", "W3", "b3")])

@@ -42,3 +42,21 @@ def test_spatial_observables_match_the_oracle_formulas(Lx, Ly, obs):
         assert abs(got[k] - want[k]) < 1e-12, k
     zero = pkg.spatial_observables(np.zeros((Ly, Lx)), cfg)
     assert zero["R_L1"] == zero["R_L2"] == zero["S_frac"] == 0.0
+
+
+def test_difference_field():
+    import numpy as np
+    rng = np.random.default_rng(3)
+    base = rng.random((5, 5))
+    sym = sum(np.rot90(base, k) for k in range(4))        # C4-symmetric about the centre
+    other = sym * 0.9 + 0.05
+    d = pkg.difference_field(sym, other)
+    assert np.allclose(d["dn"], sym - other)
+    assert abs(d["max_abs"] - np.max(np.abs(sym - other))) < 1e-15
+    assert d["c4_asym"] < 1e-12
+    skew = other.copy()
+    skew[0, 1] += 1e-3
+    assert abs(pkg.difference_field(sym, skew)["c4_asym"] - 1e-3) < 1e-12
+    assert "c4_asym" not in pkg.difference_field(np.zeros((3, 4)), np.ones((3, 4)))
+    with pytest.raises(pkg.PepoError):
+        pkg.difference_field(np.zeros((3, 3)), np.zeros((3, 4)))
