@@ -371,7 +371,11 @@ int pepo_num_bonds(const pepo_ctx* ctx, int inst);
  * bracketed by CUDA events on the context's stream and credited with its
  * algorithmic bytes and FLOPs, computed from the live bond dimensions read at
  * the start of each call (exact whenever chi does not change inside the call,
- * e.g. in the saturated regime).  Classes are numbered 0 .. pepo_timing_classes()-1. */
+ * e.g. in the saturated regime).  The Householder class ("householder_tsqr")
+ * is the exception: which sites take that branch is decided on the device,
+ * so its FLOPs (2 m n^2 - 2 n^3 / 3 per factored m x n matrix) and bytes (one
+ * read of it) are counted there, whether timing is on or not, and reset by
+ * pepo_reset_timing.  Classes are numbered 0 .. pepo_timing_classes()-1. */
 pepo_status pepo_set_timing(pepo_ctx* ctx, int enable);
 
 int pepo_timing_classes(void);
