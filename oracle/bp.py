@@ -27,17 +27,22 @@ N = 1 it is the paper's Eq. 9.
 
 Pauli weights (pauli_weights, n(r, t) of Sec. 6.4) are pinned by
 tests/test_oracle_spatial.py: on chains BP is exact, so they equal the
-dense operator's site weights (dense.site_pauli_weights); the initial
-network gives the observable at its site and the identity elsewhere; a
-centred observable on an odd grid gives C4-symmetric weights.
+dense operator's site weights (dense.site_pauli_weights), also after one
+bond is regauged by a non-orthogonal X X^-1 (its two messages then differ,
+which fixes the message of each leg); the initial network gives the
+observable at its site and the identity elsewhere; a centred observable on
+an odd grid gives C4-symmetric weights.  tests/test_oracle_mutations.py
+plants the plausible mistakes (wrong message direction, no environment,
+swapped components) and sees the chain pin fail.
 
 Pinned by: tests/test_oracle_pepo.py -- on trees (1 x N chains and the star
 around an edge site) BP is exact, so the Bethe value must equal the dense
 C(t), including the negative values of cos(2 J t)^3.  On loops the Bethe
 value has no closed form; it is pinned by the values the paper prints for
-the 4x4 grid at chi = 40 (tests/test_oracle_paper_4x4.py, a long test run
-with pytest --runslow): C(1.4) = 0.085 and C(2.0) = 0.0572, where the exact
-dynamics gives 0.0908 and 0.0645.
+the 4x4 grid (tests/test_oracle_paper_4x4.py): at chi = 20 the oracle's
+C(1.4) within 1e-3 of the printed 0.085 (default run), and at chi = 40
+(a long test run with pytest --runslow) C(1.4) = 0.085 and C(2.0) = 0.0572,
+where the exact dynamics gives 0.0908 and 0.0645.
 """
 import numpy as np
 
